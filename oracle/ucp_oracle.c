@@ -50,8 +50,8 @@
  *   - Epanechnikov fit: m = sample mean, w = scale * sample std (N-1), the
  *     scale being sqrt(5) by default (variance of the kernel is w^2/5);
  *   - histogram fit: lo = min, hi = max, bin index computed in IEEE binary32
- *     as floor(((x - lo) * B) / (hi - lo)) clamped to [0, B-1] (this file must
- *     be compiled with -ffp-contract=off), mass = count / N.
+ *     as floor((x - lo) * s) with s = B / (hi - lo), clamped to [0, B-1]
+ *     (this file must be compiled with -ffp-contract=off), mass = count / N.
  */
 #include <math.h>
 #include <stdint.h>
@@ -511,12 +511,11 @@ int orc_prob_hist_h5_at(const double *params, int H, int W, int B, const int64_t
 /* ------------------------------------------------------------------------ */
 /* exported: model fitting from an ensemble ens[N][H][W] (float32)           */
 
-static int hist_bin_f32(float x, float lo, float hi, int B) {
-  /* IEEE binary32, one rounding per operation, no contraction */
+static int hist_bin_f32(float x, float lo, float scale, int B) {
+  /* IEEE binary32, one rounding per operation, no contraction:
+   * scale = B / (hi - lo) is formed once per vertex by the caller */
   float d = x - lo;
-  float num = d * (float)B;
-  float den = hi - lo;
-  float q = num / den;
+  float q = d * scale;
   int i = (int)floorf(q);
   if (i < 0) i = 0;
   if (i > B - 1) i = B - 1;
@@ -574,7 +573,8 @@ int orc_fit(const float *ens, int N, int H, int W, int model, int B, double epan
         if (mn == mx) {
           cnt[0] = N;
         } else {
-          for (k = 0; k < N; ++k) cnt[hist_bin_f32(ens[(int64_t)k * plane + i], mn, mx, B)]++;
+          float scale = (float)B / (mx - mn);
+          for (k = 0; k < N; ++k) cnt[hist_bin_f32(ens[(int64_t)k * plane + i], mn, scale, B)]++;
         }
         params[i] = mn;
         params[plane + i] = mx;

@@ -254,7 +254,7 @@ def test_fit_matches_numpy(orc):
     h, _ = orc.fit(ens, 2, bins=B)
     lo, hi = ens.min(0), ens.max(0)
     with np.errstate(invalid="ignore", divide="ignore"):
-        q = ((ens - lo) * np.float32(B)) / (hi - lo)       # float32 numpy ops
+        q = (ens - lo) * (np.float32(B) / (hi - lo))       # float32 numpy ops
     idx = np.clip(np.nan_to_num(np.floor(q), nan=0.0).astype(np.int64), 0, B - 1)
     idx[:, 2, 3] = 0
     for j in range(B):
