@@ -1,0 +1,217 @@
+/*
+ * ucp.h -- C ABI of libucp: per-vertex critical-point probability fields of
+ * 2D uncertain scalar fields on one GB300 (sm_103a).
+ *
+ * Method: Athawale et al., "Uncertainty Visualization of Critical Points of
+ * 2D Scalar Fields for Parametric and Nonparametric Probabilistic Models"
+ * (arXiv 2407.18015).  Problem statement (Sec. "Background and Problem
+ * Setting"): a regular H x W grid; at every vertex p a random variable X_1
+ * with finite support [a_1, b_1]; its axis neighbours e, n, w, s carry X_2..X_5;
+ * the variables are independent (except for the multivariate Gaussian model).
+ * The library returns, per vertex,
+ *
+ *   P_min = Pr[X_1 < X_n for every neighbour n] = int pdf_1(x) prod_n G_n(x) dx
+ *   P_max = Pr[X_1 > X_n for every neighbour n] = int pdf_1(x) prod_n F_n(x) dx
+ *
+ * (Eq. localMinimumProb; the local maximum by negation, Sec. "Local Maximum
+ * Probability"), with F_n the CDF and G_n = 1 - F_n the survival of X_n.
+ *
+ * Conventions shared by every call
+ *   - Arrays are row-major and plane-major.  An ensemble is ens[N][H][W]
+ *     float32 (member k of vertex (y,x) at ens[(k*H + y)*W + x]).  Model
+ *     parameters are params[P][H][W] float32 (see UCP_* model comments).
+ *     Probability fields are [H][W] float32; vertex status is [H][W] uint8.
+ *   - Unless a call says "host", every array pointer is a DEVICE pointer on
+ *     the context's device, owned by the caller and borrowed for the
+ *     stream-ordered duration of the call (the library never frees it).
+ *     Work is enqueued on `stream` (NULL = the legacy default stream) and the
+ *     call returns without synchronising.
+ *   - Neighbours of (y,x): e=(y,x+1), n=(y-1,x), w=(y,x-1), s=(y+1,x).
+ *     UCP_BOUNDARY_INGRID uses the in-grid ones (2 at a corner, 3 on an edge;
+ *     a 1 x W grid is the paper's two-neighbour case, Sec. "Critical Point
+ *     Probability (Two-Pixel Neighborhood)"); UCP_BOUNDARY_ZERO writes 0 at
+ *     every vertex that lacks a neighbour.  The paper ignores the boundary.
+ *   - Every call returns a ucp_status.  Arguments are validated on the host
+ *     before anything is enqueued; UCP_ERR_ARG / UCP_ERR_SHAPE mean nothing
+ *     ran.  UCP_ERR_CUDA keeps the CUDA error text (ucp_last_error).
+ *     Per-vertex numerical problems never fail a call: they set bits of the
+ *     optional vertex_status array (ucp_vertex_flag); P is NaN only for
+ *     UCP_V_NONFINITE, UCP_V_BAD_PARAMS and UCP_V_CHOL_FAIL.
+ *   - No kernel of this library traps, asserts or waits without a bound.
+ */
+#ifndef UCP_H
+#define UCP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ucp_ctx ucp_ctx;
+typedef struct ucp_batch ucp_batch;
+/* identical to cudaStream_t */
+typedef struct CUstream_st *ucp_stream;
+
+typedef enum {
+  /* independent uniform, params (a, b): pdf 1/(b-a) on [a, b]
+   * (Sec. "Parametric Noise Models").  Fit: a = min, b = max of the members
+   * (Sec. "Validation and Performance of Proposed Algorithms"). */
+  UCP_UNIFORM = 0,
+  /* independent Epanechnikov, params (m, w): pdf 3/(4w)(1-((x-m)/w)^2) on
+   * [m-w, m+w] (Sec. "Parametric Noise Models", m=(a+b)/2, w=(b-a)/2).  Fit:
+   * m = sample mean, w = epan_width_scale * sample std (N-1 divisor); the
+   * paper fixes no constant, the default sqrt(5) matches the variance. */
+  UCP_EPANECHNIKOV = 1,
+  /* independent B-bin histogram, params (lo, hi, w_0 .. w_{B-1}): B equal
+   * bins on [lo, hi], pdf = sum_j w_j/h on bin j (a mixture of
+   * non-overlapping uniform kernels, Sec. "Closed-Form Formulation").  Fit:
+   * lo = min, hi = max, bin of member x = floor((x - lo) * (B / (hi - lo)))
+   * in IEEE binary32 (one rounding per operation), clamped to [0, B-1],
+   * w_j = count_j / N.  Masses need not sum to 1: the survival is used in the
+   * mixture form sum_j w_j S_j(x). */
+  UCP_HISTOGRAM = 2,
+  /* multivariate Gaussian over (X_v, X_e, X_n, X_w, X_s) (the prior work the
+   * paper compares with, Sec. "Comparison of Parametric Vs. Nonparametric
+   * Models"), evaluated by Monte Carlo.  params: planes 0..4 = means of
+   * (v, e, n, w, s); planes 5..19 = their covariance (N-1 divisor), packed
+   * lower triangle row by row ((0,0),(1,0),(1,1),(2,0),...); entries of
+   * absent neighbours are 0.  Sampling contract: sample s of the vertex with
+   * linear index i draws two Philox4x32-10 blocks (Salmon et al., SC'11) with
+   * counter (s, i, field_id, j), j = 0, 1, and key (seed & 0xffffffff,
+   * seed >> 32); words r give uniforms ((r >> 8) + 0.5) * 2^-24; Box-Muller
+   * on (u0,u1), (u2,u3), (u4,u5) gives z_0..z_5; x = mu + L z with L the
+   * Cholesky factor of the covariance of the vertex and its present
+   * neighbours in the order v, e, n, w, s (z_0..z_k used).  If the
+   * factorisation fails, eps*I is added, eps = 1e-6 * trace / (k+1), times
+   * 10 per retry, three retries (UCP_V_CHOL_JITTER), else UCP_V_CHOL_FAIL.
+   * A zero-trace covariance is deterministic (UCP_V_DEGENERATE). */
+  UCP_MVN_MC = 3
+} ucp_model;
+
+typedef enum { UCP_MIN = 1, UCP_MAX = 2 } ucp_cptype; /* bit mask */
+
+typedef enum { UCP_BOUNDARY_INGRID = 0, UCP_BOUNDARY_ZERO = 1 } ucp_boundary;
+
+typedef enum {
+  UCP_OK = 0,
+  UCP_ERR_ARG = 1,         /* null pointer, bad enum, bins/samples out of range */
+  UCP_ERR_SHAPE = 2,       /* N, H or W < 1, or sizes beyond the index limits   */
+  UCP_ERR_CUDA = 3,        /* a CUDA call failed; see ucp_last_error              */
+  UCP_ERR_NOMEM = 4,       /* device workspace could not be allocated             */
+  UCP_ERR_TIMEOUT = 5,     /* a bounded device-side wait expired                  */
+  UCP_ERR_UNSUPPORTED = 6  /* the combination is not implemented                  */
+} ucp_status;
+
+typedef enum {
+  UCP_V_DEGENERATE = 1,  /* the vertex is a point mass (min == max of members)  */
+  UCP_V_NONFINITE = 2,   /* a participating member or parameter is NaN/Inf      */
+  UCP_V_BAD_PARAMS = 4,  /* a participating parameter set is invalid
+                            (a > b, w < 0, lo > hi, a negative mass)            */
+  UCP_V_CHOL_JITTER = 8, /* MVN covariance needed diagonal jitter               */
+  UCP_V_CHOL_FAIL = 16   /* MVN covariance could not be factorised              */
+} ucp_vertex_flag;
+
+typedef struct {
+  int model;              /* ucp_model                                          */
+  int bins;               /* histogram bin count B, 1..64 (ignored otherwise)   */
+  float epan_width_scale; /* Epanechnikov w = scale * std; <= 0 means sqrt(5)   */
+  int mc_samples;         /* MVN samples per vertex (>= 1)                      */
+  uint64_t seed;          /* MVN Philox key                                     */
+  uint32_t field_id;      /* MVN Philox counter word 2                          */
+  int boundary;           /* ucp_boundary                                       */
+} ucp_model_desc;
+
+/* Text of a status code (static storage). */
+const char *ucp_status_string(int status);
+
+/* Library version string "ucp <major>.<minor>". */
+const char *ucp_version(void);
+
+/* Number of parameter planes P of a model: 2 (uniform, Epanechnikov),
+ * 2 + bins (histogram), 20 (MVN); 0 for an invalid descriptor. */
+int ucp_param_count(const ucp_model_desc *desc);
+
+/* Create a context bound to CUDA device `device`.  The context owns its
+ * device workspace (grown on demand, freed by ucp_destroy) and caches
+ * kernel attributes.  One context may be used from one host thread at a
+ * time.  Errors: UCP_ERR_ARG (ctx NULL), UCP_ERR_CUDA (no such device). */
+int ucp_create(ucp_ctx **ctx, int device);
+int ucp_destroy(ucp_ctx *ctx);
+
+/* Text of the last CUDA error seen by this context ("" if none). */
+const char *ucp_last_error(const ucp_ctx *ctx);
+
+/* Fit the per-vertex model (the statistics pass only): reads ens[N][H][W],
+ * writes params[P][H][W] and, if vertex_status is not NULL, status[H][W]
+ * (UCP_V_DEGENERATE, UCP_V_NONFINITE; non-finite members give NaN params).
+ * Models: Sec. "Parametric Noise Models" / "Nonparametric Noise Models"
+ * (fit rules in ucp_model).  For UCP_MVN_MC the covariance involves the
+ * neighbours' members. */
+int ucp_fit(ucp_ctx *ctx, const float *ens, int N, int H, int W, const ucp_model_desc *desc,
+            float *params, uint8_t *vertex_status, ucp_stream stream);
+
+/* Probability fields from parameters supplied directly, e.g. the uniform
+ * model [d' - eb/2, d' + eb/2] of a decompressed field d' with error bound eb
+ * (Sec. "Real Datasets", climate data).  cptypes: UCP_MIN | UCP_MAX; out_min
+ * (out_max) must be non-NULL when its bit is set.  vertex_status may be
+ * NULL. */
+int ucp_probability_from_params(ucp_ctx *ctx, const float *params, int H, int W,
+                                const ucp_model_desc *desc, unsigned cptypes, float *out_min,
+                                float *out_max, uint8_t *vertex_status, ucp_stream stream);
+
+/* Fused fit + probability from an ensemble (one pass over the members; the
+ * parameters never reach global memory).  Arguments as above. */
+int ucp_probability(ucp_ctx *ctx, const float *ens, int N, int H, int W,
+                    const ucp_model_desc *desc, unsigned cptypes, float *out_min,
+                    float *out_max, uint8_t *vertex_status, ucp_stream stream);
+
+/* Same as ucp_probability with HOST arrays: copies ens_host to a
+ * context-owned device buffer, computes, copies the fields back and
+ * synchronises the stream before returning.  Pinned host memory gives the
+ * full copy bandwidth; pageable memory works too.  out_min_host /
+ * out_max_host follow cptypes; status_host may be NULL. */
+int ucp_probability_host(ucp_ctx *ctx, const float *ens_host, int N, int H, int W,
+                         const ucp_model_desc *desc, unsigned cptypes, float *out_min_host,
+                         float *out_max_host, uint8_t *status_host, ucp_stream stream);
+
+/* Uniform parameters [d' - eb/2, d' + eb/2] from a decompressed field
+ * d'[H][W] and an absolute error bound eb >= 0 (Sec. "Real Datasets").
+ * params: [2][H][W]. */
+int ucp_params_from_error_bound(ucp_ctx *ctx, const float *decompressed, float eb, int H,
+                                int W, float *params, ucp_stream stream);
+
+/* Adjoint: gradient of L = sum_v weight_v * P_v (P_min if cptype ==
+ * UCP_MIN, P_max if UCP_MAX) with respect to every vertex's parameters.
+ * grad_params: [Q][H][W] with Q = 2 for uniform (d/da, d/db) and
+ * Epanechnikov (d/dm, d/dw), Q = bins for histogram (d/dw_j, the masses;
+ * lo and hi are held fixed).  The paper has no gradients; this is the exact
+ * derivative of its closed form: each P_v depends on the parameters of v and
+ * of its neighbours; neighbour factors are differentiated under the
+ * integral, the uniform centre adds the boundary terms of its moving support.
+ * Point masses get zero derivatives for their own (a, b) / (m, w).  Uses
+ * context workspace of 5*Q*H*W floats.  Not available for UCP_MVN_MC
+ * (UCP_ERR_UNSUPPORTED). */
+int ucp_backward(ucp_ctx *ctx, const float *params, int H, int W, const ucp_model_desc *desc,
+                 int cptype, const float *weight, float *grad_params, ucp_stream stream);
+
+/* Batched launch: many fields of different sizes, member counts, models
+ * (uniform, Epanechnikov, histogram) and types in one persistent kernel.
+ * ucp_batch_add records a field (device pointers, borrowed until the batch
+ * is destroyed); ucp_batch_tune times the tile shapes on `stream` and keeps
+ * the fastest per model (optional; call before any stream capture);
+ * ucp_batch_run enqueues the whole batch (a counter reset and one kernel
+ * launch, so it can be captured into a CUDA graph). */
+int ucp_batch_create(ucp_ctx *ctx, ucp_batch **batch);
+int ucp_batch_add(ucp_batch *batch, const float *ens, int N, int H, int W,
+                  const ucp_model_desc *desc, unsigned cptypes, float *out_min, float *out_max);
+int ucp_batch_tune(ucp_batch *batch, ucp_stream stream);
+int ucp_batch_run(ucp_batch *batch, ucp_stream stream);
+int ucp_batch_destroy(ucp_batch *batch);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UCP_H */

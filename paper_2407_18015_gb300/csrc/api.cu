@@ -1,0 +1,278 @@
+// api.cu -- the C ABI declared in include/ucp.h.
+//
+// Host code only: argument validation (before anything is enqueued), the
+// context (device, workspace, last CUDA error), and the kernel launches of
+// closed.cu, mvn.cu, backward.cu and batch.cu.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "launch.h"
+#include "ucp.h"
+#include "ucp_internal.h"
+
+using namespace ucp;
+
+namespace {
+
+const char *kStatusText[] = {
+    "ok",
+    "invalid argument",
+    "invalid shape",
+    "CUDA error",
+    "out of device memory",
+    "bounded device-side wait expired",
+    "unsupported combination",
+};
+
+struct DeviceGuard {
+  int prev = -1;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) err = cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+int valid_desc(const ucp_model_desc *d, bool allow_mvn) {
+  if (!d) return UCP_ERR_ARG;
+  if (d->model < UCP_UNIFORM || d->model > UCP_MVN_MC) return UCP_ERR_ARG;
+  if (d->model == UCP_MVN_MC && !allow_mvn) return UCP_ERR_UNSUPPORTED;
+  if (d->model == UCP_HISTOGRAM && (d->bins < 1 || d->bins > kMaxBinsHost)) return UCP_ERR_ARG;
+  if (d->model == UCP_MVN_MC && d->mc_samples < 1) return UCP_ERR_ARG;
+  if (d->boundary != UCP_BOUNDARY_INGRID && d->boundary != UCP_BOUNDARY_ZERO) return UCP_ERR_ARG;
+  return UCP_OK;
+}
+
+int valid_shape(long long N, long long H, long long W) {
+  if (N < 1 || H < 1 || W < 1) return UCP_ERR_SHAPE;
+  // vertex indices are 32-bit (Philox counter word 1); members 64-bit
+  if (H * W > 0xFFFFFFFFLL) return UCP_ERR_SHAPE;
+  if (H > 0x7FFFFFFFLL || W > 0x7FFFFFFFLL) return UCP_ERR_SHAPE;
+  return UCP_OK;
+}
+
+int valid_types(unsigned cptypes, const float *out_min, const float *out_max) {
+  if (cptypes == 0 || (cptypes & ~3u)) return UCP_ERR_ARG;
+  if ((cptypes & 1u) && !out_min) return UCP_ERR_ARG;
+  if ((cptypes & 2u) && !out_max) return UCP_ERR_ARG;
+  return UCP_OK;
+}
+
+float epan_scale(const ucp_model_desc *d) {
+  return d->epan_width_scale > 0.f ? d->epan_width_scale : 2.2360679774997896f;
+}
+
+}  // namespace
+
+int ucp_set_error(ucp_ctx *ctx, cudaError_t e) {
+  if (e == cudaSuccess) return UCP_OK;
+  if (ctx) snprintf(ctx->last_error, sizeof(ctx->last_error), "%s: %s", cudaGetErrorName(e),
+                    cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? UCP_ERR_NOMEM : UCP_ERR_CUDA;
+}
+
+int ucp_ensure_work(ucp_ctx *ctx, size_t bytes) {
+  if (bytes <= ctx->work_bytes) return UCP_OK;
+  if (ctx->work) cudaFree(ctx->work);
+  ctx->work = nullptr;
+  ctx->work_bytes = 0;
+  cudaError_t e = cudaMalloc(&ctx->work, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return ucp_set_error(ctx, e);
+  }
+  ctx->work_bytes = bytes;
+  return UCP_OK;
+}
+
+extern "C" {
+
+const char *ucp_status_string(int status) {
+  if (status < 0 || status >= (int)(sizeof(kStatusText) / sizeof(kStatusText[0])))
+    return "unknown status";
+  return kStatusText[status];
+}
+
+const char *ucp_version(void) { return "ucp 1.0"; }
+
+int ucp_param_count(const ucp_model_desc *desc) {
+  if (valid_desc(desc, true) != UCP_OK) return 0;
+  return param_planes(desc->model, desc->bins);
+}
+
+int ucp_create(ucp_ctx **ctx, int device) {
+  if (!ctx) return UCP_ERR_ARG;
+  *ctx = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return UCP_ERR_CUDA;
+  }
+  if (device < 0 || device >= n) return UCP_ERR_ARG;
+  ucp_ctx *c = new (std::nothrow) ucp_ctx();
+  if (!c) return UCP_ERR_NOMEM;
+  c->device = device;
+  DeviceGuard g(device);
+  if (g.err != cudaSuccess) {
+    delete c;
+    return UCP_ERR_CUDA;
+  }
+  e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) {
+    delete c;
+    return UCP_ERR_CUDA;
+  }
+  *ctx = c;
+  return UCP_OK;
+}
+
+int ucp_destroy(ucp_ctx *ctx) {
+  if (!ctx) return UCP_ERR_ARG;
+  {
+    DeviceGuard g(ctx->device);
+    if (ctx->work) cudaFree(ctx->work);
+    if (ctx->host_ens) cudaFree(ctx->host_ens);
+    if (ctx->host_out) cudaFree(ctx->host_out);
+    if (ctx->pipe_ready) {
+      for (int i = 0; i < 3; ++i) cudaStreamDestroy(ctx->pipe[i]);
+      for (int k = 0; k < 2; ++k)
+        for (int i = 0; i < 64; ++i) cudaEventDestroy(ctx->pipe_ev[k][i]);
+    }
+  }
+  delete ctx;
+  return UCP_OK;
+}
+
+const char *ucp_last_error(const ucp_ctx *ctx) { return ctx ? ctx->last_error : ""; }
+
+int ucp_fit(ucp_ctx *ctx, const float *ens, int N, int H, int W, const ucp_model_desc *desc,
+            float *params, uint8_t *vertex_status, ucp_stream stream) {
+  if (!ctx || !ens || !params) return UCP_ERR_ARG;
+  int rc = valid_desc(desc, true);
+  if (rc) return rc;
+  if ((rc = valid_shape(N, H, W))) return rc;
+  DeviceGuard g(ctx->device);
+  if (g.err != cudaSuccess) return ucp_set_error(ctx, g.err);
+  Field f{};
+  f.ens = ens;
+  f.params = params;
+  f.status = vertex_status;
+  f.plane = (long long)H * W;
+  f.N = N; f.H = H; f.W = W; f.B = desc->bins;
+  f.y0 = 0; f.y1 = H;
+  f.boundary = desc->boundary;
+  f.epan_scale = epan_scale(desc);
+  cudaError_t e = desc->model == UCP_MVN_MC ? launch_mvn_fit(f, (cudaStream_t)stream)
+                                            : launch_fit(f, desc->model, (cudaStream_t)stream);
+  return ucp_set_error(ctx, e);
+}
+
+static int probability_impl(ucp_ctx *ctx, const float *ens, const float *params, int N, int H,
+                            int W, const ucp_model_desc *desc, unsigned cptypes, float *out_min,
+                            float *out_max, uint8_t *vertex_status, cudaStream_t stream) {
+  Field f{};
+  f.ens = ens;
+  f.params = params;
+  f.out_min = out_min;
+  f.out_max = out_max;
+  f.status = vertex_status;
+  f.plane = (long long)H * W;
+  f.N = N; f.H = H; f.W = W; f.B = desc->bins;
+  f.y0 = 0; f.y1 = H;
+  f.boundary = desc->boundary;
+  f.epan_scale = epan_scale(desc);
+  f.cptypes = cptypes;
+  cudaError_t e;
+  if (desc->model == UCP_MVN_MC)
+    e = launch_mvn_mc(f, ens != nullptr, desc->mc_samples, desc->seed, desc->field_id, stream);
+  else
+    e = launch_closed(f, desc->model, ens != nullptr, stream);
+  return ucp_set_error(ctx, e);
+}
+
+int ucp_probability_from_params(ucp_ctx *ctx, const float *params, int H, int W,
+                                const ucp_model_desc *desc, unsigned cptypes, float *out_min,
+                                float *out_max, uint8_t *vertex_status, ucp_stream stream) {
+  if (!ctx || !params) return UCP_ERR_ARG;
+  int rc = valid_desc(desc, true);
+  if (rc) return rc;
+  if ((rc = valid_shape(1, H, W))) return rc;
+  if ((rc = valid_types(cptypes, out_min, out_max))) return rc;
+  DeviceGuard g(ctx->device);
+  if (g.err != cudaSuccess) return ucp_set_error(ctx, g.err);
+  return probability_impl(ctx, nullptr, params, 1, H, W, desc, cptypes, out_min, out_max,
+                          vertex_status, (cudaStream_t)stream);
+}
+
+int ucp_probability(ucp_ctx *ctx, const float *ens, int N, int H, int W,
+                    const ucp_model_desc *desc, unsigned cptypes, float *out_min, float *out_max,
+                    uint8_t *vertex_status, ucp_stream stream) {
+  if (!ctx || !ens) return UCP_ERR_ARG;
+  int rc = valid_desc(desc, true);
+  if (rc) return rc;
+  if ((rc = valid_shape(N, H, W))) return rc;
+  if ((rc = valid_types(cptypes, out_min, out_max))) return rc;
+  DeviceGuard g(ctx->device);
+  if (g.err != cudaSuccess) return ucp_set_error(ctx, g.err);
+  return probability_impl(ctx, ens, nullptr, N, H, W, desc, cptypes, out_min, out_max,
+                          vertex_status, (cudaStream_t)stream);
+}
+
+int ucp_probability_host(ucp_ctx *ctx, const float *ens_host, int N, int H, int W,
+                         const ucp_model_desc *desc, unsigned cptypes, float *out_min_host,
+                         float *out_max_host, uint8_t *status_host, ucp_stream stream) {
+  if (!ctx || !ens_host) return UCP_ERR_ARG;
+  int rc = valid_desc(desc, true);
+  if (rc) return rc;
+  if ((rc = valid_shape(N, H, W))) return rc;
+  if ((rc = valid_types(cptypes, out_min_host, out_max_host))) return rc;
+  DeviceGuard g(ctx->device);
+  if (g.err != cudaSuccess) return ucp_set_error(ctx, g.err);
+  return ucp_host_pipeline(ctx, ens_host, N, H, W, desc, cptypes, out_min_host, out_max_host,
+                           status_host, (cudaStream_t)stream);
+}
+
+int ucp_params_from_error_bound(ucp_ctx *ctx, const float *decompressed, float eb, int H,
+                                int W, float *params, ucp_stream stream) {
+  if (!ctx || !decompressed || !params) return UCP_ERR_ARG;
+  if (!(eb >= 0.f) || !isfinite(eb)) return UCP_ERR_ARG;
+  int rc = valid_shape(1, H, W);
+  if (rc) return rc;
+  DeviceGuard g(ctx->device);
+  if (g.err != cudaSuccess) return ucp_set_error(ctx, g.err);
+  return ucp_set_error(ctx, launch_eb_params(decompressed, eb, (long long)H * W, params,
+                                             (cudaStream_t)stream));
+}
+
+int ucp_backward(ucp_ctx *ctx, const float *params, int H, int W, const ucp_model_desc *desc,
+                 int cptype, const float *weight, float *grad_params, ucp_stream stream) {
+  if (!ctx || !params || !weight || !grad_params) return UCP_ERR_ARG;
+  int rc = valid_desc(desc, false);
+  if (rc) return rc;
+  if (cptype != UCP_MIN && cptype != UCP_MAX) return UCP_ERR_ARG;
+  if ((rc = valid_shape(1, H, W))) return rc;
+  DeviceGuard g(ctx->device);
+  if (g.err != cudaSuccess) return ucp_set_error(ctx, g.err);
+  const int Q = desc->model == UCP_HISTOGRAM ? desc->bins : 2;
+  const size_t bytes = (size_t)5 * Q * H * W * sizeof(float);
+  if ((rc = ucp_ensure_work(ctx, bytes))) return rc;
+  Field f{};
+  f.params = params;
+  f.plane = (long long)H * W;
+  f.N = 1; f.H = H; f.W = W; f.B = desc->bins;
+  f.y0 = 0; f.y1 = H;
+  f.boundary = desc->boundary;
+  f.cptypes = (unsigned)cptype;
+  return ucp_set_error(ctx, launch_backward(f, desc->model, cptype, weight, (float *)ctx->work,
+                                            grad_params, (cudaStream_t)stream));
+}
+
+}  // extern "C"

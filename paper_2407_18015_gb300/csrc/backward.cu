@@ -1,0 +1,721 @@
+// backward.cu -- adjoint of L = sum_v W_v P_v with respect to every vertex's
+// model parameters (uniform (a, b), Epanechnikov (m, w), histogram masses).
+//
+// P_v depends on the parameters of v and of its in-grid neighbours.  Pass 1
+// (one thread per centre v) writes W_v dP_v/d(theta_u) for u = v and its four
+// neighbours into rows[slot][q][H][W] (slot 0 = v, 1..4 = e, n, w, s).  Pass 2
+// gathers, for every u, its own row and the rows its neighbours wrote about it
+// (u is the west neighbour of its east neighbour, and so on), in a fixed
+// order, so the result is deterministic and needs no atomics.
+//
+// Derivatives (exact, of the closed forms integrated in device.cuh):
+//   neighbour n: d/dtheta_n int pdf_1 prod G = int pdf_1 (dG_n/dtheta_n) prod_{m!=n} G_m
+//     uniform:       dG/da = s G, dG/db = s (1 - G) on the support (s = 1/(b-a))
+//     Epanechnikov:  dG/dm = pdf_n, dG/dw = pdf_n (x - m)/w
+//     histogram:     dG/dw_q = survival of the uniform kernel of bin q
+//   centre: uniform adds the boundary terms of its moving support,
+//     dP/da1 = (P - H(a1))/(b1-a1), dP/db1 = (H(b1) - P)/(b1-a1), H = prod G;
+//     Epanechnikov differentiates the density (it vanishes at the ends);
+//     histogram: dP/dw_j = (1/h) int_{bin j} prod G.
+// Maxima use the negated variables (P_max(theta) = P_min(-theta)).
+#include "device.cuh"
+#include "launch.h"
+
+namespace ucp {
+
+namespace {
+
+__device__ __forceinline__ float qnan_b() { return __int_as_float(0x7fc00000); }
+
+// Leave-one-out products of four values.
+__device__ __forceinline__ void loo4(const float *g, float *out) {
+  const float p01 = g[0] * g[1], p23 = g[2] * g[3];
+  out[0] = g[1] * p23;
+  out[1] = g[0] * p23;
+  out[2] = p01 * g[3];
+  out[3] = p01 * g[2];
+}
+
+// ---------------------------------------------------------------------------
+// uniform, minimum, in the frame of the centre's lower end
+
+struct UniGrad {
+  float ga, gb;      // centre
+  float na[4], nb[4];  // neighbours (original slot order)
+};
+
+// al/sl/bl: neighbour start, slope (0 for point masses / absent), local end;
+// kind: 0 absent, 1 continuous, 2 point mass (at al)
+__device__ __forceinline__ void uniform_grad_side(float W1, float R, const float *al,
+                                                  const float *sl, const int *kind,
+                                                  UniGrad &g) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) g.na[i] = g.nb[i] = 0.f;
+  // survival product at the centre's ends (point masses: step, strict)
+  float H0 = 1.f, H1 = 1.f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if (kind[i] == 1) {
+      H0 *= fminf(fmaxf(fmaf(-(0.f - al[i]), sl[i], 1.f), 0.f), 1.f);
+      H1 *= fminf(fmaxf(fmaf(-(W1 - al[i]), sl[i], 1.f), 0.f), 1.f);
+    } else if (kind[i] == 2) {
+      H0 *= (0.f < al[i]) ? 1.f : 0.f;
+      H1 *= (W1 < al[i]) ? 1.f : 0.f;
+    }
+  }
+  if (R < W1) H1 = 0.f;
+  if (!(R > 0.f)) {
+    g.ga = -H0 / W1;
+    g.gb = 0.f;
+    return;
+  }
+  float t[4];
+  float pay[3][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const bool act = kind[i] == 1;
+    t[i] = act ? fminf(fmaxf(al[i], 0.f), R) : R;
+    pay[0][i] = act ? al[i] : kFar;
+    pay[1][i] = act ? sl[i] : 0.f;
+    pay[2][i] = (float)i;
+  }
+  sort4<3>(t, pay);
+  const float x[6] = {0.f, t[0], t[1], t[2], t[3], R};
+  float I[5];
+  float Db[4] = {0.f, 0.f, 0.f, 0.f};  // per sorted factor: int of (1-G_i) prod_{m!=i} G
+  I[0] = x[1];
+  float L[4], Rv[4], L2[4], R2[4];
+#pragma unroll
+  for (int j = 1; j <= 4; ++j) {
+    const float x0 = x[j], x1 = x[j + 1], len = x1 - x0;
+#pragma unroll
+    for (int i = 0; i < j; ++i) {
+      L[i] = fmaxf(fmaf(-(x0 - pay[0][i]), pay[1][i], 1.f), 0.f);
+      Rv[i] = fmaxf(fmaf(-(x1 - pay[0][i]), pay[1][i], 1.f), 0.f);
+    }
+    float Ij;
+    if (j == 1) Ij = bern_mean<1>(L, Rv);
+    else if (j == 2) Ij = bern_mean<2>(L, Rv);
+    else if (j == 3) Ij = bern_mean<3>(L, Rv);
+    else Ij = bern_mean<4>(L, Rv);
+    I[j] = len * Ij;
+#pragma unroll
+    for (int i = 0; i < j; ++i) {
+#pragma unroll
+      for (int q = 0; q < j; ++q) {
+        L2[q] = (q == i) ? 1.f - L[q] : L[q];
+        R2[q] = (q == i) ? 1.f - Rv[q] : Rv[q];
+      }
+      float Bi;
+      if (j == 1) Bi = bern_mean<1>(L2, R2);
+      else if (j == 2) Bi = bern_mean<2>(L2, R2);
+      else if (j == 3) Bi = bern_mean<3>(L2, R2);
+      else Bi = bern_mean<4>(L2, R2);
+      Db[i] += len * Bi;
+    }
+  }
+  const float iW = 1.f / W1;
+  const float P = (I[0] + I[1] + I[2] + I[3] + I[4]) * iW;
+  g.ga = (P - H0) * iW;
+  g.gb = (H1 - P) * iW;
+  // factor i (sorted) is active on pieces j >= i + 1
+  float tail = 0.f;
+  float Da[4];
+#pragma unroll
+  for (int i = 3; i >= 0; --i) {
+    tail += I[i + 1];
+    Da[i] = tail;
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int o = (int)pay[2][i];
+    const float s = pay[1][i] * iW;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (q == o) {
+        g.na[q] = s * Da[i];
+        g.nb[q] = s * Db[i];
+      }
+    }
+  }
+}
+
+// full uniform gradient of one centre (min or max) -> rows
+__device__ __forceinline__ void uniform_grad_vertex(float a1, float b1, const float *an,
+                                                   const float *bn, const bool *present,
+                                                   bool want_max, UniGrad &out) {
+  // for the maximum, work on -X: (a, b) -> (-b, -a)
+  const float A1 = want_max ? -b1 : a1, B1 = want_max ? -a1 : b1;
+  float A[4], Bv[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    A[i] = want_max ? -bn[i] : an[i];
+    Bv[i] = want_max ? -an[i] : bn[i];
+  }
+  UniGrad g;
+  if (A1 == B1) {
+    // point-mass centre: P = prod_n Pr[X_n > c]
+    const float c = A1;
+    float S[4], dsa[4], dsb[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      S[i] = 1.f; dsa[i] = 0.f; dsb[i] = 0.f;
+      if (!present[i]) continue;
+      if (A[i] == Bv[i]) {
+        S[i] = A[i] > c ? 1.f : 0.f;
+      } else {
+        const float s = 1.f / (Bv[i] - A[i]);
+        const float v = (Bv[i] - c) * s;
+        S[i] = fminf(fmaxf(v, 0.f), 1.f);
+        if (A[i] < c && c < Bv[i]) {
+          dsa[i] = S[i] * s;
+          dsb[i] = (1.f - S[i]) * s;
+        }
+      }
+    }
+    float lo[4];
+    loo4(S, lo);
+    g.ga = g.gb = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      g.na[i] = dsa[i] * lo[i];
+      g.nb[i] = dsb[i] * lo[i];
+    }
+  } else {
+    const float W1 = B1 - A1;
+    float al[4], sl[4], R = W1;
+    int kind[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (!present[i]) {
+        kind[i] = 0; al[i] = kFar; sl[i] = 0.f;
+        continue;
+      }
+      al[i] = A[i] - A1;
+      R = fminf(R, Bv[i] - A1);
+      if (A[i] == Bv[i]) {
+        kind[i] = 2; sl[i] = 0.f;
+      } else {
+        kind[i] = 1; sl[i] = 1.f / (Bv[i] - A[i]);
+      }
+    }
+    uniform_grad_side(W1, R, al, sl, kind, g);
+  }
+  if (!want_max) {
+    out = g;
+    return;
+  }
+  // d/da = -d/db', d/db = -d/da'
+  out.ga = -g.gb;
+  out.gb = -g.ga;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    out.na[i] = -g.nb[i];
+    out.nb[i] = -g.na[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Epanechnikov, minimum, Gauss-Legendre on the sorted pieces
+
+struct EpanGrad {
+  float gm, gw;
+  float nm[4], nw[4];
+};
+
+__device__ __forceinline__ void epan_grad_vertex(float m1, float w1, const float *mn,
+                                                const float *wn, const bool *present,
+                                                bool want_max, EpanGrad &out) {
+  // maximum: work on -X (m -> -m, w unchanged); d/dm flips sign
+  const float M1 = want_max ? -m1 : m1;
+  float M[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) M[i] = want_max ? -mn[i] : mn[i];
+  EpanGrad g;
+  g.gm = g.gw = 0.f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) g.nm[i] = g.nw[i] = 0.f;
+  if (w1 == 0.f) {
+    const float c = M1;
+    float S[4], dm[4], dw[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      S[i] = 1.f; dm[i] = 0.f; dw[i] = 0.f;
+      if (!present[i]) continue;
+      if (wn[i] == 0.f) {
+        S[i] = M[i] > c ? 1.f : 0.f;
+      } else {
+        const float u = (c - M[i]) / wn[i];
+        S[i] = epan_surv(u);
+        if (u > -1.f && u < 1.f) {
+          const float pd = 0.75f / wn[i] * (1.f - u * u);
+          dm[i] = pd;
+          dw[i] = pd * u;
+        }
+      }
+    }
+    float lo[4];
+    loo4(S, lo);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      g.nm[i] = dm[i] * lo[i];
+      g.nw[i] = dw[i] * lo[i];
+    }
+  } else {
+    float al[4], d[4], iw[4], R = w1;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      al[i] = kFar; d[i] = kFar; iw[i] = 0.f;
+      if (!present[i]) continue;
+      const float dn = M[i] - M1;
+      if (wn[i] == 0.f) {
+        R = fminf(R, dn);
+      } else {
+        al[i] = dn - wn[i]; d[i] = dn; iw[i] = 1.f / wn[i];
+        R = fminf(R, dn + wn[i]);
+      }
+    }
+    const float L0 = -w1;
+    if (R > L0) {
+      float t[4];
+      float pay[3][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        t[i] = fminf(fmaxf(al[i], L0), R);
+        pay[0][i] = d[i];
+        pay[1][i] = iw[i];
+        pay[2][i] = (float)i;
+      }
+      sort4<3>(t, pay);
+      const float x[6] = {L0, t[0], t[1], t[2], t[3], R};
+      const float iw1 = 1.f / w1;
+      const float c1 = 0.75f * iw1;
+      const float cm = 1.5f * iw1 * iw1 * iw1;   // d pdf / dm1 = 1.5 x / w1^3
+      const float cw = -0.75f * iw1 * iw1;       // d pdf / dw1 = -0.75/w1^2 (1 - 3u^2)
+      float am[4] = {0, 0, 0, 0}, aw[4] = {0, 0, 0, 0};
+      float gm = 0.f, gw = 0.f;
+#pragma unroll
+      for (int j = 0; j <= 4; ++j) {
+        const float x0 = x[j], x1 = x[j + 1];
+        const float half = 0.5f * (x1 - x0), mid = 0.5f * (x0 + x1);
+        float pm = 0.f, pw = 0.f, qm[4] = {0, 0, 0, 0}, qw[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float xi = (q < 4) ? -kGLx[3 - q] : kGLx[q - 4];
+          const float wi = (q < 4) ? kGLw[3 - q] : kGLw[q - 4];
+          const float xx = fmaf(half, xi, mid);
+          const float u1 = xx * iw1;
+          const float p1 = c1 * fmaxf(fmaf(-u1, u1, 1.f), 0.f);
+          float G[4] = {1.f, 1.f, 1.f, 1.f}, pd[4] = {0, 0, 0, 0}, un[4] = {0, 0, 0, 0};
+#pragma unroll
+          for (int i = 0; i < j; ++i) {
+            const float u = fminf(fmaxf((xx - pay[0][i]) * pay[1][i], -1.f), 1.f);
+            G[i] = epan_surv(u);
+            pd[i] = 0.75f * pay[1][i] * (1.f - u * u);
+            un[i] = u;
+          }
+          float lo[4];
+          loo4(G, lo);
+          const float Hx = lo[0] * G[0];
+          pm = fmaf(wi, cm * xx * Hx, pm);
+          pw = fmaf(wi, cw * fmaf(-3.f * u1, u1, 1.f) * Hx, pw);
+#pragma unroll
+          for (int i = 0; i < j; ++i) {
+            const float e = wi * p1 * pd[i] * lo[i];
+            qm[i] += e;
+            qw[i] = fmaf(e, un[i], qw[i]);
+          }
+        }
+        gm = fmaf(pm, half, gm);
+        gw = fmaf(pw, half, gw);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          am[i] = fmaf(qm[i], half, am[i]);
+          aw[i] = fmaf(qw[i], half, aw[i]);
+        }
+      }
+      g.gm = gm;
+      g.gw = gw;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int o = (int)pay[2][i];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (q == o) {
+            g.nm[q] = am[i];
+            g.nw[q] = aw[i];
+          }
+      }
+    }
+  }
+  const float sgn = want_max ? -1.f : 1.f;
+  out.gm = sgn * g.gm;
+  out.gw = g.gw;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    out.nm[i] = sgn * g.nm[i];
+    out.nw[i] = g.nw[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// histogram, minimum (maximum through the negated histogram)
+
+// read access to one vertex's histogram, optionally negated (X -> -X:
+// support [-hi, -lo], bins reversed)
+struct HistView {
+  const float *p;
+  long long plane;
+  int B;
+  bool neg;
+  __device__ __forceinline__ float lo() const { return neg ? -p[plane] : p[0]; }
+  __device__ __forceinline__ float hi() const { return neg ? -p[0] : p[plane]; }
+  __device__ __forceinline__ float mass(int q) const {
+    return p[(long long)(2 + (neg ? B - 1 - q : q)) * plane];
+  }
+  __device__ __forceinline__ int orig(int q) const { return neg ? B - 1 - q : q; }
+};
+
+struct NWalk {
+  HistView v;
+  int B, j;            // j: -1 before, B after
+  float lam, h, end, eleft, enext, S, slope, T;
+  float C, Cstart, inbin;
+};
+
+__device__ __forceinline__ void nwalk_advance(NWalk &n, float *rows_n, long long plane,
+                                              long long vi, float wv) {
+  // leaving bin j (if inside the support): its partial is C(e_j) + within-bin
+  if (n.j >= 0 && n.j < n.B) rows_n[(long long)n.v.orig(n.j) * plane + vi] = wv * (n.Cstart + n.inbin);
+  ++n.j;
+  n.Cstart = n.C;
+  n.inbin = 0.f;
+  if (n.j >= n.B) {
+    n.j = n.B;
+    n.S = 0.f;
+    n.slope = 0.f;
+    n.eleft = n.enext;
+    n.enext = kFar;
+    return;
+  }
+  if (n.j > 0) n.S -= n.v.mass(n.j - 1);
+  n.slope = n.v.mass(n.j) / n.h;
+  n.eleft = n.enext;
+  n.enext = (n.j + 1 < n.B) ? fmaf((float)(n.j + 1), n.h, n.lam) : n.end;
+}
+
+__device__ __forceinline__ float nwalk_G(const NWalk &n, float x) {
+  return fmaxf(fmaf(-n.slope, x - n.eleft, n.S), 0.f);
+}
+
+__device__ void hist_grad_vertex(const float *params, long long plane, long long vi,
+                                 const long long *ni, const bool *present, int B, bool want_max,
+                                 float wv, float *rows) {
+  const HistView cv{params + vi, plane, B, want_max};
+  const float lo1 = cv.lo(), hi1 = cv.hi();
+  float T[4];
+  NWalk nw[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    T[i] = 1.f;
+    if (!present[i]) continue;
+    nw[i].v = HistView{params + ni[i], plane, B, want_max};
+    float t = 0.f;
+    for (int q = 0; q < B; ++q) t += nw[i].v.mass(q);
+    T[i] = t;
+  }
+  float *own = rows;  // slot 0
+  if (lo1 == hi1) {
+    // point-mass centre at c (total T1): P = T1 prod_n S_n(c)
+    const float c = lo1;
+    float S[4];
+    float T1 = 0.f;
+    for (int q = 0; q < B; ++q) T1 += cv.mass(q);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      S[i] = 1.f;
+      if (!present[i]) continue;
+      const HistView &v = nw[i].v;
+      const float lo = v.lo(), hi = v.hi();
+      if (lo == hi) {
+        S[i] = lo > c ? T[i] : 0.f;
+      } else if (c <= lo) {
+        S[i] = T[i];
+      } else if (c >= hi) {
+        S[i] = 0.f;
+      } else {
+        const float h = (hi - lo) / (float)B;
+        const int j = min(max((int)floorf((c - lo) / h), 0), B - 1);
+        float Cs = 0.f;
+        for (int q = 0; q < j; ++q) Cs += v.mass(q);
+        const float fr = fminf(fmaxf((c - lo - (float)j * h) / h, 0.f), 1.f);
+        S[i] = fmaxf(T[i] - Cs - fr * v.mass(j), 0.f);
+      }
+    }
+    float lo4[4];
+    loo4(S, lo4);
+    const float Pn = lo4[0] * S[0];
+    for (int q = 0; q < B; ++q) own[(long long)cv.orig(q) * plane + vi] = wv * Pn;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (!present[i]) continue;
+      float *rn = rows + (long long)(1 + i) * B * plane;
+      const HistView &v = nw[i].v;
+      const float lo = v.lo(), hi = v.hi();
+      const float h = (hi - lo) / (float)B;
+      for (int q = 0; q < B; ++q) {
+        float d;
+        if (lo == hi) {
+          d = c < lo ? 1.f : 0.f;
+        } else {
+          const float e0 = lo + (float)q * h, e1 = (q + 1 < B) ? lo + (float)(q + 1) * h : hi;
+          d = c < e0 ? 1.f : (c >= e1 ? 0.f : (e1 - c) / (e1 - e0));
+        }
+        rn[(long long)v.orig(q) * plane + vi] = wv * T1 * d * lo4[i];
+      }
+    }
+    return;
+  }
+  // walk over [0, W1] in the frame of lo1
+  const float W1 = hi1 - lo1;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if (!present[i]) continue;
+    NWalk &n = nw[i];
+    const float lo = n.v.lo(), hi = n.v.hi();
+    n.lam = lo - lo1;
+    n.B = (lo == hi) ? 0 : B;
+    n.h = (lo == hi) ? 1.f : (hi - lo) / (float)B;
+    n.end = (lo == hi) ? n.lam : hi - lo1;
+    n.j = -1;
+    n.S = T[i];
+    n.slope = 0.f;
+    n.eleft = -kFar;
+    n.enext = n.lam;
+    n.C = n.Cstart = n.inbin = 0.f;
+    n.T = T[i];
+    float *rn = rows + (long long)(1 + i) * B * plane;
+    if (n.B == 0) {
+      // point mass: every mass partial is int_{x < c} pdf_1 prod_{m!=n} G; filled at the end
+      continue;
+    }
+    for (int g = 0; g <= B && n.enext <= 0.f && n.j < n.B; ++g) nwalk_advance(n, rn, plane, vi, wv);
+  }
+  const float h1 = W1 / (float)B;
+  int j1 = 0;
+  float p1 = cv.mass(0) / h1;
+  float e1 = (B > 1) ? h1 : W1;
+  float own_acc = 0.f;
+  float x0 = 0.f;
+  float Gl[4];
+  float pmC[4] = {0, 0, 0, 0};  // point-mass neighbours: int up to their position
+#pragma unroll
+  for (int i = 0; i < 4; ++i) Gl[i] = present[i] ? nwalk_G(nw[i], 0.f) : 1.f;
+  const int max_steps = 5 * (B + 2) + 4;
+  for (int step = 0; step < max_steps; ++step) {
+    float x1 = e1;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (present[i]) x1 = fminf(x1, nw[i].enext);
+    x1 = fminf(x1, W1);
+    float Gr[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) Gr[i] = present[i] ? nwalk_G(nw[i], x1) : 1.f;
+    const float len = x1 - x0;
+    if (len > 0.f) {
+      own_acc += len * bern_mean<4>(Gl, Gr);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (!present[i]) continue;
+        float L3[4], R3[4];
+        int q = 0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+          if (m != i) {
+            L3[q] = Gl[m];
+            R3[q] = Gr[m];
+            ++q;
+          }
+        const float A = len * p1 * bern_mean<3>(L3, R3);
+        NWalk &n = nw[i];
+        n.C += A;
+        if (n.j >= 0 && n.j < n.B) {
+          // within-bin factor (e_{j+1} - x) / h
+          L3[3] = (n.enext - x0) / n.h;
+          R3[3] = (n.enext - x1) / n.h;
+          n.inbin += len * p1 * bern_mean<4>(L3, R3);
+        }
+      }
+    }
+    if (x1 >= W1) break;
+    if (e1 <= x1) {
+      own[(long long)cv.orig(j1) * plane + vi] = wv * own_acc / h1;
+      own_acc = 0.f;
+      ++j1;
+      p1 = (j1 < B) ? cv.mass(j1) / h1 : 0.f;
+      e1 = (j1 + 1 < B) ? (float)(j1 + 1) * h1 : W1;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (present[i] && nw[i].enext <= x1) {
+        NWalk &n = nw[i];
+        if (n.B == 0) pmC[i] = n.C;  // crossing a point mass
+        nwalk_advance(n, rows + (long long)(1 + i) * B * plane, plane, vi, wv);
+        Gr[i] = nwalk_G(n, x1);
+      }
+      Gl[i] = Gr[i];
+    }
+    x0 = x1;
+  }
+  if (j1 < B) own[(long long)cv.orig(j1) * plane + vi] = wv * own_acc / h1;
+  for (int q = j1 + 1; q < B; ++q) own[(long long)cv.orig(q) * plane + vi] = 0.f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if (!present[i]) continue;
+    NWalk &n = nw[i];
+    float *rn = rows + (long long)(1 + i) * B * plane;
+    if (n.B == 0) {
+      // point mass at lam: partial = int_{x < lam} ...; never crossed -> whole integral
+      const float v = (n.j < 0) ? (n.lam <= 0.f ? 0.f : n.C) : pmC[i];
+      for (int q = 0; q < B; ++q) rn[(long long)q * plane + vi] = wv * v;
+      continue;
+    }
+    if (n.j >= 0 && n.j < n.B) rn[(long long)n.v.orig(n.j) * plane + vi] = wv * (n.Cstart + n.inbin);
+    // bins entirely above the walk: the survival of the bin is 1 on [0, W1]
+    for (int q = (n.j < 0 ? 0 : n.j + 1); q < n.B; ++q)
+      rn[(long long)n.v.orig(q) * plane + vi] = wv * n.C;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pass 1: partial rows per centre
+
+template <int MODEL>
+__global__ void __launch_bounds__(128) partials_kernel(Field f, int want_max,
+                                                       const float *__restrict__ weight,
+                                                       float *__restrict__ rows) {
+  const long long plane = f.plane;
+  const int Q = (MODEL == kHist) ? f.B : 2;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < plane;
+       v += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(v / f.W), x = (int)(v % f.W);
+    bool present[4];
+    long long ni[4];
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int yy = y + kDy[i], xx = x + kDx[i];
+      present[i] = (yy >= 0 && yy < f.H && xx >= 0 && xx < f.W);
+      ni[i] = present[i] ? (long long)yy * f.W + xx : v;
+      k += present[i];
+    }
+    // validity of every participant
+    bool bad = false;
+    const int P = (MODEL == kHist) ? 2 + f.B : 2;
+    for (int t = 0; t < 5; ++t) {
+      if (t > 0 && !present[t - 1]) continue;
+      const long long u = t == 0 ? v : ni[t - 1];
+      const float a = f.params[u], b = f.params[plane + u];
+      if (!isfinite(a) || !isfinite(b)) bad = true;
+      else if (MODEL == kEpan ? (b < 0.f) : (a > b)) bad = true;
+      if (MODEL == kHist)
+        for (int q = 2; q < P; ++q) {
+          const float w = f.params[(long long)q * plane + u];
+          if (!(isfinite(w) && w >= 0.f)) bad = true;
+        }
+    }
+    const float wv = weight[v];
+    if (bad || (f.boundary == 1 && k < 4)) {
+      const float fill = bad ? qnan_b() : 0.f;
+      for (int s = 0; s < 5; ++s)
+        for (int q = 0; q < Q; ++q) rows[((long long)s * Q + q) * plane + v] = fill;
+      continue;
+    }
+    if (MODEL == kUniform) {
+      float an[4], bn[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        an[i] = f.params[ni[i]];
+        bn[i] = f.params[plane + ni[i]];
+      }
+      UniGrad g;
+      uniform_grad_vertex(f.params[v], f.params[plane + v], an, bn, present, want_max != 0, g);
+      rows[v] = wv * g.ga;
+      rows[plane + v] = wv * g.gb;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        rows[((long long)(1 + i) * 2) * plane + v] = wv * g.na[i];
+        rows[((long long)(1 + i) * 2 + 1) * plane + v] = wv * g.nb[i];
+      }
+    } else if (MODEL == kEpan) {
+      float mn[4], wn[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        mn[i] = f.params[ni[i]];
+        wn[i] = f.params[plane + ni[i]];
+      }
+      EpanGrad g;
+      epan_grad_vertex(f.params[v], f.params[plane + v], mn, wn, present, want_max != 0, g);
+      rows[v] = wv * g.gm;
+      rows[plane + v] = wv * g.gw;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        rows[((long long)(1 + i) * 2) * plane + v] = wv * g.nm[i];
+        rows[((long long)(1 + i) * 2 + 1) * plane + v] = wv * g.nw[i];
+      }
+    } else {
+      // absent neighbours: zero their rows (never gathered, kept defined)
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (!present[i])
+          for (int q = 0; q < Q; ++q) rows[((long long)(1 + i) * Q + q) * plane + v] = 0.f;
+      hist_grad_vertex(f.params, plane, v, ni, present, f.B, want_max != 0, wv, rows);
+    }
+  }
+}
+
+// pass 2: grad[q][u] = own row + the rows u's neighbours wrote about u
+__global__ void __launch_bounds__(256) gather_kernel(Field f, int Q, const float *__restrict__ rows,
+                                                     float *__restrict__ grad) {
+  const long long plane = f.plane;
+  const long long total = plane * Q;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(t / plane);
+    const long long u = t - (long long)q * plane;
+    const int y = (int)(u / f.W), x = (int)(u % f.W);
+    float s = rows[(long long)q * plane + u];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      const int yy = y + kDy[d], xx = x + kDx[d];
+      if (yy < 0 || yy >= f.H || xx < 0 || xx >= f.W) continue;
+      const int opp = (d + 2) & 3;  // u is the opposite-direction neighbour of v
+      s += rows[((long long)(1 + opp) * Q + q) * plane + (long long)yy * f.W + xx];
+    }
+    grad[t] = s;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_backward(const Field &f, int model, int cptype, const float *weight,
+                            float *rows, float *grad, cudaStream_t s) {
+  const int Q = model == kHist ? f.B : 2;
+  long long b = (f.plane + 127) / 128;
+  if (b > (1LL << 30)) b = 1LL << 30;
+  const int want_max = cptype == 2;
+  switch (model) {
+    case kUniform: partials_kernel<kUniform><<<(int)b, 128, 0, s>>>(f, want_max, weight, rows); break;
+    case kEpan: partials_kernel<kEpan><<<(int)b, 128, 0, s>>>(f, want_max, weight, rows); break;
+    case kHist: partials_kernel<kHist><<<(int)b, 128, 0, s>>>(f, want_max, weight, rows); break;
+    default: return cudaErrorInvalidValue;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  long long g = (f.plane * Q + 255) / 256;
+  if (g > (1LL << 30)) g = 1LL << 30;
+  gather_kernel<<<(int)g, 256, 0, s>>>(f, Q, rows, grad);
+  return cudaGetLastError();
+}
+
+}  // namespace ucp

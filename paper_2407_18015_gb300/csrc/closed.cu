@@ -1,0 +1,330 @@
+// closed.cu -- closed-form critical-point probability kernels (uniform,
+// Epanechnikov, histogram) and the statistics pass.
+//
+// Tile kernel: one CTA per 16 x 32 tile of vertices.  Phase 1 stages the
+// parameters of the tile and its one-vertex halo (18 x 34) in shared memory,
+// either fitted from the members (the statistics pass fused into the same
+// launch, so parameters never reach HBM) or loaded from a parameter array.
+// Phase 2 gives each thread two vertices; a vertex reads its own and its
+// four neighbours' parameters from shared memory (the neighbourhood access
+// of the paper's VTK-m worklet, Sec. "Integration with VTK-m and ParaView")
+// and integrates P_min / P_max exactly (device.cuh).
+#include "device.cuh"
+#include "launch.h"
+
+namespace ucp {
+
+// ---------------------------------------------------------------------------
+// statistics pass alone: params[P][H][W] + status
+
+template <int MODEL>
+__global__ void __launch_bounds__(256) fit_kernel(Field f) {
+  const long long plane = f.plane;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < plane;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float *p = f.ens + i;
+    float *out = const_cast<float *>(f.params);
+    uint8_t st = 0;
+    if (MODEL == kUniform) {
+      float mn, mx;
+      bool nf;
+      members_minmax(p, plane, f.N, mn, mx, nf);
+      if (nf) {
+        mn = mx = __int_as_float(0x7fc00000);
+        st |= V_NONFINITE;
+      } else if (mn == mx) {
+        st |= V_DEGENERATE;
+      }
+      out[i] = mn;
+      out[plane + i] = mx;
+    } else if (MODEL == kEpan) {
+      float m, w, mn, mx;
+      bool nf;
+      members_epan(p, plane, f.N, f.epan_scale, m, w, mn, mx, nf);
+      if (nf) {
+        m = w = __int_as_float(0x7fc00000);
+        st |= V_NONFINITE;
+      } else if (mn == mx) {
+        st |= V_DEGENERATE;
+      }
+      out[i] = m;
+      out[plane + i] = w;
+    } else {
+      float mn, mx;
+      bool nf;
+      members_minmax(p, plane, f.N, mn, mx, nf);
+      const int B = f.B;
+      if (nf) {
+        for (int q = 0; q < 2 + B; ++q) out[q * plane + i] = __int_as_float(0x7fc00000);
+        st |= V_NONFINITE;
+      } else {
+        int cnt[kMaxBins];
+        for (int q = 0; q < B; ++q) cnt[q] = 0;
+        if (mn == mx) {
+          cnt[0] = f.N;
+          st |= V_DEGENERATE;
+        } else {
+          const float s = __fdiv_rn((float)B, __fsub_rn(mx, mn));
+          for (int k = 0; k < f.N; ++k) cnt[hist_bin(__ldg(p + (long long)k * plane), mn, s, B)]++;
+        }
+        out[i] = mn;
+        out[plane + i] = mx;
+        for (int q = 0; q < B; ++q)
+          out[(2 + q) * plane + i] = __fdiv_rn((float)cnt[q], (float)f.N);
+      }
+    }
+    if (f.status) f.status[i] = st;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// tile kernel
+
+__device__ __forceinline__ float qnan() { return __int_as_float(0x7fc00000); }
+
+template <int MODEL, bool FROM_MEMBERS>
+__device__ __forceinline__ void stage_vertex(const Field &f, float *sm, int l, long long gi) {
+  const long long plane = f.plane;
+  if (!FROM_MEMBERS) {
+    const int P = (MODEL == kHist) ? 2 + f.B : 2;
+    for (int q = 0; q < P; ++q) sm[q * HALO + l] = __ldg(f.params + q * plane + gi);
+    return;
+  }
+  const float *p = f.ens + gi;
+  if (MODEL == kUniform) {
+    float mn, mx;
+    bool nf;
+    members_minmax(p, plane, f.N, mn, mx, nf);
+    sm[l] = nf ? qnan() : mn;
+    sm[HALO + l] = nf ? qnan() : mx;
+  } else if (MODEL == kEpan) {
+    float m, w, mn, mx;
+    bool nf;
+    members_epan(p, plane, f.N, f.epan_scale, m, w, mn, mx, nf);
+    sm[l] = nf ? qnan() : m;
+    sm[HALO + l] = nf ? qnan() : w;
+  } else {
+    float mn, mx;
+    bool nf;
+    members_minmax(p, plane, f.N, mn, mx, nf);
+    const int B = f.B;
+    float *wq = sm + 2 * HALO + l;
+    if (nf) {
+      sm[l] = sm[HALO + l] = qnan();
+      for (int q = 0; q < B; ++q) wq[q * HALO] = qnan();
+      return;
+    }
+    sm[l] = mn;
+    sm[HALO + l] = mx;
+    for (int q = 0; q < B; ++q) wq[q * HALO] = 0.f;
+    if (mn == mx) {
+      wq[0] = 1.f;
+      return;
+    }
+    const float s = __fdiv_rn((float)B, __fsub_rn(mx, mn));
+    for (int k = 0; k < f.N; ++k) {
+      const int j = hist_bin(__ldg(p + (long long)k * plane), mn, s, B);
+      wq[j * HALO] += 1.f;
+    }
+    for (int q = 0; q < B; ++q) wq[q * HALO] = __fdiv_rn(wq[q * HALO], (float)f.N);
+  }
+}
+
+// validity of one participant's parameters; returns status bits and the
+// histogram total mass
+template <int MODEL>
+__device__ __forceinline__ uint8_t check_params(const float *sm, int l, int B, float &T) {
+  const float a = sm[l], b = sm[HALO + l];
+  T = 1.f;
+  if (!isfinite(a) || !isfinite(b)) return V_NONFINITE;
+  if (MODEL == kUniform) return a > b ? V_BAD : (a == b ? V_DEGENERATE : 0);
+  if (MODEL == kEpan) return b < 0.f ? V_BAD : (b == 0.f ? V_DEGENERATE : 0);
+  uint8_t st = a > b ? V_BAD : (a == b ? V_DEGENERATE : 0);
+  float t = 0.f;
+  for (int q = 0; q < B; ++q) {
+    const float w = sm[(2 + q) * HALO + l];
+    if (!isfinite(w)) st |= V_NONFINITE;
+    else if (w < 0.f) st |= V_BAD;
+    t += w;
+  }
+  T = t;
+  return st;
+}
+
+template <int MODEL, bool FROM_MEMBERS>
+__global__ void __launch_bounds__(NTHREADS) tile_kernel(Field f, int tiles_x) {
+  extern __shared__ float sm[];
+  const int tile = blockIdx.x;
+  const int ty0 = f.y0 + (tile / tiles_x) * TY, tx0 = (tile % tiles_x) * TX;
+  // rows beyond y1 are neither computed nor needed (row y1 is a neighbour)
+  const int ylim = min(f.H, f.y1 + 1);
+
+  for (int l = threadIdx.x; l < HALO; l += NTHREADS) {
+    const int r = l / HX, c = l - r * HX;
+    const int gy = ty0 + r - 1, gx = tx0 + c - 1;
+    if (gy < 0 || gy >= ylim || gx < 0 || gx >= f.W) continue;
+    stage_vertex<MODEL, FROM_MEMBERS>(f, sm, l, (long long)gy * f.W + gx);
+  }
+  __syncthreads();
+
+  for (int v = threadIdx.x; v < TY * TX; v += NTHREADS) {
+    const int r = v / TX + 1, c = v % TX + 1;
+    const int gy = ty0 + r - 1, gx = tx0 + c - 1;
+    if (gy >= f.y1 || gx >= f.W) continue;
+    const int l = r * HX + c;
+    bool present[4];
+    int nl[4];
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int yy = gy + kDy[i], xx = gx + kDx[i];
+      present[i] = (yy >= 0 && yy < f.H && xx >= 0 && xx < f.W);
+      nl[i] = l + kDy[i] * HX + kDx[i];
+      k += present[i];
+    }
+    float T[4], Tc;
+    uint8_t st = check_params<MODEL>(sm, l, f.B, Tc);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      T[i] = 1.f;
+      if (present[i]) st |= check_params<MODEL>(sm, nl[i], f.B, T[i]) & (V_NONFINITE | V_BAD);
+    }
+    float pmin = 0.f, pmax = 0.f;
+    if (st & (V_NONFINITE | V_BAD)) {
+      pmin = pmax = qnan();
+    } else if (f.boundary == 1 && k < 4) {
+      pmin = pmax = 0.f;
+    } else if (MODEL == kUniform) {
+      UniParams cp{sm[l], sm[HALO + l]}, nb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) nb[i] = UniParams{sm[nl[i]], sm[HALO + nl[i]]};
+      uniform_vertex(cp, nb, present, f.cptypes, pmin, pmax);
+    } else if (MODEL == kEpan) {
+      EpanParams cp{sm[l], sm[HALO + l]}, nb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) nb[i] = EpanParams{sm[nl[i]], sm[HALO + nl[i]]};
+      epan_vertex(cp, nb, present, f.cptypes, pmin, pmax);
+    } else {
+      const int B = f.B;
+      const float lo1 = sm[l], hi1 = sm[HALO + l];
+      if (lo1 == hi1) {
+        float gm = Tc, gM = Tc;
+        for (int i = 0; i < 4; ++i) {
+          if (!present[i]) continue;
+          float gt, lt;
+          hist_tails_at(sm + 2 * HALO + nl[i], HALO, B, sm[nl[i]], sm[HALO + nl[i]], T[i], lo1,
+                        gt, lt);
+          gm *= gt;
+          gM *= lt;
+        }
+        pmin = gm;
+        pmax = gM;
+      } else {
+        HistWalk nw[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          HistWalk &h = nw[i];
+          h.w = sm + 2 * HALO + nl[i];
+          h.ws = HALO;
+          h.j = -1;
+          h.S = T[i];
+          h.slope = 0.f;
+          h.eleft = -kFar;
+          if (!present[i]) {
+            h.B = 0; h.lam = kFar; h.h = 1.f; h.end = kFar; h.enext = kFar;
+            continue;
+          }
+          const float lo = sm[nl[i]], hi = sm[HALO + nl[i]];
+          h.lam = lo - lo1;
+          if (lo == hi) {
+            h.B = 0; h.h = 1.f; h.end = h.lam;
+          } else {
+            h.B = B; h.h = (hi - lo) / (float)B; h.end = hi - lo1;
+          }
+          h.enext = h.lam;
+          for (int g = 0; g <= B && h.enext <= 0.f && h.j < h.B; ++g) h.advance();
+        }
+        hist_walk(sm + 2 * HALO + l, HALO, B, hi1 - lo1, nw, present, T, f.cptypes, pmin, pmax);
+      }
+    }
+    const long long gi = (long long)gy * f.W + gx;
+    if ((f.cptypes & kMin) && f.out_min) f.out_min[gi] = pmin;
+    if ((f.cptypes & kMax) && f.out_max) f.out_max[gi] = pmax;
+    if (f.status) f.status[gi] = st;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// uniform parameters from a decompressed field and an error bound
+
+__global__ void eb_params_kernel(const float *__restrict__ d, float eb, long long n,
+                                 float *__restrict__ params) {
+  const float h = 0.5f * eb;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float v = d[i];
+    params[i] = v - h;
+    params[n + i] = v + h;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+
+static int grid_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  if (b > (1LL << 30)) b = 1LL << 30;
+  return (int)(b < 1 ? 1 : b);
+}
+
+cudaError_t launch_fit(const Field &f, int model, cudaStream_t s) {
+  const int g = grid_for(f.plane, 256);
+  switch (model) {
+    case kUniform: fit_kernel<kUniform><<<g, 256, 0, s>>>(f); break;
+    case kEpan: fit_kernel<kEpan><<<g, 256, 0, s>>>(f); break;
+    case kHist: fit_kernel<kHist><<<g, 256, 0, s>>>(f); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <int MODEL, bool FM>
+static cudaError_t launch_tile(const Field &f, cudaStream_t s) {
+  const int P = (MODEL == kHist) ? 2 + f.B : 2;
+  const size_t smem = (size_t)P * HALO * sizeof(float);
+  static bool attr_set[128] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+  if (!attr_set[dev]) {
+    e = cudaFuncSetAttribute(tile_kernel<MODEL, FM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((2 + kMaxBins) * HALO * sizeof(float)));
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  const int tiles_x = (f.W + TX - 1) / TX, tiles_y = (f.y1 - f.y0 + TY - 1) / TY;
+  if (tiles_y <= 0) return cudaSuccess;
+  const long long tiles = (long long)tiles_x * tiles_y;
+  if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  tile_kernel<MODEL, FM><<<(int)tiles, NTHREADS, smem, s>>>(f, tiles_x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_closed(const Field &f, int model, bool from_members, cudaStream_t s) {
+  if (model == kUniform) return from_members ? launch_tile<kUniform, true>(f, s)
+                                             : launch_tile<kUniform, false>(f, s);
+  if (model == kEpan) return from_members ? launch_tile<kEpan, true>(f, s)
+                                          : launch_tile<kEpan, false>(f, s);
+  if (model == kHist) return from_members ? launch_tile<kHist, true>(f, s)
+                                          : launch_tile<kHist, false>(f, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_eb_params(const float *d, float eb, long long n, float *params,
+                             cudaStream_t s) {
+  eb_params_kernel<<<grid_for(n, 256), 256, 0, s>>>(d, eb, n, params);
+  return cudaGetLastError();
+}
+
+}  // namespace ucp

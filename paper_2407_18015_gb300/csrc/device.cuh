@@ -1,0 +1,547 @@
+// device.cuh -- per-vertex device routines of libucp (sm_103a).
+//
+// Critical-point probabilities of a vertex with value X_1 and in-grid axis
+// neighbours X_n (arXiv 2407.18015, Eq. localMinimumProb and the negation
+// rule for maxima):
+//   P_min = int pdf_1(x) prod_n G_n(x) dx,   P_max = int pdf_1(x) prod_n F_n(x) dx.
+// On every piece between consecutive support starts (Task 1 of the paper's
+// algorithm) each factor is one polynomial, so each piece integral is exact:
+//   - uniform / histogram: pdf_1 is constant and every G_n is linear on a
+//     piece, so the integral of the product is the Bernstein mean of its end
+//     values (no quadrature, all terms non-negative, no cancellation);
+//   - Epanechnikov: pdf_1 quadratic, G_n cubic, degree <= 14 on a piece,
+//     integrated exactly by 8-point Gauss-Legendre (exact to degree 15).
+// All arithmetic is FP32 in a vertex-local frame (the centre's lower support
+// end or mean is the origin), pieces are summed with Neumaier compensation.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace ucp {
+
+constexpr int kUniform = 0, kEpan = 1, kHist = 2, kMvn = 3;
+constexpr unsigned kMin = 1u, kMax = 2u;
+constexpr int kMaxBins = 64;
+
+enum : uint8_t {
+  V_DEGENERATE = 1,
+  V_NONFINITE = 2,
+  V_BAD = 4,
+  V_JITTER = 8,
+  V_CHOLFAIL = 16
+};
+
+// Neighbour directions e, n, w, s (same order as the MVN variable slots 1..4).
+__device__ __constant__ const int kDy[4] = {0, -1, 0, 1};
+__device__ __constant__ const int kDx[4] = {1, 0, -1, 0};
+
+constexpr float kFar = 3.0e38f;  // "never starts" breakpoint (finite: 0*kFar = 0)
+
+// ---------------------------------------------------------------------------
+// small helpers
+
+struct Neumaier {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    float t = s + x;
+    c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
+    s = t;
+  }
+  __device__ __forceinline__ float get() const { return s + c; }
+};
+
+__host__ __device__ constexpr int binom(int n, int k) {
+  int r = 1;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  return r;
+}
+
+// integral over [0,1] of (1-t)^(K-j) t^j = 1 / ((K+1) C(K,j))
+__host__ __device__ constexpr float bern_weight(int K, int j) { return 1.0f / float((K + 1) * binom(K, j)); }
+
+// integral over tau in [0,1] of prod_{i<K} (L[i] (1-tau) + R[i] tau):
+// the product in the Bernstein basis of degree K (coefficients e_j = sums of
+// products of j right values and K-j left values), then its exact mean.
+template <int K>
+__device__ __forceinline__ float bern_mean(const float *L, const float *R) {
+  if constexpr (K == 0) {
+    return 1.0f;
+  } else {
+    float e[K + 1];
+    e[0] = L[0];
+    e[1] = R[0];
+#pragma unroll
+    for (int i = 1; i < K; ++i) {
+      e[i + 1] = e[i] * R[i];
+#pragma unroll
+      for (int j = i; j >= 1; --j) e[j] = fmaf(e[j - 1], R[i], e[j] * L[i]);
+      e[0] = e[0] * L[i];
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j <= K; ++j) s = fmaf(e[j], bern_weight(K, j), s);
+    return s;
+  }
+}
+
+// Sort four (key, payload...) tuples ascending by key with a 5-exchange network.
+template <int NP>
+__device__ __forceinline__ void cswap(float *k, float (*p)[4], int a, int b) {
+  bool sw = k[b] < k[a];
+  float ka = k[a], kb = k[b];
+  k[a] = sw ? kb : ka;
+  k[b] = sw ? ka : kb;
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    float pa = p[q][a], pb = p[q][b];
+    p[q][a] = sw ? pb : pa;
+    p[q][b] = sw ? pa : pb;
+  }
+}
+template <int NP>
+__device__ __forceinline__ void sort4(float *k, float (*p)[4]) {
+  cswap<NP>(k, p, 0, 1);
+  cswap<NP>(k, p, 2, 3);
+  cswap<NP>(k, p, 0, 2);
+  cswap<NP>(k, p, 1, 3);
+  cswap<NP>(k, p, 1, 2);
+}
+
+// ---------------------------------------------------------------------------
+// fitting (the statistics pass)
+
+// min / max over N members at stride `plane`; nonfinite set if any is NaN/Inf
+__device__ __forceinline__ void members_minmax(const float *__restrict__ p, long long plane,
+                                               int N, float &mn, float &mx, bool &nonfinite) {
+  float a = p[0], b = p[0];
+  bool nf = false;
+  int k = 0;
+  for (; k + 4 <= N; k += 4) {
+    float v0 = __ldg(p + (long long)k * plane), v1 = __ldg(p + (long long)(k + 1) * plane);
+    float v2 = __ldg(p + (long long)(k + 2) * plane), v3 = __ldg(p + (long long)(k + 3) * plane);
+    nf |= !(isfinite(v0) && isfinite(v1) && isfinite(v2) && isfinite(v3));
+    a = fminf(fminf(a, v0), fminf(v1, fminf(v2, v3)));
+    b = fmaxf(fmaxf(b, v0), fmaxf(v1, fmaxf(v2, v3)));
+  }
+  for (; k < N; ++k) {
+    float v = __ldg(p + (long long)k * plane);
+    nf |= !isfinite(v);
+    a = fminf(a, v);
+    b = fmaxf(b, v);
+  }
+  mn = a;
+  mx = b;
+  nonfinite = nf;
+}
+
+// Epanechnikov fit: one pass, shifted by the first member, compensated sums
+// of d = x - x_0 and d^2; m = x_0 + mean(d), var = (S2 - S1^2/N) / (N-1).
+__device__ __forceinline__ void members_epan(const float *__restrict__ p, long long plane, int N,
+                                             float scale, float &m, float &w, float &mn,
+                                             float &mx, bool &nonfinite) {
+  const float x0 = __ldg(p);
+  Neumaier s1, s2;
+  float a = x0, b = x0;
+  bool nf = false;
+  for (int k = 0; k < N; ++k) {
+    float v = __ldg(p + (long long)k * plane);
+    nf |= !isfinite(v);
+    a = fminf(a, v);
+    b = fmaxf(b, v);
+    float d = v - x0;
+    s1.add(d);
+    s2.add(d * d);
+  }
+  mn = a;
+  mx = b;
+  nonfinite = nf;
+  if (a == b) {
+    m = a;
+    w = 0.f;
+    return;
+  }
+  float S1 = s1.get(), S2 = s2.get();
+  float md = S1 / (float)N;
+  float var = fmaxf(S2 - S1 * md, 0.f) / (float)(N - 1);
+  m = x0 + md;
+  w = scale * sqrtf(var);
+}
+
+// histogram bin of x: floor((x - lo) * s), s = B / (hi - lo), one rounding per
+// operation (no contraction), clamped to [0, B-1]
+__device__ __forceinline__ int hist_bin(float x, float lo, float s, int B) {
+  int i = (int)floorf(__fmul_rn(__fsub_rn(x, lo), s));
+  return min(max(i, 0), B - 1);
+}
+
+// ---------------------------------------------------------------------------
+// closed-form integration, uniform model
+
+// One-sided problem in a local frame: the centre is uniform on [0, W1]
+// (W1 > 0), factor i is 1 - max(0, x - al[i]) * sl[i] (a neighbour survival
+// that starts at al[i]; sl = 0 for absent or point-mass neighbours), the
+// integration range is [0, R].  Returns int_0^R (1/W1) prod_i factor_i dx.
+__device__ __forceinline__ float uniform_side(float W1, float R, float al[4], float sl[4]) {
+  if (!(R > 0.f)) return 0.f;
+  float t[4];
+  float pay[2][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    t[i] = fminf(fmaxf(al[i], 0.f), R);
+    pay[0][i] = al[i];
+    pay[1][i] = sl[i];
+  }
+  sort4<2>(t, pay);
+  // breakpoints x_0 = 0 < t0 <= t1 <= t2 <= t3 <= x_5 = R; on piece j the
+  // factors 0..j-1 (sorted) have started and the others are 1.
+  float x[6] = {0.f, t[0], t[1], t[2], t[3], R};
+  Neumaier acc;
+  acc.add(x[1]);  // piece 0: no factor has started
+  float L[4], Rv[4];
+#pragma unroll
+  for (int j = 1; j <= 4; ++j) {
+    const float x0 = x[j], x1 = x[j + 1];
+#pragma unroll
+    for (int i = 0; i < j; ++i) {
+      L[i] = fmaxf(fmaf(-(x0 - pay[0][i]), pay[1][i], 1.f), 0.f);
+      Rv[i] = fmaxf(fmaf(-(x1 - pay[0][i]), pay[1][i], 1.f), 0.f);
+    }
+    float I;
+    if (j == 1) I = bern_mean<1>(L, Rv);
+    else if (j == 2) I = bern_mean<2>(L, Rv);
+    else if (j == 3) I = bern_mean<3>(L, Rv);
+    else I = bern_mean<4>(L, Rv);
+    acc.add((x1 - x0) * I);
+  }
+  return acc.get() / W1;
+}
+
+struct UniParams {
+  float a, b;
+};
+
+// P_min and P_max of a centre (a1,b1) with neighbours nb[0..3] (present[i]).
+// Degenerate centre: products of strict tail probabilities.
+__device__ __forceinline__ void uniform_vertex(UniParams c, const UniParams *nb,
+                                               const bool *present, unsigned want, float &pmin,
+                                               float &pmax) {
+  if (c.a == c.b) {
+    const float v = c.a;
+    float gm = 1.f, gM = 1.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (!present[i]) continue;
+      float a = nb[i].a, b = nb[i].b;
+      float gt, lt;
+      if (a == b) {
+        gt = a > v ? 1.f : 0.f;
+        lt = a < v ? 1.f : 0.f;
+      } else {
+        float r = 1.f / (b - a);
+        gt = fminf(fmaxf((b - v) * r, 0.f), 1.f);
+        lt = fminf(fmaxf((v - a) * r, 0.f), 1.f);
+      }
+      gm *= gt;
+      gM *= lt;
+    }
+    pmin = gm;
+    pmax = gM;
+    return;
+  }
+  const float W1 = c.b - c.a;
+  if (want & kMin) {
+    float al[4], sl[4], R = W1;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (present[i]) {
+        const float a = nb[i].a, b = nb[i].b;
+        al[i] = a - c.a;
+        sl[i] = (a == b) ? 0.f : 1.f / (b - a);
+        R = fminf(R, b - c.a);
+      } else {
+        al[i] = kFar;
+        sl[i] = 0.f;
+      }
+    }
+    pmin = uniform_side(W1, R, al, sl);
+  }
+  if (want & kMax) {
+    // negated variables: -X has support [-b, -a]; origin at -b1
+    float al[4], sl[4], R = W1;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (present[i]) {
+        const float a = nb[i].a, b = nb[i].b;
+        al[i] = c.b - b;
+        sl[i] = (a == b) ? 0.f : 1.f / (b - a);
+        R = fminf(R, c.b - a);
+      } else {
+        al[i] = kFar;
+        sl[i] = 0.f;
+      }
+    }
+    pmax = uniform_side(W1, R, al, sl);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// closed-form integration, Epanechnikov model
+
+// 8-point Gauss-Legendre rule on [-1, 1] (roots of P_8, weights
+// 2 / ((1 - x^2) P_8'(x)^2)); exact for polynomials of degree <= 15.
+__device__ __constant__ const float kGLx[4] = {0.18343464249564978f, 0.525532409916329f,
+                                               0.7966664774136267f, 0.9602898564975362f};
+__device__ __constant__ const float kGLw[4] = {0.36268378337836166f, 0.3137066458778869f,
+                                               0.22238103445337443f, 0.10122853629037706f};
+
+// survival of the standard Epanechnikov kernel on [-1,1]: (1-u)^2 (2+u) / 4
+__device__ __forceinline__ float epan_surv(float u) {
+  u = fminf(fmaxf(u, -1.f), 1.f);
+  const float q = 1.f - u;
+  return 0.25f * q * q * (2.f + u);
+}
+
+// One-sided problem in the centre's frame (origin m1): centre pdf
+// 3/(4 w1) (1 - (x/w1)^2) on [-w1, w1], factor i = epan_surv((x - d[i]) * iw[i])
+// starting at al[i] = d[i] - 1/iw[i] (iw = 0, d = kFar for absent/point-mass
+// neighbours).  Integrates over [L, R].
+__device__ __forceinline__ float epan_side(float w1, float L, float R, float al[4], float d[4],
+                                           float iw[4]) {
+  if (!(R > L)) return 0.f;
+  float t[4];
+  float pay[2][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    t[i] = fminf(fmaxf(al[i], L), R);
+    pay[0][i] = d[i];
+    pay[1][i] = iw[i];
+  }
+  sort4<2>(t, pay);
+  const float x[6] = {L, t[0], t[1], t[2], t[3], R};
+  const float iw1 = 1.f / w1;
+  const float c1 = 0.75f * iw1;
+  Neumaier acc;
+#pragma unroll
+  for (int j = 0; j <= 4; ++j) {
+    const float x0 = x[j], x1 = x[j + 1];
+    const float half = 0.5f * (x1 - x0), mid = 0.5f * (x0 + x1);
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float xi = (q < 4) ? -kGLx[3 - q] : kGLx[q - 4];
+      const float wi = (q < 4) ? kGLw[3 - q] : kGLw[q - 4];
+      const float xx = fmaf(half, xi, mid);
+      const float u1 = xx * iw1;
+      float f = c1 * fmaxf(fmaf(-u1, u1, 1.f), 0.f);
+#pragma unroll
+      for (int i = 0; i < j; ++i) f *= epan_surv((xx - pay[0][i]) * pay[1][i]);
+      s = fmaf(wi, f, s);
+    }
+    acc.add(s * half);
+  }
+  return acc.get();
+}
+
+struct EpanParams {
+  float m, w;
+};
+
+__device__ __forceinline__ void epan_vertex(EpanParams c, const EpanParams *nb,
+                                            const bool *present, unsigned want, float &pmin,
+                                            float &pmax) {
+  if (c.w == 0.f) {
+    const float v = c.m;
+    float gm = 1.f, gM = 1.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (!present[i]) continue;
+      float gt, lt;
+      if (nb[i].w == 0.f) {
+        gt = nb[i].m > v ? 1.f : 0.f;
+        lt = nb[i].m < v ? 1.f : 0.f;
+      } else {
+        gt = epan_surv((v - nb[i].m) / nb[i].w);
+        lt = epan_surv((nb[i].m - v) / nb[i].w);
+      }
+      gm *= gt;
+      gM *= lt;
+    }
+    pmin = gm;
+    pmax = gM;
+    return;
+  }
+  const float w1 = c.w;
+  if (want & kMin) {
+    float al[4], d[4], iw[4], R = w1;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (present[i]) {
+        const float dn = nb[i].m - c.m, wn = nb[i].w;
+        if (wn == 0.f) {  // point mass: survival 1 below it, and it caps R
+          al[i] = kFar; d[i] = kFar; iw[i] = 0.f;
+          R = fminf(R, dn);
+        } else {
+          al[i] = dn - wn; d[i] = dn; iw[i] = 1.f / wn;
+          R = fminf(R, dn + wn);
+        }
+      } else {
+        al[i] = kFar; d[i] = kFar; iw[i] = 0.f;
+      }
+    }
+    pmin = epan_side(w1, -w1, R, al, d, iw);
+  }
+  if (want & kMax) {
+    // negated variables: -X_n has mean -m_n; in the frame of -m1: d = m1 - m_n
+    float al[4], d[4], iw[4], R = w1;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (present[i]) {
+        const float dn = c.m - nb[i].m, wn = nb[i].w;
+        if (wn == 0.f) {
+          al[i] = kFar; d[i] = kFar; iw[i] = 0.f;
+          R = fminf(R, dn);
+        } else {
+          al[i] = dn - wn; d[i] = dn; iw[i] = 1.f / wn;
+          R = fminf(R, dn + wn);
+        }
+      } else {
+        al[i] = kFar; d[i] = kFar; iw[i] = 0.f;
+      }
+    }
+    pmax = epan_side(w1, -w1, R, al, d, iw);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// closed-form integration, histogram model (breakpoint merge)
+
+// A neighbour's survival G(x) (mixture form) as a walk over its segments:
+// before the support G = T; on bin j G = S_j - w_j (x - e_j) / h; after it 0.
+// A point mass is a histogram without bins (one jump from T to 0).
+struct HistWalk {
+  const float *w;   // masses in shared memory, stride `ws`
+  int ws;
+  int B, j;         // j: -1 before the support, B after it
+  float lam, h, end;  // local support start, bin width, local support end
+  float eleft, enext, S, slope;
+  __device__ __forceinline__ float mass(int q) const { return w[q * ws]; }
+  __device__ __forceinline__ void advance() {
+    ++j;
+    if (j >= B) {
+      j = B;
+      S = 0.f;
+      slope = 0.f;
+      eleft = enext;
+      enext = kFar;
+      return;
+    }
+    if (j > 0) S -= mass(j - 1);
+    const float wj = mass(j);
+    slope = wj / h;
+    eleft = enext;
+    enext = (j + 1 < B) ? fmaf((float)(j + 1), h, lam) : end;
+  }
+  __device__ __forceinline__ float G(float x) const {
+    return fmaxf(fmaf(-slope, x - eleft, S), 0.f);
+  }
+};
+
+// Both probabilities of a non-degenerate histogram centre in one walk over
+// [0, W1] (local frame at lo1): all bin edges of the centre and of the
+// neighbours are merged in increasing order; on each piece the centre pdf is
+// the constant w_j / h1 and each factor is linear, so the piece integral is
+// the Bernstein mean of the factor end values.  Beyond a neighbour's support
+// its survival is 0, before it its CDF is 0, so both integrals can run over
+// the centre's whole support.
+__device__ __forceinline__ void hist_walk(const float *cw, int cws, int B, float W1,
+                                          HistWalk *nw, const bool *present, const float *T,
+                                          unsigned want, float &pmin, float &pmax) {
+  const float h1 = W1 / (float)B;
+  int j1 = 0;
+  float p1 = cw[0] / h1;
+  float e1 = (B > 1) ? h1 : W1;
+  float x0 = 0.f;
+  float Gl[4], Fl[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if (present[i]) {
+      Gl[i] = nw[i].G(0.f);
+      Fl[i] = fmaxf(T[i] - Gl[i], 0.f);
+    } else {
+      Gl[i] = 1.f;
+      Fl[i] = 1.f;
+    }
+  }
+  Neumaier amin, amax;
+  const int max_steps = 5 * (B + 2) + 4;
+  for (int step = 0; step < max_steps; ++step) {
+    float x1 = e1;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (present[i]) x1 = fminf(x1, nw[i].enext);
+    x1 = fminf(x1, W1);
+    float Gr[4], Fr[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (present[i]) {
+        Gr[i] = nw[i].G(x1);
+        Fr[i] = fmaxf(T[i] - Gr[i], 0.f);
+      } else {
+        Gr[i] = 1.f;
+        Fr[i] = 1.f;
+      }
+    }
+    const float len = (x1 - x0) * p1;
+    if (want & kMin) amin.add(len * bern_mean<4>(Gl, Gr));
+    if (want & kMax) amax.add(len * bern_mean<4>(Fl, Fr));
+    if (x1 >= W1) break;
+    if (e1 <= x1) {
+      ++j1;
+      p1 = (j1 < B) ? cw[j1 * cws] / h1 : 0.f;
+      e1 = (j1 + 1 < B) ? (float)(j1 + 1) * h1 : W1;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (present[i] && nw[i].enext <= x1) {
+        nw[i].advance();
+        Gr[i] = nw[i].G(x1);
+        Fr[i] = fmaxf(T[i] - Gr[i], 0.f);
+      }
+      Gl[i] = Gr[i];
+      Fl[i] = Fr[i];
+    }
+    x0 = x1;
+  }
+  pmin = amin.get();
+  pmax = amax.get();
+}
+
+// survival and CDF of a histogram neighbour at a point v (degenerate centre)
+__device__ __forceinline__ void hist_tails_at(const float *w, int ws, int B, float lo, float hi,
+                                              float T, float v, float &gt, float &lt) {
+  if (lo == hi) {
+    gt = lo > v ? T : 0.f;
+    lt = lo < v ? T : 0.f;
+    return;
+  }
+  if (v <= lo) {
+    gt = T; lt = 0.f;
+    return;
+  }
+  if (v >= hi) {
+    gt = 0.f; lt = T;
+    return;
+  }
+  const float h = (hi - lo) / (float)B;
+  int j = min(max((int)floorf((v - lo) / h), 0), B - 1);
+  float C = 0.f;
+  for (int q = 0; q < j; ++q) C += w[q * ws];
+  const float wj = w[j * ws];
+  const float part = fminf(fmaxf((v - lo - (float)j * h) / h, 0.f), 1.f) * wj;
+  lt = C + part;
+  gt = fmaxf(T - lt, 0.f);
+}
+
+}  // namespace ucp

@@ -1,0 +1,44 @@
+// launch.h -- internal launch interface between the C ABI (api.cu) and the
+// kernel translation units.  Host and device visible; no torch types.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ucp {
+
+// One field of work for the closed-form and Monte Carlo kernels.
+struct Field {
+  const float *ens;     // [N][H][W] members, or nullptr
+  const float *params;  // [P][H][W] parameters, or nullptr
+  float *out_min;       // [H][W] or nullptr
+  float *out_max;       // [H][W] or nullptr
+  uint8_t *status;      // [H][W] or nullptr
+  long long plane;      // H * W
+  int N, H, W, B;
+  int y0, y1;           // rows [y0, y1) are computed (the arrays cover all H rows)
+  int boundary;         // 0 in-grid neighbours, 1 zero at the boundary
+  float epan_scale;
+  unsigned cptypes;     // bit 1 min, bit 2 max
+};
+
+// Tile of the closed-form kernels: TY x TX vertices plus a one-vertex halo.
+constexpr int TY = 16, TX = 32, HY = TY + 2, HX = TX + 2, HALO = HY * HX, NTHREADS = 256;
+
+inline int param_planes(int model, int B) { return model == 2 ? 2 + B : (model == 3 ? 20 : 2); }
+
+cudaError_t launch_fit(const Field &f, int model, cudaStream_t s);
+cudaError_t launch_closed(const Field &f, int model, bool from_members, cudaStream_t s);
+cudaError_t launch_eb_params(const float *d, float eb, long long n, float *params,
+                             cudaStream_t s);
+
+// Monte Carlo for the multivariate Gaussian model.
+cudaError_t launch_mvn_fit(const Field &f, cudaStream_t s);
+cudaError_t launch_mvn_mc(const Field &f, bool from_members, int samples, uint64_t seed,
+                          uint32_t field_id, cudaStream_t s);
+
+// Adjoint: partial rows into `rows` ([5][Q][H][W]) then the gather into grad.
+cudaError_t launch_backward(const Field &f, int model, int cptype, const float *weight,
+                            float *rows, float *grad, cudaStream_t s);
+
+}  // namespace ucp

@@ -1,0 +1,32 @@
+// ucp_internal.h -- host-side internals shared by the C ABI translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "ucp.h"
+
+constexpr int kMaxBinsHost = 64;
+
+struct ucp_ctx {
+  int device = 0;
+  int sm_count = 0;
+  char last_error[256] = {0};
+  // backward partial rows and other scratch (grown on demand)
+  void *work = nullptr;
+  size_t work_bytes = 0;
+  // device copies for the host-buffer entry point
+  float *host_ens = nullptr;
+  size_t host_ens_bytes = 0;
+  void *host_out = nullptr;
+  size_t host_out_bytes = 0;
+  cudaStream_t pipe[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t pipe_ev[2][64] = {};
+  bool pipe_ready = false;
+};
+
+int ucp_set_error(ucp_ctx *ctx, cudaError_t e);
+int ucp_ensure_work(ucp_ctx *ctx, size_t bytes);
+int ucp_host_pipeline(ucp_ctx *ctx, const float *ens_host, int N, int H, int W,
+                      const ucp_model_desc *desc, unsigned cptypes, float *out_min_host,
+                      float *out_max_host, uint8_t *status_host, cudaStream_t stream);

@@ -1,0 +1,356 @@
+"""Python binding of libucp (include/ucp.h): argument marshalling only.
+
+Every function named ``ucp_*`` here calls the C entry point of the same name
+with the device pointers of torch tensors and the current CUDA stream; all
+computation happens in the library's kernels.  There is no CPU fallback: if
+libucp.so is missing or a call fails, an exception is raised.
+
+Convenience wrappers (``Context``, ``probability``, ``UcpProbability``)
+allocate outputs with torch and call the same entry points.
+"""
+import ctypes
+import os
+import threading
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libucp.so")
+
+UCP_UNIFORM, UCP_EPANECHNIKOV, UCP_HISTOGRAM, UCP_MVN_MC = 0, 1, 2, 3
+UCP_MIN, UCP_MAX = 1, 2
+UCP_BOUNDARY_INGRID, UCP_BOUNDARY_ZERO = 0, 1
+UCP_OK, UCP_ERR_ARG, UCP_ERR_SHAPE, UCP_ERR_CUDA, UCP_ERR_NOMEM, UCP_ERR_TIMEOUT, \
+    UCP_ERR_UNSUPPORTED = range(7)
+UCP_V_DEGENERATE, UCP_V_NONFINITE, UCP_V_BAD_PARAMS, UCP_V_CHOL_JITTER, UCP_V_CHOL_FAIL = \
+    1, 2, 4, 8, 16
+
+MODELS = {"uniform": UCP_UNIFORM, "epanechnikov": UCP_EPANECHNIKOV,
+          "histogram": UCP_HISTOGRAM, "mvn": UCP_MVN_MC}
+
+
+class ucp_model_desc(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int), ("bins", ctypes.c_int),
+                ("epan_width_scale", ctypes.c_float), ("mc_samples", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("field_id", ctypes.c_uint32),
+                ("boundary", ctypes.c_int)]
+
+
+class UcpError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        msg = f"{where}: {status_string(status)}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+
+
+_lock = threading.Lock()
+_lib = None
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+
+
+def lib():
+    """The loaded libucp.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"libucp.so not built ({LIB_PATH}); run "
+                                  "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = ctypes.CDLL(LIB_PATH)
+            D = ctypes.POINTER(ucp_model_desc)
+            sig = {
+                "ucp_status_string": ([_I], ctypes.c_char_p),
+                "ucp_version": ([], ctypes.c_char_p),
+                "ucp_param_count": ([D], _I),
+                "ucp_create": ([ctypes.POINTER(_P), _I], _I),
+                "ucp_destroy": ([_P], _I),
+                "ucp_last_error": ([_P], ctypes.c_char_p),
+                "ucp_fit": ([_P, _P, _I, _I, _I, D, _P, _P, _P], _I),
+                "ucp_probability_from_params": ([_P, _P, _I, _I, D, ctypes.c_uint, _P, _P, _P,
+                                                 _P], _I),
+                "ucp_probability": ([_P, _P, _I, _I, _I, D, ctypes.c_uint, _P, _P, _P, _P], _I),
+                "ucp_probability_host": ([_P, _P, _I, _I, _I, D, ctypes.c_uint, _P, _P, _P, _P],
+                                         _I),
+                "ucp_params_from_error_bound": ([_P, _P, ctypes.c_float, _I, _I, _P, _P], _I),
+                "ucp_backward": ([_P, _P, _I, _I, D, _I, _P, _P, _P], _I),
+                "ucp_batch_create": ([_P, ctypes.POINTER(_P)], _I),
+                "ucp_batch_add": ([_P, _P, _I, _I, _I, D, ctypes.c_uint, _P, _P], _I),
+                "ucp_batch_tune": ([_P, _P], _I),
+                "ucp_batch_run": ([_P, _P], _I),
+                "ucp_batch_destroy": ([_P], _I),
+            }
+            for name, (args, res) in sig.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def status_string(status):
+    return lib().ucp_status_string(int(status)).decode()
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+
+
+def _ptr(t, dtype=None, device=None, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def _hptr(a, name="array"):
+    """Host pointer of a CPU tensor (pinned or pageable) or numpy array."""
+    if a is None:
+        return None
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or not a.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CPU tensor")
+        return a.data_ptr()
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError(f"{name} must be C-contiguous")
+    return a.ctypes.data
+
+
+def _stream(stream=None, device=None):
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    return s.cuda_stream
+
+
+def make_desc(model="uniform", bins=8, epan_width_scale=0.0, mc_samples=10000, seed=0x5EED,
+              field_id=0, boundary=UCP_BOUNDARY_INGRID):
+    m = MODELS[model] if isinstance(model, str) else int(model)
+    return ucp_model_desc(m, int(bins), float(epan_width_scale), int(mc_samples),
+                          int(seed) & 0xFFFFFFFFFFFFFFFF, int(field_id) & 0xFFFFFFFF,
+                          int(boundary))
+
+
+def _check(rc, where, ctx=None):
+    if rc != UCP_OK:
+        detail = ""
+        if ctx is not None and rc in (UCP_ERR_CUDA, UCP_ERR_NOMEM):
+            detail = lib().ucp_last_error(ctx).decode()
+        raise UcpError(rc, where, detail)
+
+
+# ---------------------------------------------------------------------------
+# same-name entry points (tensor arguments)
+
+
+def ucp_create(device=0):
+    h = _P()
+    _check(lib().ucp_create(ctypes.byref(h), int(device)), "ucp_create")
+    return h
+
+
+def ucp_destroy(ctx):
+    _check(lib().ucp_destroy(ctx), "ucp_destroy")
+
+
+def ucp_param_count(desc):
+    return lib().ucp_param_count(ctypes.byref(desc))
+
+
+def ucp_fit(ctx, ens, desc, params, vertex_status=None, stream=None):
+    N, H, W = ens.shape
+    rc = lib().ucp_fit(ctx, _ptr(ens, torch.float32, name="ens"), N, H, W, ctypes.byref(desc),
+                       _ptr(params, torch.float32, name="params"),
+                       _ptr(vertex_status, torch.uint8, name="vertex_status"),
+                       _stream(stream, ens.device))
+    _check(rc, "ucp_fit", ctx)
+
+
+def ucp_probability_from_params(ctx, params, desc, cptypes, out_min, out_max,
+                                vertex_status=None, stream=None):
+    _, H, W = params.shape
+    rc = lib().ucp_probability_from_params(
+        ctx, _ptr(params, torch.float32, name="params"), H, W, ctypes.byref(desc), int(cptypes),
+        _ptr(out_min, torch.float32, name="out_min"), _ptr(out_max, torch.float32, name="out_max"),
+        _ptr(vertex_status, torch.uint8, name="vertex_status"), _stream(stream, params.device))
+    _check(rc, "ucp_probability_from_params", ctx)
+
+
+def ucp_probability(ctx, ens, desc, cptypes, out_min, out_max, vertex_status=None,
+                    stream=None):
+    N, H, W = ens.shape
+    rc = lib().ucp_probability(
+        ctx, _ptr(ens, torch.float32, name="ens"), N, H, W, ctypes.byref(desc), int(cptypes),
+        _ptr(out_min, torch.float32, name="out_min"), _ptr(out_max, torch.float32, name="out_max"),
+        _ptr(vertex_status, torch.uint8, name="vertex_status"), _stream(stream, ens.device))
+    _check(rc, "ucp_probability", ctx)
+
+
+def ucp_probability_host(ctx, ens_host, desc, cptypes, out_min_host, out_max_host,
+                         status_host=None, stream=None):
+    N, H, W = ens_host.shape
+    rc = lib().ucp_probability_host(
+        ctx, _hptr(ens_host, "ens_host"), N, H, W, ctypes.byref(desc), int(cptypes),
+        _hptr(out_min_host, "out_min_host"), _hptr(out_max_host, "out_max_host"),
+        _hptr(status_host, "status_host"), _stream(stream))
+    _check(rc, "ucp_probability_host", ctx)
+
+
+def ucp_params_from_error_bound(ctx, decompressed, eb, params, stream=None):
+    H, W = decompressed.shape
+    rc = lib().ucp_params_from_error_bound(
+        ctx, _ptr(decompressed, torch.float32, name="decompressed"), float(eb), H, W,
+        _ptr(params, torch.float32, name="params"), _stream(stream, decompressed.device))
+    _check(rc, "ucp_params_from_error_bound", ctx)
+
+
+def ucp_backward(ctx, params, desc, cptype, weight, grad_params, stream=None):
+    _, H, W = params.shape
+    rc = lib().ucp_backward(ctx, _ptr(params, torch.float32, name="params"), H, W,
+                            ctypes.byref(desc), int(cptype),
+                            _ptr(weight, torch.float32, name="weight"),
+                            _ptr(grad_params, torch.float32, name="grad_params"),
+                            _stream(stream, params.device))
+    _check(rc, "ucp_backward", ctx)
+
+
+def ucp_batch_create(ctx):
+    h = _P()
+    _check(lib().ucp_batch_create(ctx, ctypes.byref(h)), "ucp_batch_create")
+    return h
+
+
+def ucp_batch_add(batch, ens, desc, cptypes, out_min, out_max):
+    N, H, W = ens.shape
+    rc = lib().ucp_batch_add(batch, _ptr(ens, torch.float32, name="ens"), N, H, W,
+                             ctypes.byref(desc), int(cptypes),
+                             _ptr(out_min, torch.float32, name="out_min"),
+                             _ptr(out_max, torch.float32, name="out_max"))
+    _check(rc, "ucp_batch_add")
+
+
+def ucp_batch_tune(batch, stream=None):
+    _check(lib().ucp_batch_tune(batch, _stream(stream)), "ucp_batch_tune")
+
+
+def ucp_batch_run(batch, stream=None):
+    _check(lib().ucp_batch_run(batch, _stream(stream)), "ucp_batch_run")
+
+
+def ucp_batch_destroy(batch):
+    _check(lib().ucp_batch_destroy(batch), "ucp_batch_destroy")
+
+
+# ---------------------------------------------------------------------------
+# convenience layer
+
+
+class Context:
+    """Owns a ucp_ctx on one CUDA device."""
+
+    def __init__(self, device=None):
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = torch.device("cuda", int(device) if not isinstance(device, torch.device)
+                                   else device.index or 0)
+        self.handle = ucp_create(self.device.index)
+
+    def close(self):
+        if self.handle is not None:
+            ucp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def fit(self, ens, desc, with_status=False):
+        _, H, W = ens.shape
+        params = torch.empty((ucp_param_count(desc), H, W), dtype=torch.float32,
+                             device=ens.device)
+        st = torch.empty((H, W), dtype=torch.uint8, device=ens.device) if with_status else None
+        ucp_fit(self.handle, ens, desc, params, st)
+        return (params, st) if with_status else params
+
+    def _outs(self, H, W, device, cptypes):
+        pmin = torch.empty((H, W), dtype=torch.float32, device=device) if cptypes & 1 else None
+        pmax = torch.empty((H, W), dtype=torch.float32, device=device) if cptypes & 2 else None
+        st = torch.empty((H, W), dtype=torch.uint8, device=device)
+        return pmin, pmax, st
+
+    def probability(self, ens, desc, cptypes=UCP_MIN | UCP_MAX):
+        _, H, W = ens.shape
+        pmin, pmax, st = self._outs(H, W, ens.device, cptypes)
+        ucp_probability(self.handle, ens, desc, cptypes, pmin, pmax, st)
+        return pmin, pmax, st
+
+    def probability_from_params(self, params, desc, cptypes=UCP_MIN | UCP_MAX):
+        _, H, W = params.shape
+        pmin, pmax, st = self._outs(H, W, params.device, cptypes)
+        ucp_probability_from_params(self.handle, params, desc, cptypes, pmin, pmax, st)
+        return pmin, pmax, st
+
+    def backward(self, params, desc, cptype, weight):
+        Q = desc.bins if desc.model == UCP_HISTOGRAM else 2
+        _, H, W = params.shape
+        grad = torch.empty((Q, H, W), dtype=torch.float32, device=params.device)
+        ucp_backward(self.handle, params, desc, cptype, weight.contiguous(), grad)
+        return grad
+
+
+_ctx_cache = {}
+
+
+def default_context(device=None):
+    if device is None:
+        device = torch.cuda.current_device()
+    idx = device.index if isinstance(device, torch.device) else int(device)
+    if idx not in _ctx_cache:
+        _ctx_cache[idx] = Context(idx)
+    return _ctx_cache[idx]
+
+
+def probability(ens, model="uniform", types=("min", "max"), **kw):
+    """P_min / P_max fields of an ensemble ens[N][H][W] (float32, CUDA)."""
+    desc = make_desc(model, **kw)
+    cp = (UCP_MIN if "min" in types else 0) | (UCP_MAX if "max" in types else 0)
+    return default_context(ens.device).probability(ens, desc, cp)
+
+
+class UcpProbability(torch.autograd.Function):
+    """P = probability field from parameters; backward is the library's
+    adjoint kernel (ucp_backward) with the incoming gradient as the weight."""
+
+    @staticmethod
+    def forward(ctx, params, model="uniform", bins=8, cptype=UCP_MIN, boundary=0):
+        desc = make_desc(model, bins=bins, boundary=boundary)
+        c = default_context(params.device)
+        pmin, pmax, _ = c.probability_from_params(params.contiguous(), desc, cptype)
+        ctx.save_for_backward(params)
+        ctx.desc_args = (model, bins, boundary)
+        ctx.cptype = cptype
+        return pmin if cptype == UCP_MIN else pmax
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (params,) = ctx.saved_tensors
+        model, bins, boundary = ctx.desc_args
+        desc = make_desc(model, bins=bins, boundary=boundary)
+        c = default_context(params.device)
+        grad = c.backward(params.contiguous(), desc, ctx.cptype,
+                          grad_out.to(torch.float32).contiguous())
+        if desc.model == UCP_HISTOGRAM:
+            full = torch.zeros_like(params)
+            full[2:] = grad
+            grad = full
+        return grad, None, None, None, None

@@ -1,0 +1,158 @@
+"""GPU parity of the multivariate-Gaussian Monte Carlo path.
+
+At identical Philox streams the GPU (FP32 transforms) and the oracle (FP64)
+draw the same samples up to rounding, so a sample can only be counted
+differently when it is a near tie.  The bound per vertex is
+|P_gpu - P_oracle| <= 1e-6 + T_v / S, T_v = the oracle's count of samples with
+min_n |x_v - x_n| < 1e-4 sqrt(Sigma_vv).  Independently seeded runs are
+compared statistically: z = dP / sqrt(2 P (1-P) / S) must look standard normal.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+S = 10_000
+SEED = 0x5EED
+
+
+@pytest.fixture(scope="module")
+def ucp():
+    from paper_2407_18015_gb300 import build
+    build.build()
+    from paper_2407_18015_gb300 import ucp as u
+    return u
+
+
+@pytest.fixture(scope="module")
+def ctx(ucp):
+    c = ucp.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _tie_check(p_gpu, hmin, ties, idx, what):
+    a = p_gpu.cpu().numpy().ravel()[idx].astype(np.float64)
+    ref = hmin / S
+    bound = 1e-6 + ties / S
+    bad = np.abs(a - ref) > bound
+    assert not bad.any(), (what, np.flatnonzero(bad)[:5], a[bad][:5], ref[bad][:5])
+    return float((ties > 0).mean())
+
+
+def test_identical_streams_from_params(ucp, ctx, orc):
+    from paper_2407_18015_gb300 import synth
+    ens_np = synth.ensemble_correlated(40, 48, 40, seed=3)
+    prm, _ = orc.fit(ens_np, orc.MVN)
+    p32 = prm.astype(np.float32)
+    desc = ucp.make_desc("mvn", mc_samples=S, seed=SEED)
+    pmin, pmax, st = ctx.probability_from_params(_dev(p32), desc)
+    torch.cuda.synchronize()
+    idx = np.arange(40 * 48)
+    hmin, hmax, ties, ost = orc.mvn_mc_at(p32.astype(np.float64), idx, S, SEED)
+    frac = _tie_check(pmin, hmin, ties, idx, "min")
+    _tie_check(pmax, hmax, ties, idx, "max")
+    np.testing.assert_array_equal(st.cpu().numpy().ravel(), ost)
+    assert frac < 0.9
+
+
+def test_fused_fit_matches_oracle(ucp, ctx, orc):
+    from paper_2407_18015_gb300 import synth
+    ens_np = synth.ensemble_correlated(33, 29, 40, seed=13)
+    desc = ucp.make_desc("mvn", mc_samples=S, seed=SEED, field_id=7)
+    pmin, pmax, st = ctx.probability(_dev(ens_np), desc)
+    gparams = ctx.fit(_dev(ens_np), desc)
+    torch.cuda.synchronize()
+    prm, _ = orc.fit(ens_np, orc.MVN)
+    np.testing.assert_allclose(gparams.double().cpu().numpy(), prm, rtol=2e-5, atol=2e-6)
+    idx = np.arange(33 * 29)
+    hmin, hmax, ties, _ = orc.mvn_mc_at(prm, idx, S, SEED, field=7)
+    _tie_check(pmin, hmin, ties, idx, "min")
+    _tie_check(pmax, hmax, ties, idx, "max")
+
+
+def test_independent_seed_statistics(ucp, ctx, orc):
+    from paper_2407_18015_gb300 import synth
+    ens_np = synth.ensemble_correlated(32, 32, 40, seed=21)
+    prm, _ = orc.fit(ens_np, orc.MVN)
+    desc = ucp.make_desc("mvn", mc_samples=S, seed=1234)
+    pmin, _, _ = ctx.probability_from_params(_dev(prm.astype(np.float32)), desc)
+    torch.cuda.synchronize()
+    idx = np.arange(32 * 32)
+    hmin, _, _, _ = orc.mvn_mc_at(prm, idx, S, 98765)
+    a = pmin.cpu().numpy().ravel().astype(np.float64)
+    b = hmin / S
+    p = 0.5 * (a + b)
+    keep = (p > 5.0 / S) & (p < 1 - 5.0 / S)
+    z = (a - b)[keep] / np.sqrt(2 * p[keep] * (1 - p[keep]) / S)
+    n = z.size
+    assert n > 200
+    assert abs(z.mean()) < 3.0 / math.sqrt(n)        # ~99.7% CI of the mean
+    assert abs(z.var() - 1.0) < 4.0 * math.sqrt(2.0 / n)
+    assert np.abs(z).max() < 6.0
+
+
+def test_full_size_512_sampled(ucp, ctx, orc):
+    """512 x 512 x 40 correlated ensemble, 10,000 samples per vertex (the
+    Monte Carlo workload), sampled vertices against the oracle."""
+    from paper_2407_18015_gb300 import synth
+    ens_np = synth.ensemble_correlated(512, 512, 40, seed=3)
+    desc = ucp.make_desc("mvn", mc_samples=S, seed=SEED)
+    ens = _dev(ens_np)
+    pmin, pmax, st = ctx.probability(ens, desc)
+    gparams = ctx.fit(ens, desc)
+    torch.cuda.synchronize()
+    assert ((pmin + pmax) <= 1.0 + 1e-6).all()
+    rng = np.random.default_rng(0)
+    idx = np.concatenate([rng.integers(0, 512 * 512, 150), [0, 511, 512 * 511, 512 * 512 - 1],
+                          np.arange(1, 512, 97)])
+    hmin, hmax, ties, _ = orc.mvn_mc_at(gparams.double().cpu().numpy(), idx, S, SEED)
+    # fused fit and ucp_fit sum in different orders: allow the tie band
+    _tie_check(pmin, hmin, ties, idx, "min")
+    _tie_check(pmax, hmax, ties, idx, "max")
+
+
+def test_degenerate_jitter_nonfinite_boundary(ucp, ctx, orc):
+    import helpers as H_
+    mu = np.array([[0.0, 1.0, 2.0, 1.5], [0.5, 0.2, 0.1, 3.0]])
+
+    def cov(y, x, pr):
+        if (y, x) == (0, 1):
+            return np.zeros((5, 5))
+        if (y, x) == (1, 1):
+            return np.ones((5, 5)) * 0.25         # rank one: an exact zero pivot
+        A = np.random.default_rng(y * 7 + x).normal(size=(5, 5))
+        return A @ A.T * 0.1 + np.eye(5) * 0.05
+    prm = H_.mvn_params(2, 4, mu, cov)
+    prm[0, 1, 3] = np.nan
+    p32 = prm.astype(np.float32)
+    for boundary in (0, 1):
+        desc = ucp.make_desc("mvn", mc_samples=4000, seed=9, boundary=boundary)
+        pmin, pmax, st = ctx.probability_from_params(_dev(p32), desc)
+        torch.cuda.synchronize()
+        idx = np.arange(8)
+        hmin, hmax, ties, ost = orc.mvn_mc_at(p32.astype(np.float64), idx, 4000, 9,
+                                              boundary=boundary)
+        g = pmin.cpu().numpy().ravel()
+        gst = st.cpu().numpy().ravel()
+        nan = hmin < 0
+        assert np.isnan(g[nan]).all()
+        # the jittered factor of a singular covariance is too ill-conditioned
+        # for per-sample agreement between FP32 and FP64: flags and range only
+        jit = 5
+        if boundary == 0:
+            assert gst[jit] & ucp.UCP_V_CHOL_JITTER and ost[jit] & ucp.UCP_V_CHOL_JITTER
+            assert 0.0 <= g[jit] <= 1.0
+        ok = ~nan
+        ok[jit] = False
+        assert (np.abs(g[ok] - hmin[ok] / 4000) <= 1e-6 + ties[ok] / 4000).all()
+        keep = np.ones(8, bool)
+        keep[jit] = False
+        np.testing.assert_array_equal(gst[keep], ost[keep])
