@@ -1,0 +1,469 @@
+"""Benchmark: critical-point probability fields on GB300.
+
+Headline workload (one step): a 1024 x 1024 grid with N = 20 float32 members
+(seeded bimodal mixture around a smooth sinusoid base), probability of local
+minimum and maximum under the uniform, Epanechnikov and 8-bin histogram
+models, each a fused statistics + integration kernel.  value = grid vertices
+per second with all three models evaluated (whole job over all ranks).
+
+Also measured in the same run (key "rows"): the multivariate-Gaussian Monte
+Carlo workload (512^2 x 40, 10,000 Philox samples per vertex), the forward +
+adjoint workload (2048^2 x 50, histogram-16 and Epanechnikov), and the batched
+persistent launch (64 uneven fields) against per-field launches.
+
+--impl reference times the FP64 CPU oracle on the host cores instead (the
+reference arm; a bounded sample of the same workload per step).
+
+Multi-GPU (torchrun): every rank runs an independent replica of the workload
+(weak scaling); the only collectives are the host-side barrier and the
+max-over-ranks of the timed region.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+H2, W2, N2, SEED2, BINS2 = 1024, 1024, 20, 2, 8
+MODELS2 = (("uniform", 0), ("epanechnikov", 0), ("histogram", BINS2))
+L2_FLUSH_BYTES = 512 << 20          # > 126 MB L2
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-rows", action="store_true", help="headline workload only")
+    ap.add_argument("--rows", default="mvn,fwdbwd,batch")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured",
+                "sm_max_mhz": float(d.get("sm_max_mhz", SM_MAX_MHZ))}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "source": "fallback", "sm_max_mhz": SM_MAX_MHZ}
+
+
+def fp32_peak_tflops(mhz):
+    """FP32 pipe: 152 SMs x 128 lanes x 2 flops (FMA) per clock."""
+    return SM_COUNT * FP32_LANES * 2 * mhz * 1e6 / 1e12
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+
+class ClockSampler:
+    def __init__(self, index, path):
+        self.path = path
+        self.proc = None
+        try:
+            self.f = open(path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index),
+                 "--query-gpu=timestamp,index,clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, t0=None, t1=None):
+        """Median SM clock and the throttle reasons seen between wall-clock
+        times t0 and t1 (the timed region)."""
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        import datetime
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                if t0 is not None and not (t0 - 0.15 <= ts <= t1 + 0.15):
+                    continue
+                sm.append(float(parts[2]))
+                mx.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[6:10]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work of the kernels
+
+
+def hist_piece_counts(params, bins):
+    """Pieces of the exact histogram integration per vertex: the centre's
+    B+1 bin edges plus every neighbour bin edge strictly inside the centre's
+    support (torch, on the device)."""
+    import torch
+    lo, hi = params[0], params[1]
+    Hh, Ww = lo.shape
+    cnt = torch.full_like(lo, float(bins))  # B pieces from the centre's own edges
+    j = torch.arange(bins + 1, device=lo.device, dtype=torch.float32).view(-1, 1, 1)
+    for dy, dx in ((0, 1), (-1, 0), (0, -1), (1, 0)):
+        ys = slice(max(0, -dy), Hh - max(0, dy))
+        xs = slice(max(0, -dx), Ww - max(0, dx))
+        yn = slice(ys.start + dy, ys.stop + dy)
+        xn = slice(xs.start + dx, xs.stop + dx)
+        nlo, nhi = lo[yn, xn], hi[yn, xn]
+        edges = nlo + j * (nhi - nlo) / bins
+        inside = (edges > lo[ys, xs]) & (edges < hi[ys, xs])
+        cnt[ys, xs] += inside.sum(0).float()
+    return cnt
+
+
+# flops per merged piece of the histogram walk with both types: merge (5
+# compares), four linear factors at the new breakpoint and their CDF
+# complements (16), and for each type the Bernstein product of four linear
+# factors (24), its mean (10), scale and accumulate (3)
+HIST_FLOPS_PER_PIECE = 5 + 16 + 2 * (24 + 10 + 3)
+# Epanechnikov, per vertex and type: 5 pieces x 8 Gauss-Legendre nodes, the
+# density (5) and on average two active cubic survivals (2 x 9) per node,
+# product and weighted sum (4)
+EPAN_FLOPS_PER_VERTEX_TYPE = 5 * 8 * (5 + 2 * 9 + 4)
+
+
+def work_of(model, N, HW, params=None, bins=BINS2):
+    if model == "uniform":
+        return "hbm", (4.0 * N + 8.0) * HW
+    if model == "epanechnikov":
+        return "alu", 2.0 * EPAN_FLOPS_PER_VERTEX_TYPE * HW
+    pieces = float(hist_piece_counts(params, bins).sum().item())
+    return "alu", HIST_FLOPS_PER_PIECE * pieces
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2407_18015_gb300 import synth
+    oracle.build()
+    ens = synth.ensemble_bimodal(H2, W2, N2, seed=SEED2)
+    rows = 96                         # bounded sample per step: 96 x 1024 vertices
+    times = []
+    for s in range(args.warmup + args.steps):
+        y0 = (s * rows) % (H2 - rows)
+        crop = np.ascontiguousarray(ens[:, y0:y0 + rows, :])
+        t = time.perf_counter()
+        for model, bins in MODELS2:
+            mid = {"uniform": 0, "epanechnikov": 1, "histogram": 2}[model]
+            p, _ = oracle.fit(crop, mid, bins=bins or 8)
+            oracle.prob(p, mid, bins=bins or 8)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t)
+    tot = sum(times)
+    verts = rows * W2 * len(times)
+    value = verts / tot
+    cores = oracle.get_threads()
+    line = {
+        "impl": "reference", "metric": "critical-point probability vertices/s "
+        "(uniform + Epanechnikov + histogram-8, min and max, 1024x1024x20)",
+        "value": value, "unit": "vertices/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": "bimodal ensemble 1024x1024, N=20, "
+                                        "uniform/Epanechnikov/hist-8, min+max",
+                                        "sample_rows_per_step": rows},
+        "cpu_baseline": {"value": value, "unit": "vertices/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{rows} rows x 1024 of the 1024x1024x20 field per step"},
+        "e2e": {"value": value, "unit": "vertices/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+
+
+def cpu_baseline_headline(ens_np):
+    """The oracle as it stands on the host cores, on the full headline field
+    (fit + both probabilities for the three models)."""
+    import oracle
+    oracle.build()
+    t = time.perf_counter()
+    for model, bins in MODELS2:
+        mid = {"uniform": 0, "epanechnikov": 1, "histogram": 2}[model]
+        p, _ = oracle.fit(ens_np, mid, bins=bins or 8)
+        oracle.prob(p, mid, bins=bins or 8)
+    dt = time.perf_counter() - t
+    return {"value": H2 * W2 / dt, "unit": "vertices/s", "cores": oracle.get_threads(),
+            "kind": "oracle", "seconds": dt,
+            "sample": "the full 1024x1024x20 field, all three models, min and max, once"}
+
+
+class L2Flush:
+    """Write a 512 MB buffer, then read another: the L2 (126 MB) ends up
+    holding clean lines of unrelated data, so the next step neither hits in L2
+    nor pays for write-backs of the flush."""
+
+    def __init__(self, torch, dev):
+        self.w = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        self.r = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        self.acc = torch.zeros((), dtype=torch.float32, device=dev)
+
+    def __call__(self):
+        self.w.fill_(1.0)
+        self.acc += self.r.sum()
+
+
+def timed_steps(torch, step, steps, warmup, flush, per_kernel_events=False):
+    """Warm-up, then `steps` steps each bracketed by CUDA events on the current
+    stream; the L2 is flushed between steps, outside the events."""
+    for _ in range(warmup):
+        step(None)
+    torch.cuda.synchronize()
+    total = 0.0
+    kernel_ms = {}
+    for _ in range(steps):
+        flush()
+        ev = [] if per_kernel_events else None
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        step(ev)
+        b.record()
+        torch.cuda.synchronize()
+        total += a.elapsed_time(b)
+        if ev:
+            for name, e0, e1 in ev:
+                kernel_ms.setdefault(name, []).append(e0.elapsed_time(e1))
+    return total, kernel_ms
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_2407_18015_gb300 import build, synth, ucp
+    build.build()
+    ctx = ucp.Context(local)
+    ens_np = synth.ensemble_bimodal(H2, W2, N2, seed=SEED2 + 100 * rank)
+    ens = torch.from_numpy(ens_np).to(dev)
+    outs = {m: (torch.empty((H2, W2), device=dev), torch.empty((H2, W2), device=dev))
+            for m, _ in MODELS2}
+    descs = {m: ucp.make_desc(m, bins=b or 8) for m, b in MODELS2}
+    flush = L2Flush(torch, dev)
+
+    def step(ev):
+        for m, _ in MODELS2:
+            if ev is not None:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+            ucp.ucp_probability(ctx.handle, ens, descs[m], ucp.UCP_MIN | ucp.UCP_MAX,
+                                outs[m][0], outs[m][1])
+            if ev is not None:
+                e1.record()
+                ev.append((m, e0, e1))
+
+    # the timed region: barrier + synchronize on both sides
+    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+    sampler = ClockSampler(local, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv"))
+    time.sleep(1.0)                      # let the sampler start before timing
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    total_ms, _ = timed_steps(torch, step, args.steps, args.warmup, flush)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t_wall1 = time.time()
+    clocks = sampler.stop(t_wall0, t_wall1)
+    # per-kernel durations (separate pass, same launches, events between kernels)
+    _, kms = timed_steps(torch, step, max(5, args.steps // 2), 1, flush, per_kernel_events=True)
+    t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = H2 * W2 * args.steps * world / (total_ms / 1e3)
+
+    peaks = measured_peaks()
+    per_model = {}
+    shares = {}
+    for m, b in MODELS2:
+        avg = statistics.mean(kms[m])
+        params = ctx.fit(ens, descs[m]) if m == "histogram" else None
+        bound, amount = work_of(m, N2, H2 * W2, params, BINS2)
+        if bound == "hbm":
+            ach, peak, unit = amount / (avg / 1e3) / 1e9, peaks["hbm_gbs"], "GB/s"
+        else:
+            ach, peak, unit = amount / (avg / 1e3) / 1e12, fp32_peak_tflops(
+                peaks["sm_max_mhz"]), "TFLOP/s"
+        per_model[m] = {"ms": avg, "vertices_per_s": H2 * W2 / (avg / 1e3),
+                        "roofline": {"bound": bound, "achieved": ach, "peak": peak,
+                                     "unit": unit, "frac": ach / peak}}
+        shares[m] = avg
+    dom = max(shares, key=shares.get)
+    rf = dict(per_model[dom]["roofline"])
+    rf["kernel"] = f"tile_kernel<{dom}, from members>"
+    rf["traffic"] = None
+    rf["peak_source"] = ("MEASURED_PEAKS.json hbm_gbs" if rf["bound"] == "hbm" else
+                         f"152 SMs x 128 FP32 lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz")
+    rf["share"] = shares[dom] / sum(shares.values())
+
+    line = {
+        "metric": "critical-point probability vertices/s (uniform + Epanechnikov + "
+                  "histogram-8, min and max, 1024x1024x20)",
+        "value": value, "unit": "vertices/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "bimodal ensemble 1024x1024, N=20, uniform/Epanechnikov/"
+                               "hist-8, min+max, fused fit+integrate",
+                   "grid": [H2, W2], "members": N2, "bins": BINS2,
+                   "parallelism": f"replicas x{world}",
+                   "l2": "flushed between timed steps (512 MB write)"},
+        "gpu_launches": len(MODELS2) * args.steps,
+        "clocks": clocks,
+        "roofline": rf,
+        "per_model": per_model,
+    }
+    if rank == 0:
+        line["e2e"] = e2e_headline(torch, ucp, ctx, ens_np, args)
+        line["cpu_baseline"] = cpu_baseline_headline(ens_np) if world == 1 else None
+        if not args.no_rows:
+            line["rows"] = other_rows(torch, ucp, ctx, dev, args, flush, peaks)
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def e2e_headline(torch, ucp, ctx, ens_np, args):
+    """Same metric through ucp_probability_host: pinned host members in,
+    host probability fields out, copies inside the timed region."""
+    ens_h = torch.from_numpy(ens_np).pin_memory()
+    outs = {m: (torch.empty((H2, W2)).pin_memory(), torch.empty((H2, W2)).pin_memory())
+            for m, _ in MODELS2}
+    descs = {m: ucp.make_desc(m, bins=b or 8) for m, b in MODELS2}
+
+    def step():
+        for m, _ in MODELS2:
+            ucp.ucp_probability_host(ctx.handle, ens_h, descs[m], 3, outs[m][0], outs[m][1])
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    n = max(3, min(args.steps, 10))
+    t = time.perf_counter()
+    for _ in range(n):
+        step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t) / n
+    return {"value": H2 * W2 / dt, "unit": "vertices/s", "ms_per_step": dt * 1e3,
+            "h2d_bytes_per_step": len(MODELS2) * ens_np.nbytes,
+            "d2h_bytes_per_step": len(MODELS2) * 2 * H2 * W2 * 4,
+            "api": "ucp_probability_host, one call per model"}
+
+
+def other_rows(torch, ucp, ctx, dev, args, flush, peaks):
+    from paper_2407_18015_gb300 import synth
+    want = set(args.rows.split(","))
+    rows = {}
+    steps = max(3, min(args.steps, 5))
+    if "mvn" in want:
+        e3 = torch.from_numpy(synth.ensemble_correlated(512, 512, 40, seed=3)).to(dev)
+        d = ucp.make_desc("mvn", mc_samples=10000, seed=0x5EED)
+        pm = torch.empty((512, 512), device=dev)
+        px = torch.empty_like(pm)
+        ms, _ = timed_steps(torch, lambda ev: ucp.ucp_probability(ctx.handle, e3, d, 3, pm, px),
+                            steps, 2, flush)
+        ms /= steps
+        samples = 512 * 512 * 10000
+        rows["mvn_512x512x40_S10000"] = {
+            "ms": ms, "vertices_per_s": 512 * 512 / (ms / 1e3),
+            "samples_per_s": samples / (ms / 1e3), "min_and_max": True}
+        del e3
+    if "fwdbwd" in want:
+        e4 = torch.from_numpy(synth.ensemble_bimodal(2048, 2048, 50, seed=4)).to(dev)
+        Wt = torch.from_numpy(synth.weight_field(2048, 2048, seed=44)).to(dev)
+        for m, b in (("histogram", 16), ("epanechnikov", 0)):
+            d = ucp.make_desc(m, bins=b or 8)
+            params = ctx.fit(e4, d)
+            pmin = torch.empty((2048, 2048), device=dev)
+            Q = b if m == "histogram" else 2
+            grad = torch.empty((Q, 2048, 2048), device=dev)
+
+            def fb(ev, d=d, params=params, pmin=pmin, grad=grad):
+                ucp.ucp_fit(ctx.handle, e4, d, params)
+                ucp.ucp_probability_from_params(ctx.handle, params, d, ucp.UCP_MIN, pmin, None)
+                ucp.ucp_backward(ctx.handle, params, d, ucp.UCP_MIN, Wt, grad)
+
+            def fw(ev, d=d, pmin=pmin):
+                ucp.ucp_probability(ctx.handle, e4, d, ucp.UCP_MIN, pmin, None)
+            ms_fb, _ = timed_steps(torch, fb, steps, 2, flush)
+            ms_fw, _ = timed_steps(torch, fw, steps, 2, flush)
+            rows[f"fwd_bwd_2048x2048x50_{m}{b or ''}"] = {
+                "ms_fwd_bwd": ms_fb / steps,
+                "fwd_bwd_vertices_per_s": 2048 * 2048 / (ms_fb / steps / 1e3),
+                "ms_fwd": ms_fw / steps,
+                "fwd_vertices_per_s": 2048 * 2048 / (ms_fw / steps / 1e3)}
+            del params, grad
+        del e4
+    return rows
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -82,6 +82,120 @@ __global__ void __launch_bounds__(256) fit_kernel(Field f) {
 
 __device__ __forceinline__ float qnan() { return __int_as_float(0x7fc00000); }
 
+// Statistics of V consecutive vertices of one row (V = 1, or 4 with one
+// 16-byte load per member), written to the shared parameter tile at l.
+template <int V>
+__device__ __forceinline__ void load_v(const float *p, float (&v)[V]) {
+  if constexpr (V == 4) {
+    const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else {
+    v[0] = __ldg(p);
+  }
+}
+
+template <int MODEL, int V>
+__device__ __forceinline__ void stage_members(const Field &f, float *sm, int l, long long gi) {
+  const long long plane = f.plane;
+  const float *p = f.ens + gi;
+  const int N = f.N;
+  float mn[V], mx[V];
+  bool nf[V];
+  if constexpr (MODEL == kEpan) {
+    // one pass, shifted by the first member (see members_epan)
+    float x0[V];
+    Kahan s1[V], s2[V];
+    load_v<V>(p, x0);
+#pragma unroll
+    for (int q = 0; q < V; ++q) { mn[q] = mx[q] = x0[q]; nf[q] = false; }
+#pragma unroll 4
+    for (int k = 0; k < N; ++k) {
+      float v[V];
+      load_v<V>(p + (long long)k * plane, v);
+#pragma unroll
+      for (int q = 0; q < V; ++q) {
+        nf[q] |= !isfinite(v[q]);
+        mn[q] = fminf(mn[q], v[q]);
+        mx[q] = fmaxf(mx[q], v[q]);
+        const float d = v[q] - x0[q];
+        s1[q].add(d);
+        s2[q].add(d * d);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+      float m, w;
+      if (mn[q] == mx[q]) {
+        m = mn[q];
+        w = 0.f;
+      } else {
+        const float S1 = s1[q].get(), S2 = s2[q].get();
+        const float md = S1 / (float)N;
+        m = x0[q] + md;
+        w = f.epan_scale * sqrtf(fmaxf(S2 - S1 * md, 0.f) / (float)(N - 1));
+      }
+      sm[l + q] = nf[q] ? qnan() : m;
+      sm[HALO + l + q] = nf[q] ? qnan() : w;
+    }
+  } else {
+    {
+      float v[V];
+      load_v<V>(p, v);
+#pragma unroll
+      for (int q = 0; q < V; ++q) { mn[q] = mx[q] = v[q]; nf[q] = false; }
+    }
+#pragma unroll 8
+    for (int k = 0; k < N; ++k) {
+      float v[V];
+      load_v<V>(p + (long long)k * plane, v);
+#pragma unroll
+      for (int q = 0; q < V; ++q) {
+        nf[q] |= !isfinite(v[q]);
+        mn[q] = fminf(mn[q], v[q]);
+        mx[q] = fmaxf(mx[q], v[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+      sm[l + q] = nf[q] ? qnan() : mn[q];
+      sm[HALO + l + q] = nf[q] ? qnan() : mx[q];
+    }
+    if constexpr (MODEL == kHist) {
+      const int B = f.B;
+      float sc[V];
+      bool bin[V];
+#pragma unroll
+      for (int q = 0; q < V; ++q) {
+        float *wq = sm + 2 * HALO + l + q;
+        for (int b = 0; b < B; ++b) wq[b * HALO] = nf[q] ? qnan() : 0.f;
+        bin[q] = !nf[q] && mn[q] != mx[q];
+        if (!nf[q] && !bin[q]) wq[0] = 1.f;
+        sc[q] = bin[q] ? __fdiv_rn((float)B, __fsub_rn(mx[q], mn[q])) : 0.f;
+      }
+      bool any = false;
+#pragma unroll
+      for (int q = 0; q < V; ++q) any |= bin[q];
+      if (any) {
+#pragma unroll 4
+        for (int k = 0; k < N; ++k) {
+          float v[V];
+          load_v<V>(p + (long long)k * plane, v);
+#pragma unroll
+          for (int q = 0; q < V; ++q)
+            if (bin[q]) sm[(2 + hist_bin(v[q], mn[q], sc[q], B)) * HALO + l + q] += 1.f;
+        }
+#pragma unroll
+        for (int q = 0; q < V; ++q)
+          if (bin[q])
+            for (int b = 0; b < B; ++b) {
+              float *w = sm + (2 + b) * HALO + l + q;
+              *w = __fdiv_rn(*w, (float)N);
+            }
+      }
+    }
+  }
+}
+
 template <int MODEL, bool FROM_MEMBERS>
 __device__ __forceinline__ void stage_vertex(const Field &f, float *sm, int l, long long gi) {
   const long long plane = f.plane;
@@ -151,19 +265,48 @@ __device__ __forceinline__ uint8_t check_params(const float *sm, int l, int B, f
   return st;
 }
 
+// resident CTAs per SM each model's register budget is tuned for
+template <int MODEL>
+struct TileOcc {
+  static constexpr int value = MODEL == kUniform ? 5 : (MODEL == kEpan ? 4 : 3);
+};
+
 template <int MODEL, bool FROM_MEMBERS>
-__global__ void __launch_bounds__(NTHREADS) tile_kernel(Field f, int tiles_x) {
+__global__ void __launch_bounds__(NTHREADS, TileOcc<MODEL>::value) tile_kernel(Field f, int tiles_x) {
   extern __shared__ float sm[];
   const int tile = blockIdx.x;
   const int ty0 = f.y0 + (tile / tiles_x) * TY, tx0 = (tile % tiles_x) * TX;
   // rows beyond y1 are neither computed nor needed (row y1 is a neighbour)
   const int ylim = min(f.H, f.y1 + 1);
 
-  for (int l = threadIdx.x; l < HALO; l += NTHREADS) {
-    const int r = l / HX, c = l - r * HX;
-    const int gy = ty0 + r - 1, gx = tx0 + c - 1;
-    if (gy < 0 || gy >= ylim || gx < 0 || gx >= f.W) continue;
-    stage_vertex<MODEL, FROM_MEMBERS>(f, sm, l, (long long)gy * f.W + gx);
+  if (FROM_MEMBERS) {
+    // work items per halo row: the two halo columns (scalar) and eight
+    // groups of four interior columns (one float4 per member when aligned)
+    for (int it = threadIdx.x; it < HY * 10; it += NTHREADS) {
+      const int r = it / 10, g = it - r * 10;
+      const int gy = ty0 + r - 1;
+      if (gy < 0 || gy >= ylim) continue;
+      const long long rowi = (long long)gy * f.W;
+      if (g == 0 || g == 9) {
+        const int c = g == 0 ? 0 : HX - 1, gx = tx0 + c - 1;
+        if (gx >= 0 && gx < f.W) stage_members<MODEL, 1>(f, sm, r * HX + c, rowi + gx);
+      } else {
+        const int c0 = 1 + 4 * (g - 1), gx0 = tx0 + 4 * (g - 1);
+        if (f.vec4 && gx0 + 3 < f.W) {
+          stage_members<MODEL, 4>(f, sm, r * HX + c0, rowi + gx0);
+        } else {
+          for (int q = 0; q < 4; ++q)
+            if (gx0 + q < f.W) stage_members<MODEL, 1>(f, sm, r * HX + c0 + q, rowi + gx0 + q);
+        }
+      }
+    }
+  } else {
+    for (int l = threadIdx.x; l < HALO; l += NTHREADS) {
+      const int r = l / HX, c = l - r * HX;
+      const int gy = ty0 + r - 1, gx = tx0 + c - 1;
+      if (gy < 0 || gy >= ylim || gx < 0 || gx >= f.W) continue;
+      stage_vertex<MODEL, false>(f, sm, l, (long long)gy * f.W + gx);
+    }
   }
   __syncthreads();
 
@@ -221,30 +364,24 @@ __global__ void __launch_bounds__(NTHREADS) tile_kernel(Field f, int tiles_x) {
         pmax = gM;
       } else {
         HistWalk nw[4];
+        float Tw[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           HistWalk &h = nw[i];
-          h.w = sm + 2 * HALO + nl[i];
-          h.ws = HALO;
-          h.j = -1;
-          h.S = T[i];
-          h.slope = 0.f;
-          h.eleft = -kFar;
           if (!present[i]) {
-            h.B = 0; h.lam = kFar; h.h = 1.f; h.end = kFar; h.enext = kFar;
+            h.init_absent();
+            Tw[i] = 2.f;  // CDF complement 2 - 1 = 1 for an absent neighbour
             continue;
           }
+          Tw[i] = T[i];
           const float lo = sm[nl[i]], hi = sm[HALO + nl[i]];
-          h.lam = lo - lo1;
-          if (lo == hi) {
-            h.B = 0; h.h = 1.f; h.end = h.lam;
-          } else {
-            h.B = B; h.h = (hi - lo) / (float)B; h.end = hi - lo1;
-          }
-          h.enext = h.lam;
-          for (int g = 0; g <= B && h.enext <= 0.f && h.j < h.B; ++g) h.advance();
+          if (lo == hi)
+            h.init(nl[i], 0, lo - lo1, 1.f, lo - lo1, T[i]);
+          else
+            h.init(nl[i], B, lo - lo1, (hi - lo) / (float)B, hi - lo1, T[i]);
+          for (int g = 0; g <= B && h.nx <= 0.f && h.k < h.B; ++g) h.advance<HALO>(sm + 2 * HALO);
         }
-        hist_walk(sm + 2 * HALO + l, HALO, B, hi1 - lo1, nw, present, T, f.cptypes, pmin, pmax);
+        hist_walk<HALO>(sm + 2 * HALO, l, B, hi1 - lo1, nw, Tw, f.cptypes, pmin, pmax);
       }
     }
     const long long gi = (long long)gy * f.W + gx;
@@ -303,11 +440,13 @@ static cudaError_t launch_tile(const Field &f, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
+  Field g = f;
+  g.vec4 = (f.ens != nullptr) && (f.W % 4 == 0) && ((reinterpret_cast<uintptr_t>(f.ens) & 15) == 0);
   const int tiles_x = (f.W + TX - 1) / TX, tiles_y = (f.y1 - f.y0 + TY - 1) / TY;
   if (tiles_y <= 0) return cudaSuccess;
   const long long tiles = (long long)tiles_x * tiles_y;
   if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-  tile_kernel<MODEL, FM><<<(int)tiles, NTHREADS, smem, s>>>(f, tiles_x);
+  tile_kernel<MODEL, FM><<<(int)tiles, NTHREADS, smem, s>>>(g, tiles_x);
   return cudaGetLastError();
 }
 

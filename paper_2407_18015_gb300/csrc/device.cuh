@@ -12,7 +12,7 @@
 //   - Epanechnikov: pdf_1 quadratic, G_n cubic, degree <= 14 on a piece,
 //     integrated exactly by 8-point Gauss-Legendre (exact to degree 15).
 // All arithmetic is FP32 in a vertex-local frame (the centre's lower support
-// end or mean is the origin), pieces are summed with Neumaier compensation.
+// end or mean is the origin), pieces are summed with Kahan compensation.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -42,14 +42,21 @@ constexpr float kFar = 3.0e38f;  // "never starts" breakpoint (finite: 0*kFar = 
 // ---------------------------------------------------------------------------
 // small helpers
 
-struct Neumaier {
+// Reciprocal of a positive, finite, normal width (2 ulp; no IEEE division
+// sequence): support widths and bin widths only.
+__device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
+
+// Compensated (Kahan) summation: the running rounding error c is fed back
+// into the next addend.
+struct Kahan {
   float s = 0.f, c = 0.f;
   __device__ __forceinline__ void add(float x) {
-    float t = s + x;
-    c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
     s = t;
   }
-  __device__ __forceinline__ float get() const { return s + c; }
+  __device__ __forceinline__ float get() const { return s; }
 };
 
 __host__ __device__ constexpr int binom(int n, int k) {
@@ -58,8 +65,20 @@ __host__ __device__ constexpr int binom(int n, int k) {
   return r;
 }
 
-// integral over [0,1] of (1-t)^(K-j) t^j = 1 / ((K+1) C(K,j))
-__host__ __device__ constexpr float bern_weight(int K, int j) { return 1.0f / float((K + 1) * binom(K, j)); }
+// integral over [0,1] of (1-t)^(K-j) t^j = 1 / ((K+1) C(K,j)), as a table
+// built at compile time (index [K][j], K <= 4)
+struct BernTable {
+  float w[5][5];
+  constexpr BernTable() : w{} {
+    for (int K = 0; K <= 4; ++K)
+      for (int j = 0; j <= K; ++j) w[K][j] = 1.0f / float((K + 1) * binom(K, j));
+  }
+};
+constexpr BernTable kBern{};
+template <int K, int J>
+struct BernW {
+  static constexpr float value = kBern.w[K][J];
+};
 
 // integral over tau in [0,1] of prod_{i<K} (L[i] (1-tau) + R[i] tau):
 // the product in the Bernstein basis of degree K (coefficients e_j = sums of
@@ -79,9 +98,18 @@ __device__ __forceinline__ float bern_mean(const float *L, const float *R) {
       for (int j = i; j >= 1; --j) e[j] = fmaf(e[j - 1], R[i], e[j] * L[i]);
       e[0] = e[0] * L[i];
     }
-    float s = 0.f;
-#pragma unroll
-    for (int j = 0; j <= K; ++j) s = fmaf(e[j], bern_weight(K, j), s);
+    // weights 1/((K+1) C(K,j)) are symmetric in j
+    float s;
+    if constexpr (K == 1) {
+      s = 0.5f * (e[0] + e[1]);
+    } else if constexpr (K == 2) {
+      s = fmaf(e[0] + e[2], BernW<2, 0>::value, e[1] * BernW<2, 1>::value);
+    } else if constexpr (K == 3) {
+      s = fmaf(e[0] + e[3], BernW<3, 0>::value, (e[1] + e[2]) * BernW<3, 1>::value);
+    } else {
+      s = fmaf(e[0] + e[4], BernW<4, 0>::value,
+               fmaf(e[1] + e[3], BernW<4, 1>::value, e[2] * BernW<4, 2>::value));
+    }
     return s;
   }
 }
@@ -142,7 +170,7 @@ __device__ __forceinline__ void members_epan(const float *__restrict__ p, long l
                                              float scale, float &m, float &w, float &mn,
                                              float &mx, bool &nonfinite) {
   const float x0 = __ldg(p);
-  Neumaier s1, s2;
+  Kahan s1, s2;
   float a = x0, b = x0;
   bool nf = false;
   for (int k = 0; k < N; ++k) {
@@ -197,17 +225,19 @@ __device__ __forceinline__ float uniform_side(float W1, float R, float al[4], fl
   // breakpoints x_0 = 0 < t0 <= t1 <= t2 <= t3 <= x_5 = R; on piece j the
   // factors 0..j-1 (sorted) have started and the others are 1.
   float x[6] = {0.f, t[0], t[1], t[2], t[3], R};
-  Neumaier acc;
+  Kahan acc;
   acc.add(x[1]);  // piece 0: no factor has started
   float L[4], Rv[4];
 #pragma unroll
   for (int j = 1; j <= 4; ++j) {
     const float x0 = x[j], x1 = x[j + 1];
+    // left values: the previous piece's right values, plus the factor that
+    // starts at x0 (1 there unless its start was clamped to 0)
 #pragma unroll
-    for (int i = 0; i < j; ++i) {
-      L[i] = fmaxf(fmaf(-(x0 - pay[0][i]), pay[1][i], 1.f), 0.f);
-      Rv[i] = fmaxf(fmaf(-(x1 - pay[0][i]), pay[1][i], 1.f), 0.f);
-    }
+    for (int i = 0; i < j - 1; ++i) L[i] = Rv[i];
+    L[j - 1] = fmaxf(fmaf(-(x0 - pay[0][j - 1]), pay[1][j - 1], 1.f), 0.f);
+#pragma unroll
+    for (int i = 0; i < j; ++i) Rv[i] = fmaxf(fmaf(-(x1 - pay[0][i]), pay[1][i], 1.f), 0.f);
     float I;
     if (j == 1) I = bern_mean<1>(L, Rv);
     else if (j == 2) I = bern_mean<2>(L, Rv);
@@ -215,7 +245,7 @@ __device__ __forceinline__ float uniform_side(float W1, float R, float al[4], fl
     else I = bern_mean<4>(L, Rv);
     acc.add((x1 - x0) * I);
   }
-  return acc.get() / W1;
+  return acc.get() * frcp(W1);
 }
 
 struct UniParams {
@@ -251,38 +281,38 @@ __device__ __forceinline__ void uniform_vertex(UniParams c, const UniParams *nb,
     return;
   }
   const float W1 = c.b - c.a;
+  float sl[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    sl[i] = (present[i] && nb[i].a != nb[i].b) ? frcp(nb[i].b - nb[i].a) : 0.f;
   if (want & kMin) {
-    float al[4], sl[4], R = W1;
+    float al[4], s2[4], R = W1;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
+      s2[i] = sl[i];
       if (present[i]) {
-        const float a = nb[i].a, b = nb[i].b;
-        al[i] = a - c.a;
-        sl[i] = (a == b) ? 0.f : 1.f / (b - a);
-        R = fminf(R, b - c.a);
+        al[i] = nb[i].a - c.a;
+        R = fminf(R, nb[i].b - c.a);
       } else {
         al[i] = kFar;
-        sl[i] = 0.f;
       }
     }
-    pmin = uniform_side(W1, R, al, sl);
+    pmin = uniform_side(W1, R, al, s2);
   }
   if (want & kMax) {
     // negated variables: -X has support [-b, -a]; origin at -b1
-    float al[4], sl[4], R = W1;
+    float al[4], s2[4], R = W1;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
+      s2[i] = sl[i];
       if (present[i]) {
-        const float a = nb[i].a, b = nb[i].b;
-        al[i] = c.b - b;
-        sl[i] = (a == b) ? 0.f : 1.f / (b - a);
-        R = fminf(R, c.b - a);
+        al[i] = c.b - nb[i].b;
+        R = fminf(R, c.b - nb[i].a);
       } else {
         al[i] = kFar;
-        sl[i] = 0.f;
       }
     }
-    pmax = uniform_side(W1, R, al, sl);
+    pmax = uniform_side(W1, R, al, s2);
   }
 }
 
@@ -320,9 +350,9 @@ __device__ __forceinline__ float epan_side(float w1, float L, float R, float al[
   }
   sort4<2>(t, pay);
   const float x[6] = {L, t[0], t[1], t[2], t[3], R};
-  const float iw1 = 1.f / w1;
+  const float iw1 = frcp(w1);
   const float c1 = 0.75f * iw1;
-  Neumaier acc;
+  Kahan acc;
 #pragma unroll
   for (int j = 0; j <= 4; ++j) {
     const float x0 = x[j], x1 = x[j + 1];
@@ -383,7 +413,7 @@ __device__ __forceinline__ void epan_vertex(EpanParams c, const EpanParams *nb,
           al[i] = kFar; d[i] = kFar; iw[i] = 0.f;
           R = fminf(R, dn);
         } else {
-          al[i] = dn - wn; d[i] = dn; iw[i] = 1.f / wn;
+          al[i] = dn - wn; d[i] = dn; iw[i] = frcp(wn);
           R = fminf(R, dn + wn);
         }
       } else {
@@ -403,7 +433,7 @@ __device__ __forceinline__ void epan_vertex(EpanParams c, const EpanParams *nb,
           al[i] = kFar; d[i] = kFar; iw[i] = 0.f;
           R = fminf(R, dn);
         } else {
-          al[i] = dn - wn; d[i] = dn; iw[i] = 1.f / wn;
+          al[i] = dn - wn; d[i] = dn; iw[i] = frcp(wn);
           R = fminf(R, dn + wn);
         }
       } else {
@@ -418,33 +448,55 @@ __device__ __forceinline__ void epan_vertex(EpanParams c, const EpanParams *nb,
 // closed-form integration, histogram model (breakpoint merge)
 
 // A neighbour's survival G(x) (mixture form) as a walk over its segments:
-// before the support G = T; on bin j G = S_j - w_j (x - e_j) / h; after it 0.
-// A point mass is a histogram without bins (one jump from T to 0).
+// before the support G = T; on bin k G = S_k - w_k (x - e_k) / h; after it 0.
+// A point mass is a histogram without bins (one jump from T to 0).  An absent
+// neighbour is the constant 1 (S = 1, slope 0, never advances); its "total"
+// is set to 2 so that the CDF complement T - G is 1 as well.
 struct HistWalk {
-  const float *w;   // masses in shared memory, stride `ws`
-  int ws;
-  int B, j;         // j: -1 before the support, B after it
-  float lam, h, end;  // local support start, bin width, local support end
-  float eleft, enext, S, slope;
-  __device__ __forceinline__ float mass(int q) const { return w[q * ws]; }
-  __device__ __forceinline__ void advance() {
-    ++j;
-    if (j >= B) {
-      j = B;
-      S = 0.f;
-      slope = 0.f;
-      eleft = enext;
-      enext = kFar;
-      return;
-    }
-    if (j > 0) S -= mass(j - 1);
-    const float wj = mass(j);
-    slope = wj / h;
-    eleft = enext;
-    enext = (j + 1 < B) ? fmaf((float)(j + 1), h, lam) : end;
+  int off;          // shared-memory index of the neighbour's first mass
+  int B, k;         // k: -1 before the support, B after it
+  float lam, h, invh, end;  // local support start, bin width, 1/h, local end
+  float el, nx, S, sl;      // current segment: left edge, next edge, G(el), slope
+  __device__ __forceinline__ void init_absent() {
+    off = 0; B = 0; k = 0; lam = kFar; h = 1.f; invh = 0.f; end = kFar;
+    el = 0.f; nx = kFar; S = 1.f; sl = 0.f;
+  }
+  __device__ __forceinline__ void init(int off_, int B_, float lam_, float h_, float end_,
+                                       float T) {
+    off = off_; B = B_; k = -1;
+    lam = lam_; h = h_; invh = B_ > 0 ? frcp(h_) : 0.f; end = end_;
+    el = -kFar; nx = lam_; S = T; sl = 0.f;
+  }
+  // move to the next segment; G is continuous at a bin edge, so the new left
+  // value is the current segment's value there (a point mass jumps to 0)
+  template <int WS>
+  __device__ __forceinline__ void advance(const float *w) {
+    const float Sn = fmaxf(fmaf(-sl, nx - el, S), 0.f);
+    ++k;
+    const bool in = k < B;
+    S = in ? Sn : 0.f;
+    sl = in ? w[off + k * WS] * invh : 0.f;
+    el = nx;
+    nx = (k + 1 < B) ? fmaf((float)(k + 1), h, lam) : (in ? end : kFar);
+  }
+  // advance if the next edge is at or before x (straight-line code: the
+  // mass load always reads a valid address of this neighbour's planes)
+  template <int WS>
+  __device__ __forceinline__ void advance_if(const float *w, float x) {
+    const bool a = nx <= x;
+    const float Sn = fmaxf(fmaf(-sl, nx - el, S), 0.f);
+    const int kn = a ? k + 1 : k;
+    const bool in = kn < B;
+    const float wv = w[off + max(min(kn, B - 1), 0) * WS];
+    const float nxn = (kn + 1 < B) ? fmaf((float)(kn + 1), h, lam) : (in ? end : kFar);
+    S = a ? (in ? Sn : 0.f) : S;
+    sl = a ? (in ? wv * invh : 0.f) : sl;
+    el = a ? nx : el;
+    nx = a ? nxn : nx;
+    k = kn;
   }
   __device__ __forceinline__ float G(float x) const {
-    return fmaxf(fmaf(-slope, x - eleft, S), 0.f);
+    return fmaxf(fmaf(-sl, x - el, S), 0.f);
   }
 };
 
@@ -454,63 +506,53 @@ struct HistWalk {
 // the constant w_j / h1 and each factor is linear, so the piece integral is
 // the Bernstein mean of the factor end values.  Beyond a neighbour's support
 // its survival is 0, before it its CDF is 0, so both integrals can run over
-// the centre's whole support.
-__device__ __forceinline__ void hist_walk(const float *cw, int cws, int B, float W1,
-                                          HistWalk *nw, const bool *present, const float *T,
-                                          unsigned want, float &pmin, float &pmax) {
-  const float h1 = W1 / (float)B;
+// the centre's whole support.  Pieces are summed per centre bin and the bin
+// sums (times the bin density) with Kahan compensation.
+template <int WS>
+__device__ __forceinline__ void hist_walk(const float *w, int coff, int B, float W1,
+                                          HistWalk *nw, const float *T, unsigned want,
+                                          float &pmin, float &pmax) {
+  const float h1 = W1 / (float)B, ih1 = frcp(h1);
   int j1 = 0;
-  float p1 = cw[0] / h1;
   float e1 = (B > 1) ? h1 : W1;
   float x0 = 0.f;
   float Gl[4], Fl[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    if (present[i]) {
-      Gl[i] = nw[i].G(0.f);
-      Fl[i] = fmaxf(T[i] - Gl[i], 0.f);
-    } else {
-      Gl[i] = 1.f;
-      Fl[i] = 1.f;
-    }
+    Gl[i] = nw[i].G(0.f);
+    Fl[i] = fmaxf(T[i] - Gl[i], 0.f);
   }
-  Neumaier amin, amax;
+  Kahan amin, amax;
+  float bmin = 0.f, bmax = 0.f;
   const int max_steps = 5 * (B + 2) + 4;
   for (int step = 0; step < max_steps; ++step) {
-    float x1 = e1;
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-      if (present[i]) x1 = fminf(x1, nw[i].enext);
-    x1 = fminf(x1, W1);
+    float x1 = fminf(fminf(e1, W1), fminf(fminf(nw[0].nx, nw[1].nx), fminf(nw[2].nx, nw[3].nx)));
     float Gr[4], Fr[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      if (present[i]) {
-        Gr[i] = nw[i].G(x1);
-        Fr[i] = fmaxf(T[i] - Gr[i], 0.f);
-      } else {
-        Gr[i] = 1.f;
-        Fr[i] = 1.f;
-      }
+      Gr[i] = nw[i].G(x1);
+      Fr[i] = fmaxf(T[i] - Gr[i], 0.f);
     }
-    const float len = (x1 - x0) * p1;
-    if (want & kMin) amin.add(len * bern_mean<4>(Gl, Gr));
-    if (want & kMax) amax.add(len * bern_mean<4>(Fl, Fr));
-    if (x1 >= W1) break;
-    if (e1 <= x1) {
+    const float len = x1 - x0;
+    if (want & kMin) bmin = fmaf(len, bern_mean<4>(Gl, Gr), bmin);
+    if (want & kMax) bmax = fmaf(len, bern_mean<4>(Fl, Fr), bmax);
+    const bool last = x1 >= W1;
+    if (last || e1 <= x1) {
+      const float p1 = w[coff + j1 * WS] * ih1;
+      amin.add(bmin * p1);
+      amax.add(bmax * p1);
+      bmin = bmax = 0.f;
       ++j1;
-      p1 = (j1 < B) ? cw[j1 * cws] / h1 : 0.f;
       e1 = (j1 + 1 < B) ? (float)(j1 + 1) * h1 : W1;
     }
+    if (last) break;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      if (present[i] && nw[i].enext <= x1) {
-        nw[i].advance();
-        Gr[i] = nw[i].G(x1);
-        Fr[i] = fmaxf(T[i] - Gr[i], 0.f);
-      }
-      Gl[i] = Gr[i];
-      Fl[i] = Fr[i];
+      // continuous at a bin edge, but a point mass jumps: the left value of
+      // the next piece is re-evaluated on the new segment
+      nw[i].advance_if<WS>(w, x1);
+      Gl[i] = nw[i].G(x1);
+      Fl[i] = fmaxf(T[i] - Gl[i], 0.f);
     }
     x0 = x1;
   }

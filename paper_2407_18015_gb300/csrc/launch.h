@@ -20,6 +20,7 @@ struct Field {
   int boundary;         // 0 in-grid neighbours, 1 zero at the boundary
   float epan_scale;
   unsigned cptypes;     // bit 1 min, bit 2 max
+  bool vec4;            // members may be read as aligned float4 (W % 4 == 0, 16B base)
 };
 
 // Tile of the closed-form kernels: TY x TX vertices plus a one-vertex halo.
