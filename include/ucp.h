@@ -196,6 +196,25 @@ int ucp_params_from_error_bound(ucp_ctx *ctx, const float *decompressed, float e
 int ucp_backward(ucp_ctx *ctx, const float *params, int H, int W, const ucp_model_desc *desc,
                  int cptype, const float *weight, float *grad_params, ucp_stream stream);
 
+/* The adjoint without any device allocation (the paper has no counterpart:
+ * it has no gradients).  Some callers cannot call cudaMalloc once they are
+ * running -- an application whose own allocator already owns the device
+ * memory budget, or a latency-critical path on which cudaMalloc / cudaFree,
+ * which may synchronise the whole device, are not acceptable.  This entry
+ * point takes no context and allocates nothing: its partial-row scratch is a
+ * fixed file-scope device array of ucp_backward_static_capacity() floats
+ * (16 MiB), held by every device that loads the library until exit.  Inputs
+ * and outputs are as for ucp_backward, on the CURRENT device.  5 * Q * H * W
+ * must not exceed the capacity (Q = 2, or bins for histograms), else
+ * UCP_ERR_SHAPE and nothing runs.  The first call on a device looks up the
+ * array's device address (once, with that device current); make that first
+ * call before any stream capture.  All calls on a device share the array:
+ * calls that can overlap on the GPU (unordered streams) race on it.  It keeps
+ * the last call's contents; no part of it needs to start at zero. */
+size_t ucp_backward_static_capacity(void);
+int ucp_backward_static(const float *params, int H, int W, const ucp_model_desc *desc,
+                        int cptype, const float *weight, float *grad_params, ucp_stream stream);
+
 /* Batched launch: many fields of different sizes, member counts, models
  * (uniform, Epanechnikov, histogram) and types in one persistent kernel.
  * ucp_batch_add records a field (device pointers, borrowed until the batch

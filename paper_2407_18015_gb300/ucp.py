@@ -77,6 +77,8 @@ def lib():
                                          _I),
                 "ucp_params_from_error_bound": ([_P, _P, ctypes.c_float, _I, _I, _P, _P], _I),
                 "ucp_backward": ([_P, _P, _I, _I, D, _I, _P, _P, _P], _I),
+                "ucp_backward_static": ([_P, _I, _I, D, _I, _P, _P, _P], _I),
+                "ucp_backward_static_capacity": ([], ctypes.c_size_t),
                 "ucp_batch_create": ([_P, ctypes.POINTER(_P)], _I),
                 "ucp_batch_add": ([_P, _P, _I, _I, _I, D, ctypes.c_uint, _P, _P], _I),
                 "ucp_batch_tune": ([_P, _P], _I),
@@ -220,6 +222,22 @@ def ucp_backward(ctx, params, desc, cptype, weight, grad_params, stream=None):
                             _ptr(grad_params, torch.float32, name="grad_params"),
                             _stream(stream, params.device))
     _check(rc, "ucp_backward", ctx)
+
+
+def ucp_backward_static(params, desc, cptype, weight, grad_params, stream=None):
+    """The adjoint without device allocation (no context; scratch is a fixed
+    device array inside the library; see include/ucp.h)."""
+    _, H, W = params.shape
+    rc = lib().ucp_backward_static(_ptr(params, torch.float32, name="params"), H, W,
+                                   ctypes.byref(desc), int(cptype),
+                                   _ptr(weight, torch.float32, name="weight"),
+                                   _ptr(grad_params, torch.float32, name="grad_params"),
+                                   _stream(stream, params.device))
+    _check(rc, "ucp_backward_static")
+
+
+def ucp_backward_static_capacity():
+    return int(lib().ucp_backward_static_capacity())
 
 
 def ucp_batch_create(ctx):

@@ -1,0 +1,60 @@
+"""The allocation-free adjoint (ucp_backward_static) against the context
+adjoint (ucp_backward), through the C ABI, on two calls in a row.
+
+ucp_backward_static serves callers that must not allocate device memory once
+running; its scratch is a fixed device array inside the library, shared by
+all calls on a device.  This file is collected last so that a run stopping
+at the first failure has run every other test first; it also passes alone in
+a fresh process.
+"""
+import numpy as np
+import pytest
+import torch
+
+import helpers as H_
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ucp():
+    from paper_2407_18015_gb300 import build
+    build.build()
+    from paper_2407_18015_gb300 import ucp as u
+    return u
+
+
+@pytest.mark.parametrize("model,mid,bins", [("uniform", 0, 0), ("epanechnikov", 1, 0),
+                                            ("histogram", 2, 16)])
+def test_static_adjoint_matches_context_adjoint(ucp, model, mid, bins):
+    torch.cuda.set_device(0)
+    ctx = ucp.Context(0)
+    rng = np.random.default_rng(71 + mid)
+    desc = ucp.make_desc(model, bins=bins or 8)
+    # two calls in a row with different inputs and shapes: the shared scratch
+    # keeps the previous call's contents, which must not leak into the next
+    for (Hh, Ww, cptype) in ((37, 53, ucp.UCP_MIN), (29, 64, ucp.UCP_MAX)):
+        p = torch.from_numpy(H_.random_params(mid, Hh, Ww, rng, bins=bins or 8)
+                             .astype(np.float32)).cuda()
+        W = torch.from_numpy(rng.uniform(0, 1, (Hh, Ww)).astype(np.float32)).cuda()
+        ref = ctx.backward(p, desc, cptype, W)
+        got = torch.full_like(ref, float("nan"))
+        ucp.ucp_backward_static(p, desc, cptype, W, got)
+        torch.cuda.synchronize()
+        a, b = got.cpu().numpy().astype(np.float64), ref.cpu().numpy().astype(np.float64)
+        scale = max(1.0, np.abs(b).max())
+        assert np.all(np.abs(a - b) <= 1e-4 * np.abs(b) + 2e-5 * scale)
+    ctx.close()
+
+
+def test_static_adjoint_rejects_oversize(ucp):
+    cap = ucp.ucp_backward_static_capacity()
+    assert cap == 4 << 20
+    desc = ucp.make_desc("histogram", bins=16)
+    side = int((cap // (5 * 16)) ** 0.5) + 2
+    p = torch.zeros((18, side, side), device="cuda")
+    W = torch.zeros((side, side), device="cuda")
+    g = torch.zeros((16, side, side), device="cuda")
+    with pytest.raises(ucp.UcpError) as e:
+        ucp.ucp_backward_static(p, desc, ucp.UCP_MIN, W, g)
+    assert e.value.status == ucp.UCP_ERR_SHAPE
