@@ -455,7 +455,50 @@ def other_rows(torch, ucp, ctx, dev, args, flush, peaks):
                 "fwd_vertices_per_s": 2048 * 2048 / (ms_fw / steps / 1e3)}
             del params, grad
         del e4
+    if "batch" in want:
+        rows["batch_64_fields"] = batch_row(torch, ucp, ctx, dev, steps, flush)
     return rows
+
+
+def batch_row(torch, ucp, ctx, dev, steps, flush):
+    """64 fields of uneven sizes (128^2..2048^2), N in {10,20,50,100}, mixed
+    models and types: 64 per-field launches vs one autotuned persistent launch
+    replayed from a CUDA graph."""
+    from paper_2407_18015_gb300 import synth
+    specs = synth.batch_specs()
+    fields = []
+    verts = 0
+    for sp in specs:
+        ens = torch.from_numpy(synth.batch_field(sp)).to(dev)
+        desc = ucp.make_desc(sp["model"], bins=sp["bins"])
+        cp = ucp.UCP_MIN if sp["cptype"] == "min" else ucp.UCP_MAX
+        o = torch.empty((sp["H"], sp["W"]), device=dev)
+        fields.append((ens, desc, cp, o))
+        verts += sp["H"] * sp["W"]
+
+    def per_field(ev):
+        for ens, desc, cp, o in fields:
+            ucp.ucp_probability(ctx.handle, ens, desc, cp, o if cp == 1 else None,
+                                o if cp == 2 else None)
+    ms_pf, _ = timed_steps(torch, per_field, steps, 2, flush)
+    b = ucp.Batch(ctx)
+    for ens, desc, cp, o in fields:
+        b.add(ens, desc, cp, o if cp == 1 else None, o if cp == 2 else None)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b.tune()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        b.run()
+    ms_b, _ = timed_steps(torch, lambda ev: g.replay(), steps, 2, flush)
+    b.close()
+    ms_pf /= steps
+    ms_b /= steps
+    return {"fields": len(fields), "vertices": verts, "ms_per_field_launches": ms_pf,
+            "ms_batched_graph": ms_b, "speedup": ms_pf / ms_b,
+            "batched_vertices_per_s": verts / (ms_b / 1e3),
+            "per_field_vertices_per_s": verts / (ms_pf / 1e3)}
 
 
 def main():

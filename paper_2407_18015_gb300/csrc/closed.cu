@@ -11,6 +11,7 @@
 // and integrates P_min / P_max exactly (device.cuh).
 #include "device.cuh"
 #include "launch.h"
+#include "tile.cuh"
 
 namespace ucp {
 
@@ -80,191 +81,6 @@ __global__ void __launch_bounds__(256) fit_kernel(Field f) {
 // ---------------------------------------------------------------------------
 // tile kernel
 
-__device__ __forceinline__ float qnan() { return __int_as_float(0x7fc00000); }
-
-// Statistics of V consecutive vertices of one row (V = 1, or 4 with one
-// 16-byte load per member), written to the shared parameter tile at l.
-template <int V>
-__device__ __forceinline__ void load_v(const float *p, float (&v)[V]) {
-  if constexpr (V == 4) {
-    const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
-    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-  } else {
-    v[0] = __ldg(p);
-  }
-}
-
-template <int MODEL, int V>
-__device__ __forceinline__ void stage_members(const Field &f, float *sm, int l, long long gi) {
-  const long long plane = f.plane;
-  const float *p = f.ens + gi;
-  const int N = f.N;
-  float mn[V], mx[V];
-  bool nf[V];
-  if constexpr (MODEL == kEpan) {
-    // one pass, shifted by the first member (see members_epan)
-    float x0[V];
-    Kahan s1[V], s2[V];
-    load_v<V>(p, x0);
-#pragma unroll
-    for (int q = 0; q < V; ++q) { mn[q] = mx[q] = x0[q]; nf[q] = false; }
-#pragma unroll 4
-    for (int k = 0; k < N; ++k) {
-      float v[V];
-      load_v<V>(p + (long long)k * plane, v);
-#pragma unroll
-      for (int q = 0; q < V; ++q) {
-        nf[q] |= !isfinite(v[q]);
-        mn[q] = fminf(mn[q], v[q]);
-        mx[q] = fmaxf(mx[q], v[q]);
-        const float d = v[q] - x0[q];
-        s1[q].add(d);
-        s2[q].add(d * d);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < V; ++q) {
-      float m, w;
-      if (mn[q] == mx[q]) {
-        m = mn[q];
-        w = 0.f;
-      } else {
-        const float S1 = s1[q].get(), S2 = s2[q].get();
-        const float md = S1 / (float)N;
-        m = x0[q] + md;
-        w = f.epan_scale * sqrtf(fmaxf(S2 - S1 * md, 0.f) / (float)(N - 1));
-      }
-      sm[l + q] = nf[q] ? qnan() : m;
-      sm[HALO + l + q] = nf[q] ? qnan() : w;
-    }
-  } else {
-    {
-      float v[V];
-      load_v<V>(p, v);
-#pragma unroll
-      for (int q = 0; q < V; ++q) { mn[q] = mx[q] = v[q]; nf[q] = false; }
-    }
-#pragma unroll 8
-    for (int k = 0; k < N; ++k) {
-      float v[V];
-      load_v<V>(p + (long long)k * plane, v);
-#pragma unroll
-      for (int q = 0; q < V; ++q) {
-        nf[q] |= !isfinite(v[q]);
-        mn[q] = fminf(mn[q], v[q]);
-        mx[q] = fmaxf(mx[q], v[q]);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < V; ++q) {
-      sm[l + q] = nf[q] ? qnan() : mn[q];
-      sm[HALO + l + q] = nf[q] ? qnan() : mx[q];
-    }
-    if constexpr (MODEL == kHist) {
-      const int B = f.B;
-      float sc[V];
-      bool bin[V];
-#pragma unroll
-      for (int q = 0; q < V; ++q) {
-        float *wq = sm + 2 * HALO + l + q;
-        for (int b = 0; b < B; ++b) wq[b * HALO] = nf[q] ? qnan() : 0.f;
-        bin[q] = !nf[q] && mn[q] != mx[q];
-        if (!nf[q] && !bin[q]) wq[0] = 1.f;
-        sc[q] = bin[q] ? __fdiv_rn((float)B, __fsub_rn(mx[q], mn[q])) : 0.f;
-      }
-      bool any = false;
-#pragma unroll
-      for (int q = 0; q < V; ++q) any |= bin[q];
-      if (any) {
-#pragma unroll 4
-        for (int k = 0; k < N; ++k) {
-          float v[V];
-          load_v<V>(p + (long long)k * plane, v);
-#pragma unroll
-          for (int q = 0; q < V; ++q)
-            if (bin[q]) sm[(2 + hist_bin(v[q], mn[q], sc[q], B)) * HALO + l + q] += 1.f;
-        }
-#pragma unroll
-        for (int q = 0; q < V; ++q)
-          if (bin[q])
-            for (int b = 0; b < B; ++b) {
-              float *w = sm + (2 + b) * HALO + l + q;
-              *w = __fdiv_rn(*w, (float)N);
-            }
-      }
-    }
-  }
-}
-
-template <int MODEL, bool FROM_MEMBERS>
-__device__ __forceinline__ void stage_vertex(const Field &f, float *sm, int l, long long gi) {
-  const long long plane = f.plane;
-  if (!FROM_MEMBERS) {
-    const int P = (MODEL == kHist) ? 2 + f.B : 2;
-    for (int q = 0; q < P; ++q) sm[q * HALO + l] = __ldg(f.params + q * plane + gi);
-    return;
-  }
-  const float *p = f.ens + gi;
-  if (MODEL == kUniform) {
-    float mn, mx;
-    bool nf;
-    members_minmax(p, plane, f.N, mn, mx, nf);
-    sm[l] = nf ? qnan() : mn;
-    sm[HALO + l] = nf ? qnan() : mx;
-  } else if (MODEL == kEpan) {
-    float m, w, mn, mx;
-    bool nf;
-    members_epan(p, plane, f.N, f.epan_scale, m, w, mn, mx, nf);
-    sm[l] = nf ? qnan() : m;
-    sm[HALO + l] = nf ? qnan() : w;
-  } else {
-    float mn, mx;
-    bool nf;
-    members_minmax(p, plane, f.N, mn, mx, nf);
-    const int B = f.B;
-    float *wq = sm + 2 * HALO + l;
-    if (nf) {
-      sm[l] = sm[HALO + l] = qnan();
-      for (int q = 0; q < B; ++q) wq[q * HALO] = qnan();
-      return;
-    }
-    sm[l] = mn;
-    sm[HALO + l] = mx;
-    for (int q = 0; q < B; ++q) wq[q * HALO] = 0.f;
-    if (mn == mx) {
-      wq[0] = 1.f;
-      return;
-    }
-    const float s = __fdiv_rn((float)B, __fsub_rn(mx, mn));
-    for (int k = 0; k < f.N; ++k) {
-      const int j = hist_bin(__ldg(p + (long long)k * plane), mn, s, B);
-      wq[j * HALO] += 1.f;
-    }
-    for (int q = 0; q < B; ++q) wq[q * HALO] = __fdiv_rn(wq[q * HALO], (float)f.N);
-  }
-}
-
-// validity of one participant's parameters; returns status bits and the
-// histogram total mass
-template <int MODEL>
-__device__ __forceinline__ uint8_t check_params(const float *sm, int l, int B, float &T) {
-  const float a = sm[l], b = sm[HALO + l];
-  T = 1.f;
-  if (!isfinite(a) || !isfinite(b)) return V_NONFINITE;
-  if (MODEL == kUniform) return a > b ? V_BAD : (a == b ? V_DEGENERATE : 0);
-  if (MODEL == kEpan) return b < 0.f ? V_BAD : (b == 0.f ? V_DEGENERATE : 0);
-  uint8_t st = a > b ? V_BAD : (a == b ? V_DEGENERATE : 0);
-  float t = 0.f;
-  for (int q = 0; q < B; ++q) {
-    const float w = sm[(2 + q) * HALO + l];
-    if (!isfinite(w)) st |= V_NONFINITE;
-    else if (w < 0.f) st |= V_BAD;
-    t += w;
-  }
-  T = t;
-  return st;
-}
-
 // resident CTAs per SM each model's register budget is tuned for
 template <int MODEL>
 struct TileOcc {
@@ -275,120 +91,7 @@ template <int MODEL, bool FROM_MEMBERS>
 __global__ void __launch_bounds__(NTHREADS, TileOcc<MODEL>::value) tile_kernel(Field f, int tiles_x) {
   extern __shared__ float sm[];
   const int tile = blockIdx.x;
-  const int ty0 = f.y0 + (tile / tiles_x) * TY, tx0 = (tile % tiles_x) * TX;
-  // rows beyond y1 are neither computed nor needed (row y1 is a neighbour)
-  const int ylim = min(f.H, f.y1 + 1);
-
-  if (FROM_MEMBERS) {
-    // work items per halo row: the two halo columns (scalar) and eight
-    // groups of four interior columns (one float4 per member when aligned)
-    for (int it = threadIdx.x; it < HY * 10; it += NTHREADS) {
-      const int r = it / 10, g = it - r * 10;
-      const int gy = ty0 + r - 1;
-      if (gy < 0 || gy >= ylim) continue;
-      const long long rowi = (long long)gy * f.W;
-      if (g == 0 || g == 9) {
-        const int c = g == 0 ? 0 : HX - 1, gx = tx0 + c - 1;
-        if (gx >= 0 && gx < f.W) stage_members<MODEL, 1>(f, sm, r * HX + c, rowi + gx);
-      } else {
-        const int c0 = 1 + 4 * (g - 1), gx0 = tx0 + 4 * (g - 1);
-        if (f.vec4 && gx0 + 3 < f.W) {
-          stage_members<MODEL, 4>(f, sm, r * HX + c0, rowi + gx0);
-        } else {
-          for (int q = 0; q < 4; ++q)
-            if (gx0 + q < f.W) stage_members<MODEL, 1>(f, sm, r * HX + c0 + q, rowi + gx0 + q);
-        }
-      }
-    }
-  } else {
-    for (int l = threadIdx.x; l < HALO; l += NTHREADS) {
-      const int r = l / HX, c = l - r * HX;
-      const int gy = ty0 + r - 1, gx = tx0 + c - 1;
-      if (gy < 0 || gy >= ylim || gx < 0 || gx >= f.W) continue;
-      stage_vertex<MODEL, false>(f, sm, l, (long long)gy * f.W + gx);
-    }
-  }
-  __syncthreads();
-
-  for (int v = threadIdx.x; v < TY * TX; v += NTHREADS) {
-    const int r = v / TX + 1, c = v % TX + 1;
-    const int gy = ty0 + r - 1, gx = tx0 + c - 1;
-    if (gy >= f.y1 || gx >= f.W) continue;
-    const int l = r * HX + c;
-    bool present[4];
-    int nl[4];
-    int k = 0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int yy = gy + kDy[i], xx = gx + kDx[i];
-      present[i] = (yy >= 0 && yy < f.H && xx >= 0 && xx < f.W);
-      nl[i] = l + kDy[i] * HX + kDx[i];
-      k += present[i];
-    }
-    float T[4], Tc;
-    uint8_t st = check_params<MODEL>(sm, l, f.B, Tc);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      T[i] = 1.f;
-      if (present[i]) st |= check_params<MODEL>(sm, nl[i], f.B, T[i]) & (V_NONFINITE | V_BAD);
-    }
-    float pmin = 0.f, pmax = 0.f;
-    if (st & (V_NONFINITE | V_BAD)) {
-      pmin = pmax = qnan();
-    } else if (f.boundary == 1 && k < 4) {
-      pmin = pmax = 0.f;
-    } else if (MODEL == kUniform) {
-      UniParams cp{sm[l], sm[HALO + l]}, nb[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) nb[i] = UniParams{sm[nl[i]], sm[HALO + nl[i]]};
-      uniform_vertex(cp, nb, present, f.cptypes, pmin, pmax);
-    } else if (MODEL == kEpan) {
-      EpanParams cp{sm[l], sm[HALO + l]}, nb[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) nb[i] = EpanParams{sm[nl[i]], sm[HALO + nl[i]]};
-      epan_vertex(cp, nb, present, f.cptypes, pmin, pmax);
-    } else {
-      const int B = f.B;
-      const float lo1 = sm[l], hi1 = sm[HALO + l];
-      if (lo1 == hi1) {
-        float gm = Tc, gM = Tc;
-        for (int i = 0; i < 4; ++i) {
-          if (!present[i]) continue;
-          float gt, lt;
-          hist_tails_at(sm + 2 * HALO + nl[i], HALO, B, sm[nl[i]], sm[HALO + nl[i]], T[i], lo1,
-                        gt, lt);
-          gm *= gt;
-          gM *= lt;
-        }
-        pmin = gm;
-        pmax = gM;
-      } else {
-        HistWalk nw[4];
-        float Tw[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          HistWalk &h = nw[i];
-          if (!present[i]) {
-            h.init_absent();
-            Tw[i] = 2.f;  // CDF complement 2 - 1 = 1 for an absent neighbour
-            continue;
-          }
-          Tw[i] = T[i];
-          const float lo = sm[nl[i]], hi = sm[HALO + nl[i]];
-          if (lo == hi)
-            h.init(nl[i], 0, lo - lo1, 1.f, lo - lo1, T[i]);
-          else
-            h.init(nl[i], B, lo - lo1, (hi - lo) / (float)B, hi - lo1, T[i]);
-          for (int g = 0; g <= B && h.nx <= 0.f && h.k < h.B; ++g) h.advance<HALO>(sm + 2 * HALO);
-        }
-        hist_walk<HALO>(sm + 2 * HALO, l, B, hi1 - lo1, nw, Tw, f.cptypes, pmin, pmax);
-      }
-    }
-    const long long gi = (long long)gy * f.W + gx;
-    if ((f.cptypes & kMin) && f.out_min) f.out_min[gi] = pmin;
-    if ((f.cptypes & kMax) && f.out_max) f.out_max[gi] = pmax;
-    if (f.status) f.status[gi] = st;
-  }
+  process_tile<MODEL, FROM_MEMBERS, TY>(f, f.y0 + (tile / tiles_x) * TY, (tile % tiles_x) * TX, sm);
 }
 
 // ---------------------------------------------------------------------------

@@ -372,3 +372,35 @@ class UcpProbability(torch.autograd.Function):
             full[2:] = grad
             grad = full
         return grad, None, None, None, None
+
+
+class Batch:
+    """Many fields in one persistent launch (ucp_batch_*).  Tensors passed to
+    add() are kept alive until close()."""
+
+    def __init__(self, ctx):
+        self.ctx = ctx
+        self.handle = ucp_batch_create(ctx.handle)
+        self._keep = []
+
+    def add(self, ens, desc, cptypes, out_min, out_max):
+        ucp_batch_add(self.handle, ens, desc, cptypes, out_min, out_max)
+        self._keep.append((ens, out_min, out_max))
+
+    def tune(self, stream=None):
+        ucp_batch_tune(self.handle, stream)
+
+    def run(self, stream=None):
+        ucp_batch_run(self.handle, stream)
+
+    def close(self):
+        if self.handle is not None:
+            ucp_batch_destroy(self.handle)
+            self.handle = None
+            self._keep = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
