@@ -281,13 +281,11 @@ def timed_steps(torch, step, steps, warmup, flush, per_kernel_events=False):
 
 def run_ours(args):
     import torch
-    rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2407_18015_gb300 import replicas
+    rank, world, local = replicas.rank_env()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
+    replicas.init("nccl", dev)
     from paper_2407_18015_gb300 import build, synth, ucp
     build.build()
     ctx = ucp.Context(local)
@@ -314,23 +312,17 @@ def run_ours(args):
     os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
     sampler = ClockSampler(local, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv"))
     time.sleep(1.0)                      # let the sampler start before timing
-    if world > 1:
-        torch.distributed.barrier()
+    replicas.barrier()
     torch.cuda.synchronize()
     t_wall0 = time.time()
     total_ms, _ = timed_steps(torch, step, args.steps, args.warmup, flush)
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    replicas.barrier()
     t_wall1 = time.time()
     clocks = sampler.stop(t_wall0, t_wall1)
     # per-kernel durations (separate pass, same launches, events between kernels)
     _, kms = timed_steps(torch, step, max(5, args.steps // 2), 1, flush, per_kernel_events=True)
-    t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = H2 * W2 * args.steps * world / (total_ms / 1e3)
+    total_ms, _, value = replicas.job_throughput(total_ms, H2 * W2 * args.steps, device=dev)
 
     peaks = measured_peaks()
     per_model = {}

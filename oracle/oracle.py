@@ -57,12 +57,14 @@ def lib():
                                               ctypes.c_int64, _d, _d]
             L.orc_mvn_mc_at.argtypes = [_d, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i64,
                                         ctypes.c_int64, ctypes.c_int, ctypes.c_uint64,
-                                        ctypes.c_uint32, _i64, _i64, _i64, _u8]
+                                        ctypes.c_uint32, _i64, _i64, _i64, _i64, _u8]
+            L.orc_saddle.argtypes = [_d, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     _i64, ctypes.c_int64, _d, _u8]
             L.orc_philox4x32_10.argtypes = [_u32, _u32, _u32]
             L.orc_grad.argtypes = [_d, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_int, ctypes.c_int, _d, _d]
             for fn in ("orc_fit", "orc_prob", "orc_prob_at", "orc_prob_hist_h5_at",
-                       "orc_mvn_mc_at", "orc_grad"):
+                       "orc_mvn_mc_at", "orc_grad", "orc_saddle"):
                 getattr(L, fn).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -151,23 +153,49 @@ def prob_hist_h5_at(params, bins, idx):
     return pmin, pmax
 
 
-def mvn_mc_at(params, idx, samples, seed, field=0, boundary=0):
+def mvn_mc_at(params, idx, samples, seed, field=0, boundary=0, with_saddle=False):
     """Multivariate-Gaussian Monte Carlo at vertices idx.
-    Returns (hits_min, hits_max, near_ties, status) as int64/uint8 arrays."""
+    Returns (hits_min, hits_max, near_ties, status) as int64/uint8 arrays, and
+    the saddle hits as a fifth array when with_saddle."""
     params = _c64(params)
     _, H, W = params.shape
     idx = np.ascontiguousarray(idx, dtype=np.int64)
     n = idx.size
     hmin = np.empty(n, np.int64)
     hmax = np.empty(n, np.int64)
+    hsad = np.empty(n, np.int64)
     ties = np.empty(n, np.int64)
     st = np.empty(n, np.uint8)
     rc = lib().orc_mvn_mc_at(_p(params, _d), H, W, boundary, _p(idx, _i64), n, int(samples),
                              int(seed) & 0xFFFFFFFFFFFFFFFF, int(field) & 0xFFFFFFFF,
-                             _p(hmin, _i64), _p(hmax, _i64), _p(ties, _i64), _p(st, _u8))
+                             _p(hmin, _i64), _p(hmax, _i64), _p(hsad, _i64), _p(ties, _i64),
+                             _p(st, _u8))
     if rc != 0:
         raise ValueError("orc_mvn_mc_at rejected its arguments")
+    if with_saddle:
+        return hmin, hmax, ties, st, hsad
     return hmin, hmax, ties, st
+
+
+def saddle(params, model, bins=0, idx=None):
+    """Saddle probability (Eq. saddleProb) of every vertex, [H][W], or of the
+    linear indices idx; and the status."""
+    params = _c64(params)
+    _, H, W = params.shape
+    if idx is None:
+        out = np.empty((H, W), np.float64)
+        st = np.empty((H, W), np.uint8)
+        rc = lib().orc_saddle(_p(params, _d), H, W, model, bins, None, 0, _p(out, _d),
+                              _p(st, _u8))
+    else:
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        out = np.empty(idx.size, np.float64)
+        st = np.empty(idx.size, np.uint8)
+        rc = lib().orc_saddle(_p(params, _d), H, W, model, bins, _p(idx, _i64), idx.size,
+                              _p(out, _d), _p(st, _u8))
+    if rc != 0:
+        raise ValueError("orc_saddle rejected its arguments")
+    return out, st
 
 
 def philox4x32_10(counter, key):

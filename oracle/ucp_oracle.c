@@ -30,6 +30,14 @@
  * t = x - x_left, multiplied out in the monomial basis and integrated with its
  * exact antiderivative.  There is no quadrature, no blocking and no fusion.
  *
+ * Saddle (Eq. saddleProb): with the neighbours e, n, w, s as X_2..X_5,
+ *   t1 = Pr[X_1 < X_e, X_1 > X_n, X_1 < X_w, X_1 > X_s] = int pdf_1 G_e F_n G_w F_s
+ *   t2 = Pr[X_1 > X_e, X_1 < X_n, X_1 > X_w, X_1 < X_s] = int pdf_1 F_e G_n F_w G_s
+ *   P_saddle = t1 + t2.  A vertex without all four neighbours has no
+ *   alternating neighbourhood: 0, except on a 1 x W or H x 1 grid, where the
+ *   two-neighbour form (Eq. 1D-saddleProb) is used with X_2 the next
+ *   neighbour (e, or s on a column) and X_3 the previous one (w, or n).
+ *
  * Distribution models (Sec. "Parametric Noise Models",
  * Sec. "Nonparametric Noise Models"):
  *   uniform      params (a, b):     pdf 1/(b-a) on [a, b]
@@ -411,6 +419,57 @@ static void vertex_min_max(const double *params, int H, int W, int model, int B,
   *pmax = prob_vertex(&v, nb, k, 1);
 }
 
+/* integral of pdf_v times, per neighbour, its survival (sign +1) or its CDF
+ * (sign -1); a point-mass centre gives the product of the strict tail
+ * probabilities */
+static double prob_mixed(const dist_t *v, const dist_t *nb, const int *sign, int k) {
+  const pw_t *f[5];
+  int n;
+  if (v->point) {
+    double p = v->total;
+    for (n = 0; n < k; ++n)
+      p *= sign[n] > 0 ? prob_greater(&nb[n], v->lo) : prob_less(&nb[n], v->lo);
+    return p;
+  }
+  f[0] = &v->pdf;
+  for (n = 0; n < k; ++n) f[1 + n] = sign[n] > 0 ? &nb[n].G : &nb[n].F;
+  return integrate_product(f, 1 + k, v->lo, v->hi);
+}
+
+static double vertex_saddle(const double *params, int H, int W, int model, int B, int y, int x,
+                            uint8_t *status) {
+  int64_t plane = (int64_t)H * W, nidx[4];
+  int slot[4], k = neighbours(H, W, y, x, nidx, slot), n, st;
+  int np = nparams(model, B), s1[4], s2[4];
+  double pv[2 + MAXB];
+  dist_t v, nb[4];
+  gather_params(params, plane, np, (int64_t)y * W + x, pv);
+  st = dist_make(model, pv, B, &v);
+  for (n = 0; n < k; ++n) {
+    double pn[2 + MAXB];
+    gather_params(params, plane, np, nidx[n], pn);
+    st |= dist_make(model, pn, B, &nb[n]) & (ST_NONFINITE | ST_BAD_PARAMS);
+  }
+  if (status) *status = (uint8_t)st;
+  if (st & (ST_NONFINITE | ST_BAD_PARAMS)) return NAN;
+  if (k == 4) {
+    /* slots are e, n, w, s in this order: t1 wants G, F, G, F */
+    for (n = 0; n < 4; ++n) {
+      s1[n] = (slot[n] == 0 || slot[n] == 2) ? 1 : -1;
+      s2[n] = -s1[n];
+    }
+  } else if (k == 2 && (H == 1 || W == 1)) {
+    /* the line case: next = e or s (slots 0, 3), previous = w or n */
+    for (n = 0; n < 2; ++n) {
+      s1[n] = (slot[n] == 0 || slot[n] == 3) ? 1 : -1;
+      s2[n] = -s1[n];
+    }
+  } else {
+    return 0.0;
+  }
+  return prob_mixed(&v, nb, s1, k) + prob_mixed(&v, nb, s2, k);
+}
+
 /* ------------------------------------------------------------------------ */
 /* exported: closed-form probability fields                                 */
 
@@ -449,6 +508,20 @@ int orc_prob_at(const double *params, int H, int W, int model, int B, int bounda
                    status ? status + t : NULL);
     if (out_min) out_min[t] = a;
     if (out_max) out_max[t] = b;
+  }
+  return 0;
+}
+
+/* Saddle probability of every vertex (or of idx[0..n-1] when idx != NULL). */
+int orc_saddle(const double *params, int H, int W, int model, int B, const int64_t *idx,
+               int64_t n, double *out, uint8_t *status) {
+  int64_t t, total = idx ? n : (int64_t)H * W;
+  if (model != ORC_UNIFORM && model != ORC_EPAN && model != ORC_HIST) return -1;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(orc_get_threads())
+  for (t = 0; t < total; ++t) {
+    int64_t i = idx ? idx[t] : t;
+    out[t] = vertex_saddle(params, H, W, model, B, (int)(i / W), (int)(i % W),
+                           status ? status + t : NULL);
   }
   return 0;
 }
@@ -691,7 +764,8 @@ static int cholesky(const double *A, int n, double *L) {
  * deterministic. */
 int orc_mvn_mc_at(const double *params, int H, int W, int boundary, const int64_t *idx,
                   int64_t n, int S, uint64_t seed, uint32_t field, int64_t *hits_min,
-                  int64_t *hits_max, int64_t *near_ties, uint8_t *status) {
+                  int64_t *hits_max, int64_t *hits_saddle, int64_t *near_ties,
+                  uint8_t *status) {
   int64_t t, plane = (int64_t)H * W;
   if (S < 1) return -1;
 #pragma omp parallel for schedule(dynamic, 1) num_threads(orc_get_threads())
@@ -700,8 +774,15 @@ int orc_mvn_mc_at(const double *params, int H, int W, int boundary, const int64_
     int y = (int)(i / W), x = (int)(i % W), slot[4], k, a, b, nv, st = 0, s;
     int sl[5];
     double mu[5], A[25], L[25], full[5][5], tr = 0.0;
-    int64_t hmin = 0, hmax = 0, ties = 0;
+    int64_t hmin = 0, hmax = 0, hsad = 0, ties = 0;
+    int ssg[5] = {0, 0, 0, 0, 0}, saddle_ok;
     k = neighbours(H, W, y, x, nidx, slot);
+    /* saddle sign of each present neighbour (see vertex_saddle): +1 wants
+     * x_v < x_n in t1, -1 wants x_v > x_n */
+    saddle_ok = (k == 4) || (k == 2 && (H == 1 || W == 1));
+    for (a = 0; a < k; ++a)
+      ssg[1 + a] = (k == 4) ? ((slot[a] == 0 || slot[a] == 2) ? 1 : -1)
+                            : ((slot[a] == 0 || slot[a] == 3) ? 1 : -1);
     /* unpack the packed covariance */
     {
       int r = 5;
@@ -725,12 +806,14 @@ int orc_mvn_mc_at(const double *params, int H, int W, int boundary, const int64_
       if (!isfinite(A[a])) st |= ST_NONFINITE;
     if (st) {
       hits_min[t] = hits_max[t] = -1;
+      if (hits_saddle) hits_saddle[t] = -1;
       near_ties[t] = 0;
       if (status) status[t] = (uint8_t)st;
       continue;
     }
     if (boundary == 1 && k < 4) {
       hits_min[t] = hits_max[t] = 0;
+      if (hits_saddle) hits_saddle[t] = 0;
       near_ties[t] = 0;
       if (status) status[t] = 0;
       continue;
@@ -743,6 +826,14 @@ int orc_mvn_mc_at(const double *params, int H, int W, int boundary, const int64_
       }
       hits_min[t] = lt ? S : 0;
       hits_max[t] = gt ? S : 0;
+      if (hits_saddle) {
+        int t1 = saddle_ok, t2 = saddle_ok;
+        for (a = 1; a < nv; ++a) {
+          t1 &= ssg[a] > 0 ? mu[0] < mu[a] : mu[0] > mu[a];
+          t2 &= ssg[a] > 0 ? mu[0] > mu[a] : mu[0] < mu[a];
+        }
+        hits_saddle[t] = (t1 || t2) ? S : 0;
+      }
       near_ties[t] = 0;
       if (status) status[t] = ST_DEGENERATE;
       continue;
@@ -759,6 +850,7 @@ int orc_mvn_mc_at(const double *params, int H, int W, int boundary, const int64_
       st |= ok ? ST_CHOL_JITTER : ST_CHOL_FAIL;
       if (!ok) {
         hits_min[t] = hits_max[t] = -1;
+        if (hits_saddle) hits_saddle[t] = -1;
         near_ties[t] = 0;
         if (status) status[t] = (uint8_t)st;
         continue;
@@ -771,7 +863,7 @@ int orc_mvn_mc_at(const double *params, int H, int W, int boundary, const int64_
       for (s = 0; s < S; ++s) {
         uint32_t ctr[4], r8[8];
         double u[6], z[6], xv[5];
-        int lt = 1, gt = 1;
+        int lt = 1, gt = 1, t1 = saddle_ok, t2 = saddle_ok;
         double dmin = INFINITY;
         ctr[0] = (uint32_t)s; ctr[1] = (uint32_t)i; ctr[2] = field; ctr[3] = 0;
         orc_philox4x32_10(ctr, key, r8);
@@ -793,15 +885,19 @@ int orc_mvn_mc_at(const double *params, int H, int W, int boundary, const int64_
           double dd = fabs(xv[0] - xv[a]);
           lt &= xv[0] < xv[a];
           gt &= xv[0] > xv[a];
+          t1 &= ssg[a] > 0 ? xv[0] < xv[a] : xv[0] > xv[a];
+          t2 &= ssg[a] > 0 ? xv[0] > xv[a] : xv[0] < xv[a];
           if (dd < dmin) dmin = dd;
         }
         hmin += lt;
         hmax += gt;
+        hsad += (t1 || t2);
         ties += (nv > 1 && dmin < tie_tol);
       }
     }
     hits_min[t] = hmin;
     hits_max[t] = hmax;
+    if (hits_saddle) hits_saddle[t] = hsad;
     near_ties[t] = ties;
     if (status) status[t] = (uint8_t)st;
   }

@@ -116,3 +116,37 @@ def mvn_params(H, W, mu, cov_fn):
                     out[r, y, x] = C[a, b] if (present[a] and present[b]) else 0.0
                     r += 1
     return out
+
+
+def saddle_events(X):
+    """Per-vertex counts of the alternating pattern (t1: below e and w, above
+    n and s; t2: the reverse) at vertices with all four neighbours, and of
+    the two-neighbour pattern on a 1 x W or H x 1 grid (next = e or s,
+    previous = w or n)."""
+    n, H, W = X.shape
+    out = np.zeros((H, W), np.int64)
+    if H == 1 or W == 1:
+        v = X.reshape(n, -1)
+        c, nxt, prv = v[:, 1:-1], v[:, 2:], v[:, :-2]
+        hits = ((c < nxt) & (c > prv)) | ((c > nxt) & (c < prv))
+        out.reshape(-1)[1:-1] = hits.sum(0)
+        return out
+    c = X[:, 1:-1, 1:-1]
+    e, w = X[:, 1:-1, 2:], X[:, 1:-1, :-2]
+    nn, s = X[:, :-2, 1:-1], X[:, 2:, 1:-1]
+    t1 = (c < e) & (c > nn) & (c < w) & (c > s)
+    t2 = (c > e) & (c < nn) & (c > w) & (c < s)
+    out[1:-1, 1:-1] = (t1 | t2).sum(0)
+    return out
+
+
+def mc_saddle(params, model, n, seed, batch=250_000):
+    rng = np.random.default_rng(seed)
+    H, W = np.asarray(params).shape[1:]
+    cnt = np.zeros((H, W), np.int64)
+    done = 0
+    while done < n:
+        m = min(batch, n - done)
+        cnt += saddle_events(sample_field(params, model, rng, m))
+        done += m
+    return cnt / n

@@ -40,9 +40,13 @@ def test_golden_closed_forms(orc, case):
     y, x = case["vertex"]
     pmin, pmax, st = orc.prob(p, MODEL_ID[case["model"]])
     assert st[y, x] == 0
-    assert abs(pmin[y, x] - float(Fraction(case["p_min"]))) < 1e-14
+    if "p_min" in case:
+        assert abs(pmin[y, x] - float(Fraction(case["p_min"]))) < 1e-14
     if "p_max" in case:
         assert abs(pmax[y, x] - float(Fraction(case["p_max"]))) < 1e-14
+    if "p_saddle" in case:
+        sad, _ = orc.saddle(p, MODEL_ID[case["model"]])
+        assert abs(sad[y, x] - float(Fraction(case["p_saddle"]))) < 1e-14
 
 
 @pytest.mark.parametrize("case", _golden(), ids=lambda c: c["name"])
@@ -72,19 +76,28 @@ def test_golden_values_by_symbolic_integration(case):
     nbrs = [dist(y0 + dy, x0 + dx) for dy, dx in ((0, 1), (-1, 0), (0, -1), (1, 0))
             if 0 <= y0 + dy < Hh and 0 <= x0 + dx < Ww]
     pts = sorted({lo1, hi1} | {q for n in nbrs for q in n[:2] if lo1 < q < hi1})
-    tot_min = tot_max = 0
+    tot_min = tot_max = tot_sad = 0
     for s, t in zip(pts[:-1], pts[1:]):
         mid = (s + t) / 2
         fmin = fmax = pdf1
+        gs = []
         for lo, hi, _, G in nbrs:
             g = 1 if mid < lo else (0 if mid > hi else G)
+            gs.append(g)
             fmin *= g
             fmax *= 1 - g
         tot_min += sp.integrate(sp.expand(fmin), (x, s, t))
         tot_max += sp.integrate(sp.expand(fmax), (x, s, t))
-    assert sp.nsimplify(tot_min) == sp.Rational(case["p_min"])
+        if len(gs) == 4:   # e, n, w, s: t1 = G F G F, t2 = F G F G
+            t1 = pdf1 * gs[0] * (1 - gs[1]) * gs[2] * (1 - gs[3])
+            t2 = pdf1 * (1 - gs[0]) * gs[1] * (1 - gs[2]) * gs[3]
+            tot_sad += sp.integrate(sp.expand(t1 + t2), (x, s, t))
+    if "p_min" in case:
+        assert sp.nsimplify(tot_min) == sp.Rational(case["p_min"])
     if "p_max" in case:
         assert sp.nsimplify(tot_max) == sp.Rational(case["p_max"])
+    if "p_saddle" in case:
+        assert sp.nsimplify(tot_sad) == sp.Rational(case["p_saddle"])
 
 
 # --------------------------------------------------------------------------
@@ -460,3 +473,72 @@ def test_gradient_identities(orc):
         P = orc.prob(p, 2, bins=5)[cptype - 1][1, 1]
         for (y, x) in ((1, 1), (0, 1), (1, 0), (1, 2), (2, 1)):
             assert abs((p[2:, y, x] * g[:, y, x]).sum() - P) < 1e-13
+
+
+# --------------------------------------------------------------------------
+# saddle probability (Eq. saddleProb)
+
+
+@pytest.mark.parametrize("model", [0, 1, 2])
+def test_saddle_exchangeable(orc, model):
+    """i.i.d. variables: t1 needs X_n, X_s < X_1 < X_e, X_w, one ordering in
+    5!/(2!2!) = 30, so P = 2/30 = 1/15 inside; on a line 2 * 1/3! = 1/3;
+    0 on the boundary of a 2D grid."""
+    rng = np.random.default_rng(70)
+    one = H_.random_params(model, 1, 1, rng, bins=5)
+    p = np.broadcast_to(one, (one.shape[0], 4, 5)).copy()
+    sad, _ = orc.saddle(p, model, bins=5)
+    ref = np.zeros((4, 5))
+    ref[1:-1, 1:-1] = 1.0 / 15
+    np.testing.assert_allclose(sad, ref, atol=1e-13)
+    line = np.broadcast_to(one, (one.shape[0], 1, 6)).copy()
+    sad, _ = orc.saddle(line, model, bins=5)
+    np.testing.assert_allclose(sad[0], [0, 1 / 3, 1 / 3, 1 / 3, 1 / 3, 0], atol=1e-13)
+    col = np.broadcast_to(one, (one.shape[0], 6, 1)).copy()
+    sad, _ = orc.saddle(col, model, bins=5)
+    np.testing.assert_allclose(sad[:, 0], [0, 1 / 3, 1 / 3, 1 / 3, 1 / 3, 0], atol=1e-13)
+
+
+@pytest.mark.parametrize("model", [0, 1, 2])
+def test_saddle_invariances(orc, model):
+    """X -> -X swaps t1 and t2; transposing the grid swaps the roles of the
+    axes (e <-> s, n <-> w), which also swaps t1 and t2: both leave P."""
+    rng = np.random.default_rng(71 + model)
+    p = H_.random_params(model, 6, 7, rng, bins=5)
+    sad, _ = orc.saddle(p, model, bins=5)
+    neg, _ = orc.saddle(H_.negate_params(p, model), model, bins=5)
+    tr, _ = orc.saddle(np.ascontiguousarray(p.transpose(0, 2, 1)), model, bins=5)
+    np.testing.assert_allclose(neg, sad, atol=1e-13)
+    np.testing.assert_allclose(tr.T, sad, atol=1e-13)
+
+
+@pytest.mark.parametrize("model", [0, 1, 2])
+def test_saddle_bruteforce_monte_carlo(orc, model):
+    rng = np.random.default_rng(81 + model)
+    p = H_.random_params(model, 4, 5, rng, bins=4, spread=0.6)
+    n = 2_000_000
+    mc = H_.mc_saddle(p, model, n, seed=500 + model)
+    sad, _ = orc.saddle(p, model, bins=4)
+    sig = np.sqrt(np.maximum(sad * (1 - sad), 1e-12) / n)
+    assert (np.abs(mc - sad) / sig).max() < 5.5
+
+
+def test_saddle_mvn_diagonal_quadrature(orc):
+    scipy_integrate = pytest.importorskip("scipy.integrate")
+    rng = np.random.default_rng(13)
+    mu = rng.normal(0, 0.3, (3, 3))
+    var = rng.uniform(0.2, 1.0, (3, 3))
+    offs = ((0, 0), (0, 1), (-1, 0), (0, -1), (1, 0))
+    prm = H_.mvn_params(3, 3, mu, lambda y, x, pr: np.diag(
+        [var[y + dy, x + dx] if p_ else 0 for (dy, dx), p_ in zip(offs, pr)]))
+    S = 400_000
+    _, _, _, _, hs = orc.mvn_mc_at(prm, [4], S, seed=5, with_saddle=True)
+    sd = np.sqrt(var)
+
+    def integrand(t):
+        v = math.exp(-0.5 * ((t - mu[1, 1]) / sd[1, 1]) ** 2) / (sd[1, 1] * math.sqrt(2 * math.pi))
+        c = [_phi((t - mu[1 + dy, 1 + dx]) / sd[1 + dy, 1 + dx]) for dy, dx in offs[1:]]
+        g = [1 - q for q in c]
+        return v * (g[0] * c[1] * g[2] * c[3] + c[0] * g[1] * c[2] * g[3])
+    p = scipy_integrate.quad(integrand, -20, 20, epsabs=1e-13, limit=200)[0]
+    assert abs(hs[0] / S - p) < 5 * math.sqrt(p * (1 - p) / S)
