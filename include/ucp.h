@@ -167,6 +167,21 @@ int ucp_probability(ucp_ctx *ctx, const float *ens, int N, int H, int W,
                     const ucp_model_desc *desc, unsigned cptypes, float *out_min,
                     float *out_max, uint8_t *vertex_status, ucp_stream stream);
 
+/* Saddle probability field (Eq. saddleProb): with the neighbours e, n, w, s
+ * as X_2..X_5, P_s = Pr[X_1 < X_e, X_1 > X_n, X_1 < X_w, X_1 > X_s]
+ * + Pr[X_1 > X_e, X_1 < X_n, X_1 > X_w, X_1 < X_s].  A vertex without all four
+ * neighbours has no alternating neighbourhood and gets 0, except on a 1 x W
+ * or H x 1 grid, where the two-neighbour form (Eq. 1D-saddleProb) is used:
+ * X_1 between its next (e, or s) and previous (w, or n) neighbour, either
+ * way round.  The boundary mode does not apply.  All four models
+ * (UCP_MVN_MC by Monte Carlo with the same sampling contract).  out_saddle:
+ * [H][W] device array; vertex_status may be NULL. */
+int ucp_saddle(ucp_ctx *ctx, const float *ens, int N, int H, int W, const ucp_model_desc *desc,
+               float *out_saddle, uint8_t *vertex_status, ucp_stream stream);
+int ucp_saddle_from_params(ucp_ctx *ctx, const float *params, int H, int W,
+                           const ucp_model_desc *desc, float *out_saddle,
+                           uint8_t *vertex_status, ucp_stream stream);
+
 /* Same as ucp_probability with HOST arrays: copies ens_host to a
  * context-owned device buffer, computes, copies the fields back and
  * synchronises the stream before returning.  Pinned host memory gives the

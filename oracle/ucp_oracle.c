@@ -811,21 +811,16 @@ int orc_mvn_mc_at(const double *params, int H, int W, int boundary, const int64_
       if (status) status[t] = (uint8_t)st;
       continue;
     }
-    if (boundary == 1 && k < 4) {
-      hits_min[t] = hits_max[t] = 0;
-      if (hits_saddle) hits_saddle[t] = 0;
-      near_ties[t] = 0;
-      if (status) status[t] = 0;
-      continue;
-    }
+    /* zero boundary mode: minimum and maximum are 0 where a neighbour is
+     * missing; the saddle and the flags are computed as usual */
     if (tr == 0.0) {
       int lt = 1, gt = 1;
       for (a = 1; a < nv; ++a) {
         lt &= mu[0] < mu[a];
         gt &= mu[0] > mu[a];
       }
-      hits_min[t] = lt ? S : 0;
-      hits_max[t] = gt ? S : 0;
+      hits_min[t] = (lt && !(boundary == 1 && k < 4)) ? S : 0;
+      hits_max[t] = (gt && !(boundary == 1 && k < 4)) ? S : 0;
       if (hits_saddle) {
         int t1 = saddle_ok, t2 = saddle_ok;
         for (a = 1; a < nv; ++a) {
@@ -895,8 +890,8 @@ int orc_mvn_mc_at(const double *params, int H, int W, int boundary, const int64_
         ties += (nv > 1 && dmin < tie_tol);
       }
     }
-    hits_min[t] = hmin;
-    hits_max[t] = hmax;
+    hits_min[t] = (boundary == 1 && k < 4) ? 0 : hmin;
+    hits_max[t] = (boundary == 1 && k < 4) ? 0 : hmax;
     if (hits_saddle) hits_saddle[t] = hsad;
     near_ties[t] = ties;
     if (status) status[t] = (uint8_t)st;

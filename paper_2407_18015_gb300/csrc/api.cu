@@ -10,6 +10,7 @@
 
 #include <new>
 
+#include "device.cuh"
 #include "launch.h"
 #include "ucp.h"
 #include "ucp_internal.h"
@@ -224,6 +225,53 @@ int ucp_probability(ucp_ctx *ctx, const float *ens, int N, int H, int W,
   if (g.err != cudaSuccess) return ucp_set_error(ctx, g.err);
   return probability_impl(ctx, ens, nullptr, N, H, W, desc, cptypes, out_min, out_max,
                           vertex_status, (cudaStream_t)stream);
+}
+
+static int saddle_impl(ucp_ctx *ctx, const float *ens, const float *params, int N, int H, int W,
+                       const ucp_model_desc *desc, float *out_saddle, uint8_t *vertex_status,
+                       cudaStream_t stream) {
+  Field f{};
+  f.ens = ens;
+  f.params = params;
+  f.out_saddle = out_saddle;
+  f.status = vertex_status;
+  f.plane = (long long)H * W;
+  f.N = N; f.H = H; f.W = W; f.B = desc->bins;
+  f.y0 = 0; f.y1 = H;
+  f.boundary = desc->boundary;
+  f.epan_scale = epan_scale(desc);
+  f.cptypes = kSaddle;
+  cudaError_t e;
+  if (desc->model == UCP_MVN_MC)
+    e = launch_mvn_mc(f, ens != nullptr, desc->mc_samples, desc->seed, desc->field_id, stream);
+  else
+    e = launch_closed(f, desc->model, ens != nullptr, stream);
+  return ucp_set_error(ctx, e);
+}
+
+int ucp_saddle(ucp_ctx *ctx, const float *ens, int N, int H, int W, const ucp_model_desc *desc,
+               float *out_saddle, uint8_t *vertex_status, ucp_stream stream) {
+  if (!ctx || !ens || !out_saddle) return UCP_ERR_ARG;
+  int rc = valid_desc(desc, true);
+  if (rc) return rc;
+  if ((rc = valid_shape(N, H, W))) return rc;
+  DeviceGuard g(ctx->device);
+  if (g.err != cudaSuccess) return ucp_set_error(ctx, g.err);
+  return saddle_impl(ctx, ens, nullptr, N, H, W, desc, out_saddle, vertex_status,
+                     (cudaStream_t)stream);
+}
+
+int ucp_saddle_from_params(ucp_ctx *ctx, const float *params, int H, int W,
+                           const ucp_model_desc *desc, float *out_saddle,
+                           uint8_t *vertex_status, ucp_stream stream) {
+  if (!ctx || !params || !out_saddle) return UCP_ERR_ARG;
+  int rc = valid_desc(desc, true);
+  if (rc) return rc;
+  if ((rc = valid_shape(1, H, W))) return rc;
+  DeviceGuard g(ctx->device);
+  if (g.err != cudaSuccess) return ucp_set_error(ctx, g.err);
+  return saddle_impl(ctx, nullptr, params, 1, H, W, desc, out_saddle, vertex_status,
+                     (cudaStream_t)stream);
 }
 
 int ucp_probability_host(ucp_ctx *ctx, const float *ens_host, int N, int H, int W,

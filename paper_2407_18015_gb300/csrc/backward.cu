@@ -379,7 +379,7 @@ struct HistView {
 struct NWalk {
   HistView v;
   int B, j;            // j: -1 before, B after
-  float lam, h, end, eleft, enext, S, slope, T;
+  float lam, h, ih, end, eleft, enext, S, slope, T;
   float C, Cstart, inbin;
 };
 
@@ -399,7 +399,7 @@ __device__ __forceinline__ void nwalk_advance(NWalk &n, float *rows_n, long long
     return;
   }
   if (n.j > 0) n.S -= n.v.mass(n.j - 1);
-  n.slope = n.v.mass(n.j) / n.h;
+  n.slope = n.v.mass(n.j) * n.ih;
   n.eleft = n.enext;
   n.enext = (n.j + 1 < n.B) ? fmaf((float)(n.j + 1), n.h, n.lam) : n.end;
 }
@@ -486,6 +486,7 @@ __device__ void hist_grad_vertex(const float *params, long long plane, long long
     n.lam = lo - lo1;
     n.B = (lo == hi) ? 0 : B;
     n.h = (lo == hi) ? 1.f : (hi - lo) / (float)B;
+    n.ih = frcp(n.h);
     n.end = (lo == hi) ? n.lam : hi - lo1;
     n.j = -1;
     n.S = T[i];
@@ -501,9 +502,9 @@ __device__ void hist_grad_vertex(const float *params, long long plane, long long
     }
     for (int g = 0; g <= B && n.enext <= 0.f && n.j < n.B; ++g) nwalk_advance(n, rn, plane, vi, wv);
   }
-  const float h1 = W1 / (float)B;
+  const float h1 = W1 / (float)B, ih1 = frcp(h1);
   int j1 = 0;
-  float p1 = cv.mass(0) / h1;
+  float p1 = cv.mass(0) * ih1;
   float e1 = (B > 1) ? h1 : W1;
   float own_acc = 0.f;
   float x0 = 0.f;
@@ -541,18 +542,18 @@ __device__ void hist_grad_vertex(const float *params, long long plane, long long
         n.C += A;
         if (n.j >= 0 && n.j < n.B) {
           // within-bin factor (e_{j+1} - x) / h
-          L3[3] = (n.enext - x0) / n.h;
-          R3[3] = (n.enext - x1) / n.h;
+          L3[3] = (n.enext - x0) * n.ih;
+          R3[3] = (n.enext - x1) * n.ih;
           n.inbin += len * p1 * bern_mean<4>(L3, R3);
         }
       }
     }
     if (x1 >= W1) break;
     if (e1 <= x1) {
-      own[(long long)cv.orig(j1) * plane + vi] = wv * own_acc / h1;
+      own[(long long)cv.orig(j1) * plane + vi] = wv * own_acc * ih1;
       own_acc = 0.f;
       ++j1;
-      p1 = (j1 < B) ? cv.mass(j1) / h1 : 0.f;
+      p1 = (j1 < B) ? cv.mass(j1) * ih1 : 0.f;
       e1 = (j1 + 1 < B) ? (float)(j1 + 1) * h1 : W1;
     }
 #pragma unroll
@@ -567,7 +568,7 @@ __device__ void hist_grad_vertex(const float *params, long long plane, long long
     }
     x0 = x1;
   }
-  if (j1 < B) own[(long long)cv.orig(j1) * plane + vi] = wv * own_acc / h1;
+  if (j1 < B) own[(long long)cv.orig(j1) * plane + vi] = wv * own_acc * ih1;
   for (int q = j1 + 1; q < B; ++q) own[(long long)cv.orig(q) * plane + vi] = 0.f;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {

@@ -87,11 +87,12 @@ struct TileOcc {
   static constexpr int value = MODEL == kUniform ? 5 : (MODEL == kEpan ? 4 : 3);
 };
 
-template <int MODEL, bool FROM_MEMBERS>
+template <int MODEL, bool FROM_MEMBERS, bool SADDLE = false>
 __global__ void __launch_bounds__(NTHREADS, TileOcc<MODEL>::value) tile_kernel(Field f, int tiles_x) {
   extern __shared__ float sm[];
   const int tile = blockIdx.x;
-  process_tile<MODEL, FROM_MEMBERS, TY>(f, f.y0 + (tile / tiles_x) * TY, (tile % tiles_x) * TX, sm);
+  process_tile<MODEL, FROM_MEMBERS, TY, SADDLE>(f, f.y0 + (tile / tiles_x) * TY,
+                                                (tile % tiles_x) * TX, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -128,7 +129,7 @@ cudaError_t launch_fit(const Field &f, int model, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int MODEL, bool FM>
+template <int MODEL, bool FM, bool SADDLE>
 static cudaError_t launch_tile(const Field &f, cudaStream_t s) {
   const int P = (MODEL == kHist) ? 2 + f.B : 2;
   const size_t smem = (size_t)P * HALO * sizeof(float);
@@ -138,7 +139,8 @@ static cudaError_t launch_tile(const Field &f, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
   if (!attr_set[dev]) {
-    e = cudaFuncSetAttribute(tile_kernel<MODEL, FM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(tile_kernel<MODEL, FM, SADDLE>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)((2 + kMaxBins) * HALO * sizeof(float)));
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
@@ -149,18 +151,27 @@ static cudaError_t launch_tile(const Field &f, cudaStream_t s) {
   if (tiles_y <= 0) return cudaSuccess;
   const long long tiles = (long long)tiles_x * tiles_y;
   if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-  tile_kernel<MODEL, FM><<<(int)tiles, NTHREADS, smem, s>>>(g, tiles_x);
+  tile_kernel<MODEL, FM, SADDLE><<<(int)tiles, NTHREADS, smem, s>>>(g, tiles_x);
   return cudaGetLastError();
 }
 
-cudaError_t launch_closed(const Field &f, int model, bool from_members, cudaStream_t s) {
-  if (model == kUniform) return from_members ? launch_tile<kUniform, true>(f, s)
-                                             : launch_tile<kUniform, false>(f, s);
-  if (model == kEpan) return from_members ? launch_tile<kEpan, true>(f, s)
-                                          : launch_tile<kEpan, false>(f, s);
-  if (model == kHist) return from_members ? launch_tile<kHist, true>(f, s)
-                                          : launch_tile<kHist, false>(f, s);
+template <bool SADDLE>
+static cudaError_t launch_closed_t(const Field &f, int model, bool fm, cudaStream_t s) {
+  if (model == kUniform) return fm ? launch_tile<kUniform, true, SADDLE>(f, s)
+                                   : launch_tile<kUniform, false, SADDLE>(f, s);
+  if (model == kEpan) return fm ? launch_tile<kEpan, true, SADDLE>(f, s)
+                                : launch_tile<kEpan, false, SADDLE>(f, s);
+  if (model == kHist) return fm ? launch_tile<kHist, true, SADDLE>(f, s)
+                                : launch_tile<kHist, false, SADDLE>(f, s);
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_closed(const Field &f, int model, bool from_members, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (f.cptypes & (kMin | kMax)) e = launch_closed_t<false>(f, model, from_members, s);
+  if (e == cudaSuccess && (f.cptypes & kSaddle))
+    e = launch_closed_t<true>(f, model, from_members, s);
+  return e;
 }
 
 cudaError_t launch_eb_params(const float *d, float eb, long long n, float *params,

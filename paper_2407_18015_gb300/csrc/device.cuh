@@ -22,7 +22,7 @@
 namespace ucp {
 
 constexpr int kUniform = 0, kEpan = 1, kHist = 2, kMvn = 3;
-constexpr unsigned kMin = 1u, kMax = 2u;
+constexpr unsigned kMin = 1u, kMax = 2u, kSaddle = 4u;
 constexpr int kMaxBins = 64;
 
 enum : uint8_t {
@@ -445,6 +445,168 @@ __device__ __forceinline__ void epan_vertex(EpanParams c, const EpanParams *nb,
 }
 
 // ---------------------------------------------------------------------------
+// saddle: products that mix survivals and CDFs (Eq. saddleProb)
+//
+// sg[i] = +1: the factor is the survival G_i (X_1 < X_i), -1: the CDF F_i
+// (X_1 > X_i), 0: absent (the constant 1).  A survival factor is 1 below its
+// support start and 0 above its end; a CDF factor is 0 below the start and 1
+// above the end.  So the product vanishes outside [L, R], L = the largest
+// start among CDF factors (and the centre's own), R = the smallest end among
+// survival factors; inside, the breakpoints are the survival factors' starts
+// and the CDF factors' ends.
+
+// uniform: t = int pdf_1 prod_i f_i in the centre's frame (origin a1)
+__device__ __forceinline__ float uniform_mixed(UniParams c, const UniParams *nb, const int *sg) {
+  if (c.a == c.b) {
+    const float v = c.a;
+    float p = 1.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (sg[i] == 0) continue;
+      const float a = nb[i].a, b = nb[i].b;
+      float q;
+      if (a == b) q = sg[i] > 0 ? (a > v ? 1.f : 0.f) : (a < v ? 1.f : 0.f);
+      else {
+        const float r = frcp(b - a);
+        q = sg[i] > 0 ? (b - v) * r : (v - a) * r;
+        q = fminf(fmaxf(q, 0.f), 1.f);
+      }
+      p *= q;
+    }
+    return p;
+  }
+  const float W1 = c.b - c.a;
+  float L = 0.f, R = W1;
+  float bp[4], al[4], be[4], sl[4];
+  int kind[4];  // 0 constant 1, 1 survival, 2 CDF
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    kind[i] = 0; al[i] = 0.f; be[i] = 0.f; sl[i] = 0.f; bp[i] = kFar;
+    if (sg[i] == 0) continue;
+    const float a = nb[i].a - c.a, b = nb[i].b - c.a;
+    if (sg[i] > 0) {
+      R = fminf(R, b);
+      if (nb[i].a != nb[i].b) { kind[i] = 1; bp[i] = a; }
+    } else {
+      L = fmaxf(L, a);
+      if (nb[i].a != nb[i].b) { kind[i] = 2; bp[i] = b; }
+    }
+    al[i] = a; be[i] = b;
+    sl[i] = nb[i].a != nb[i].b ? frcp(nb[i].b - nb[i].a) : 0.f;
+  }
+  if (!(R > L)) return 0.f;
+  float t[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) t[i] = fminf(fmaxf(bp[i], L), R);
+  float none[1][4];
+  sort4<0>(t, none);
+  const float x[6] = {L, t[0], t[1], t[2], t[3], R};
+  Kahan acc;
+  float Lv[4], Rv[4];
+#pragma unroll
+  for (int j = 0; j <= 4; ++j) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float x0 = x[j], x1 = x[j + 1];
+      if (kind[i] == 1) {
+        Lv[i] = fminf(fmaxf((be[i] - x0) * sl[i], 0.f), 1.f);
+        Rv[i] = fminf(fmaxf((be[i] - x1) * sl[i], 0.f), 1.f);
+      } else if (kind[i] == 2) {
+        Lv[i] = fminf(fmaxf((x0 - al[i]) * sl[i], 0.f), 1.f);
+        Rv[i] = fminf(fmaxf((x1 - al[i]) * sl[i], 0.f), 1.f);
+      } else {
+        Lv[i] = Rv[i] = 1.f;
+      }
+    }
+    acc.add((x[j + 1] - x[j]) * bern_mean<4>(Lv, Rv));
+  }
+  return acc.get() * frcp(W1);
+}
+
+// Epanechnikov: the same, 8-point Gauss-Legendre on each piece (origin m1);
+// F_i(x) = epan_surv((m_i - x)/w_i) by the kernel's symmetry
+__device__ __forceinline__ float epan_mixed(EpanParams c, const EpanParams *nb, const int *sg) {
+  if (c.w == 0.f) {
+    const float v = c.m;
+    float p = 1.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (sg[i] == 0) continue;
+      float q;
+      if (nb[i].w == 0.f) q = sg[i] > 0 ? (nb[i].m > v ? 1.f : 0.f) : (nb[i].m < v ? 1.f : 0.f);
+      else q = epan_surv(sg[i] > 0 ? (v - nb[i].m) / nb[i].w : (nb[i].m - v) / nb[i].w);
+      p *= q;
+    }
+    return p;
+  }
+  const float w1 = c.w;
+  float L = -w1, R = w1;
+  float bp[4], d[4], iw[4], sgn[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    bp[i] = kFar; d[i] = 0.f; iw[i] = 0.f; sgn[i] = 0.f;
+    if (sg[i] == 0) continue;
+    const float dn = nb[i].m - c.m, wn = nb[i].w;
+    if (sg[i] > 0) {
+      R = fminf(R, dn + wn);
+      if (wn > 0.f) { bp[i] = dn - wn; d[i] = dn; iw[i] = frcp(wn); sgn[i] = 1.f; }
+    } else {
+      L = fmaxf(L, dn - wn);
+      if (wn > 0.f) { bp[i] = dn + wn; d[i] = dn; iw[i] = frcp(wn); sgn[i] = -1.f; }
+    }
+  }
+  if (!(R > L)) return 0.f;
+  float t[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) t[i] = fminf(fmaxf(bp[i], L), R);
+  float none[1][4];
+  sort4<0>(t, none);
+  const float x[6] = {L, t[0], t[1], t[2], t[3], R};
+  const float iw1 = frcp(w1), c1 = 0.75f * iw1;
+  Kahan acc;
+#pragma unroll
+  for (int j = 0; j <= 4; ++j) {
+    const float half = 0.5f * (x[j + 1] - x[j]), mid = 0.5f * (x[j] + x[j + 1]);
+    float sacc = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float xi = (q < 4) ? -kGLx[3 - q] : kGLx[q - 4];
+      const float wi = (q < 4) ? kGLw[3 - q] : kGLw[q - 4];
+      const float xx = fmaf(half, xi, mid);
+      const float u1 = xx * iw1;
+      float f = c1 * fmaxf(fmaf(-u1, u1, 1.f), 0.f);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (sgn[i] != 0.f) f *= epan_surv(sgn[i] * (xx - d[i]) * iw[i]);
+      sacc = fmaf(wi, f, sacc);
+    }
+    acc.add(sacc * half);
+  }
+  return acc.get();
+}
+
+// saddle signs of the four slots (e, n, w, s) for t1, or all zero when the
+// vertex has no saddle neighbourhood: all four neighbours present -> G F G F;
+// a 1 x W (H x 1) grid with both line neighbours -> next (e / s) G, previous
+// (w / n) F
+__device__ __forceinline__ bool saddle_signs(const bool *present, int H, int W, int *sg) {
+  const int k = (int)present[0] + present[1] + present[2] + present[3];
+  sg[0] = sg[1] = sg[2] = sg[3] = 0;
+  if (k == 4) {
+    sg[0] = 1; sg[1] = -1; sg[2] = 1; sg[3] = -1;
+    return true;
+  }
+  if (k == 2 && (H == 1 || W == 1)) {
+    if (present[0]) sg[0] = 1;
+    if (present[2]) sg[2] = -1;
+    if (present[3]) sg[3] = 1;
+    if (present[1]) sg[1] = -1;
+    return true;
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------------------
 // closed-form integration, histogram model (breakpoint merge)
 
 // A neighbour's survival G(x) (mixture form) as a walk over its segments:
@@ -508,10 +670,13 @@ struct HistWalk {
 // its survival is 0, before it its CDF is 0, so both integrals can run over
 // the centre's whole support.  Pieces are summed per centre bin and the bin
 // sums (times the bin density) with Kahan compensation.
-template <int WS>
+// SADDLE = false: (pmin, pmax) = (int pdf prod G, int pdf prod F).
+// SADDLE = true:  (pmin, pmax) = (t1, t2) with factor i = G_i if sg[i] > 0
+// else F_i for t1, and the other one for t2 (absent neighbours are 1 in both).
+template <int WS, bool SADDLE = false>
 __device__ __forceinline__ void hist_walk(const float *w, int coff, int B, float W1,
                                           HistWalk *nw, const float *T, unsigned want,
-                                          float &pmin, float &pmax) {
+                                          float &pmin, float &pmax, const int *sg = nullptr) {
   const float h1 = W1 / (float)B, ih1 = frcp(h1);
   int j1 = 0;
   float e1 = (B > 1) ? h1 : W1;
@@ -534,8 +699,21 @@ __device__ __forceinline__ void hist_walk(const float *w, int coff, int B, float
       Fr[i] = fmaxf(T[i] - Gr[i], 0.f);
     }
     const float len = x1 - x0;
-    if (want & kMin) bmin = fmaf(len, bern_mean<4>(Gl, Gr), bmin);
-    if (want & kMax) bmax = fmaf(len, bern_mean<4>(Fl, Fr), bmax);
+    if constexpr (SADDLE) {
+      float L1[4], R1[4], L2[4], R2[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        L1[i] = sg[i] > 0 ? Gl[i] : Fl[i];
+        R1[i] = sg[i] > 0 ? Gr[i] : Fr[i];
+        L2[i] = sg[i] > 0 ? Fl[i] : Gl[i];
+        R2[i] = sg[i] > 0 ? Fr[i] : Gr[i];
+      }
+      bmin = fmaf(len, bern_mean<4>(L1, R1), bmin);
+      bmax = fmaf(len, bern_mean<4>(L2, R2), bmax);
+    } else {
+      if (want & kMin) bmin = fmaf(len, bern_mean<4>(Gl, Gr), bmin);
+      if (want & kMax) bmax = fmaf(len, bern_mean<4>(Fl, Fr), bmax);
+    }
     const bool last = x1 >= W1;
     if (last || e1 <= x1) {
       const float p1 = w[coff + j1 * WS] * ih1;

@@ -13,13 +13,14 @@ struct Field {
   const float *params;  // [P][H][W] parameters, or nullptr
   float *out_min;       // [H][W] or nullptr
   float *out_max;       // [H][W] or nullptr
+  float *out_saddle;    // [H][W] or nullptr
   uint8_t *status;      // [H][W] or nullptr
   long long plane;      // H * W
   int N, H, W, B;
   int y0, y1;           // rows [y0, y1) are computed (the arrays cover all H rows)
   int boundary;         // 0 in-grid neighbours, 1 zero at the boundary
   float epan_scale;
-  unsigned cptypes;     // bit 1 min, bit 2 max
+  unsigned cptypes;     // bit 1 min, bit 2 max, bit 4 saddle
   bool vec4;            // members may be read as aligned float4 (W % 4 == 0, 16B base)
 };
 

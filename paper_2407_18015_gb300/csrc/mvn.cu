@@ -15,16 +15,40 @@
 
 namespace ucp {
 
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+// Philox4x32-10 key schedule (Weyl sequence), computed once per vertex
+struct PhiloxKeys {
+  uint32_t k0[10], k1[10];
+  __device__ __forceinline__ PhiloxKeys(uint32_t a, uint32_t b) {
 #pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
+    for (int r = 0; r < 10; ++r) {
+      k0[r] = a;
+      k1[r] = b;
+      a += 0x9E3779B9u;
+      b += 0xBB67AE85u;
+    }
   }
-  return c;
+};
+
+__device__ __forceinline__ void philox_round(uint4 &c, uint32_t k0, uint32_t k1) {
+  const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+  const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+  c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+}
+
+// The two blocks of one sample: counters (s, v, field, 0) and (s, v, field, 1)
+// differ only in the last word, so the first round's products are shared.
+__device__ __forceinline__ void philox_pair(uint32_t s, uint32_t v, uint32_t field,
+                                            const PhiloxKeys &K, uint4 &r0, uint4 &r1) {
+  const uint32_t hi0 = __umulhi(0xD2511F53u, s), lo0 = 0xD2511F53u * s;
+  const uint32_t hi1 = __umulhi(0xCD9E8D57u, field), lo1 = 0xCD9E8D57u * field;
+  const uint32_t a = hi1 ^ v ^ K.k0[0];
+  r0 = make_uint4(a, lo1, hi0 ^ K.k1[0], lo0);
+  r1 = make_uint4(a, lo1, hi0 ^ 1u ^ K.k1[0], lo0);
+#pragma unroll
+  for (int r = 1; r < 10; ++r) {
+    philox_round(r0, K.k0[r], K.k1[r]);
+    philox_round(r1, K.k0[r], K.k1[r]);
+  }
 }
 
 __device__ __forceinline__ float u01(uint32_t r) {
@@ -32,12 +56,18 @@ __device__ __forceinline__ float u01(uint32_t r) {
   return fmaf(__uint2float_rn(r >> 8), 0x1p-24f, 0x1p-25f);
 }
 
+// Box-Muller: radius sqrt(-2 ln ua), angle 2 pi ub.  The angle is taken as
+// pi + t with t = 2 pi (ub - 1/2) in [-pi, pi), where the hardware sine and
+// cosine are accurate to ~4e-7 absolute: cos(2 pi ub) = -cos t,
+// sin(2 pi ub) = -sin t.  The logarithm keeps full accuracy (its error is
+// not bounded relative to the radius near ub -> 1).
 __device__ __forceinline__ void box_muller(float ua, float ub, float &z0, float &z1) {
-  const float rad = sqrtf(-2.f * logf(ua));
+  const float v = -2.f * logf(ua);
+  const float rad = v * rsqrtf(v);
   float s, c;
-  sincospif(2.f * ub, &s, &c);
-  z0 = rad * c;
-  z1 = rad * s;
+  __sincosf(6.283185307179586f * (ub - 0.5f), &s, &c);
+  z0 = -rad * c;
+  z1 = -rad * s;
 }
 
 // Slots of the variables: 0 = v, 1..4 = e, n, w, s.  Returns the number of
@@ -230,21 +260,35 @@ __global__ void __launch_bounds__(256) mvn_mc_kernel(Field f, int S, uint32_t k0
       }
     }
     uint8_t st = nf ? V_NONFINITE : 0;
-    float pmin = 0.f, pmax = 0.f;
+    float pmin = 0.f, pmax = 0.f, psad = 0.f;
+    // saddle sign of each present variable (+1: t1 wants x_v < x_n); a vertex
+    // without a saddle neighbourhood counts no saddle hits
+    float ssg[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    const bool line = (f.H == 1 || f.W == 1) && nv == 3;
+    const bool has_saddle = (nv == 5) || line;
+#pragma unroll
+    for (int a = 1; a < 5; ++a)
+      if (a < nv) {
+        const int sl = slot[a];  // 1 e, 2 n, 3 w, 4 s
+        ssg[a] = (nv == 5) ? ((sl == 1 || sl == 3) ? 1.f : -1.f)
+                           : ((sl == 1 || sl == 4) ? 1.f : -1.f);
+      }
+    const bool zero_mm = f.boundary == 1 && nv < 5;
     if (nf) {
-      pmin = pmax = __int_as_float(0x7fc00000);
-    } else if (f.boundary == 1 && nv < 5) {
-      pmin = pmax = 0.f;
+      pmin = pmax = psad = __int_as_float(0x7fc00000);
     } else if (tr == 0.f) {
-      bool lt = true, gt = true;
+      bool lt = true, gt = true, t1 = has_saddle, t2 = has_saddle;
 #pragma unroll
       for (int a = 1; a < 5; ++a)
         if (a < nv) {
           lt &= mu[0] < mu[a];
           gt &= mu[0] > mu[a];
+          t1 &= ssg[a] > 0.f ? mu[0] < mu[a] : mu[0] > mu[a];
+          t2 &= ssg[a] > 0.f ? mu[0] > mu[a] : mu[0] < mu[a];
         }
-      pmin = lt ? 1.f : 0.f;
-      pmax = gt ? 1.f : 0.f;
+      pmin = (lt && !zero_mm) ? 1.f : 0.f;
+      pmax = (gt && !zero_mm) ? 1.f : 0.f;
+      psad = (t1 || t2) ? 1.f : 0.f;
       st |= V_DEGENERATE;
     } else {
       float L[5][5];
@@ -263,7 +307,7 @@ __global__ void __launch_bounds__(256) mvn_mc_kernel(Field f, int S, uint32_t k0
         st |= ok ? V_JITTER : V_CHOLFAIL;
       }
       if (!ok) {
-        pmin = pmax = __int_as_float(0x7fc00000);
+        pmin = pmax = psad = __int_as_float(0x7fc00000);
       } else {
         // y_n = x_0 - x_n = D_n + sum_b M[n][b] z_b
         float D[5], M[5][5];
@@ -273,18 +317,19 @@ __global__ void __launch_bounds__(256) mvn_mc_kernel(Field f, int S, uint32_t k0
 #pragma unroll
           for (int b = 0; b < 5; ++b) M[n][b] = (b == 0 ? L[0][0] : 0.f) - L[n][b];
         }
-        unsigned cmin = 0, cmax = 0;
+        unsigned cmin = 0, cmax = 0, csad = 0;
         const int iters = (S + 31) >> 5;
         const uint32_t vid = (uint32_t)v;
+        const PhiloxKeys K(k0, k1);
         for (int it = 0; it < iters; ++it) {
           const int s = (it << 5) + lane;
-          const uint4 r0 = philox4x32_10(make_uint4((uint32_t)s, vid, field, 0u), k0, k1);
-          const uint4 r1 = philox4x32_10(make_uint4((uint32_t)s, vid, field, 1u), k0, k1);
+          uint4 r0, r1;
+          philox_pair((uint32_t)s, vid, field, K, r0, r1);
           float z[6];
           box_muller(u01(r0.x), u01(r0.y), z[0], z[1]);
           box_muller(u01(r0.z), u01(r0.w), z[2], z[3]);
           box_muller(u01(r1.x), u01(r1.y), z[4], z[5]);
-          bool lt = true, gt = true;
+          bool lt = true, gt = true, t1 = has_saddle, t2 = has_saddle;
 #pragma unroll
           for (int n = 1; n < 5; ++n) {
             if (n < nv) {
@@ -293,19 +338,26 @@ __global__ void __launch_bounds__(256) mvn_mc_kernel(Field f, int S, uint32_t k0
               for (int b = 0; b <= n; ++b) yv = fmaf(M[n][b], z[b], yv);
               lt &= yv < 0.f;
               gt &= yv > 0.f;
+              // y = x_v - x_n: t1 wants x_v < x_n where the sign is +1
+              const float sy = ssg[n] * yv;
+              t1 &= sy < 0.f;
+              t2 &= sy > 0.f;
             }
           }
           const bool valid = s < S;
           cmin += __popc(__ballot_sync(0xffffffffu, valid && lt));
           cmax += __popc(__ballot_sync(0xffffffffu, valid && gt));
+          if (f.cptypes & kSaddle) csad += __popc(__ballot_sync(0xffffffffu, valid && (t1 || t2)));
         }
-        pmin = (float)cmin / (float)S;
-        pmax = (float)cmax / (float)S;
+        pmin = zero_mm ? 0.f : (float)cmin / (float)S;
+        pmax = zero_mm ? 0.f : (float)cmax / (float)S;
+        psad = (float)csad / (float)S;
       }
     }
     if (lane == 0) {
       if ((f.cptypes & kMin) && f.out_min) f.out_min[v] = pmin;
       if ((f.cptypes & kMax) && f.out_max) f.out_max[v] = pmax;
+      if ((f.cptypes & kSaddle) && f.out_saddle) f.out_saddle[v] = psad;
       if (f.status) f.status[v] = st;
     }
   }

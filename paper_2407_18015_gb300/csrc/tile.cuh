@@ -197,7 +197,9 @@ __device__ __forceinline__ uint8_t check_params(const float *sm, int l, int B, f
 // One tile of TYv x 32 vertices: phase 1 stages the parameters of the tile
 // and its one-vertex halo ((TYv + 2) x 34) in shared memory -- fitted from the
 // members or loaded -- and phase 2 integrates every vertex of the tile.
-template <int MODEL, bool FROM_MEMBERS, int TYv>
+// SADDLE selects the saddle probability (Eq. saddleProb) instead of the
+// minimum / maximum: a separate instance, so neither pays for the other.
+template <int MODEL, bool FROM_MEMBERS, int TYv, bool SADDLE = false>
 __device__ __forceinline__ void process_tile(const Field &f, int ty0, int tx0, float *sm) {
   constexpr int TY = TYv, TX = 32, HY = TYv + 2, HX = TX + 2, HALO = HY * HX;
   // rows beyond y1 are neither computed nor needed (row y1 is a neighbour)
@@ -256,26 +258,39 @@ __device__ __forceinline__ void process_tile(const Field &f, int ty0, int tx0, f
       T[i] = 1.f;
       if (present[i]) st |= check_params<MODEL, HALO>(sm, nl[i], f.B, T[i]) & (V_NONFINITE | V_BAD);
     }
-    float pmin = 0.f, pmax = 0.f;
-    if (st & (V_NONFINITE | V_BAD)) {
-      pmin = pmax = qnan();
-    } else if (f.boundary == 1 && k < 4) {
-      pmin = pmax = 0.f;
+    float pmin = 0.f, pmax = 0.f, psad = 0.f;
+    int sg[4], sg2[4];
+    const bool bad = (st & (V_NONFINITE | V_BAD)) != 0;
+    const bool has_saddle = SADDLE && saddle_signs(present, f.H, f.W, sg);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) sg2[i] = SADDLE ? -sg[i] : 0;
+    if (bad) {
+      pmin = pmax = psad = qnan();
     } else if (MODEL == kUniform) {
       UniParams cp{sm[l], sm[HALO + l]}, nb[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) nb[i] = UniParams{sm[nl[i]], sm[HALO + nl[i]]};
-      uniform_vertex(cp, nb, present, f.cptypes, pmin, pmax);
+      if constexpr (!SADDLE) {
+        if (!(f.boundary == 1 && k < 4)) uniform_vertex(cp, nb, present, f.cptypes, pmin, pmax);
+      } else if (has_saddle) {
+        psad = uniform_mixed(cp, nb, sg) + uniform_mixed(cp, nb, sg2);
+      }
     } else if (MODEL == kEpan) {
       EpanParams cp{sm[l], sm[HALO + l]}, nb[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) nb[i] = EpanParams{sm[nl[i]], sm[HALO + nl[i]]};
-      epan_vertex(cp, nb, present, f.cptypes, pmin, pmax);
+      if constexpr (!SADDLE) {
+        if (!(f.boundary == 1 && k < 4)) epan_vertex(cp, nb, present, f.cptypes, pmin, pmax);
+      } else if (has_saddle) {
+        psad = epan_mixed(cp, nb, sg) + epan_mixed(cp, nb, sg2);
+      }
     } else {
       const int B = f.B;
       const float lo1 = sm[l], hi1 = sm[HALO + l];
+      const bool do_mm = !SADDLE && !(f.boundary == 1 && k < 4);
+      const bool do_sad = SADDLE && has_saddle;
       if (lo1 == hi1) {
-        float gm = Tc, gM = Tc;
+        float gm = Tc, gM = Tc, t1 = Tc, t2 = Tc;
         for (int i = 0; i < 4; ++i) {
           if (!present[i]) continue;
           float gt, lt;
@@ -283,10 +298,17 @@ __device__ __forceinline__ void process_tile(const Field &f, int ty0, int tx0, f
                         gt, lt);
           gm *= gt;
           gM *= lt;
+          if (sg[i] != 0) {
+            t1 *= sg[i] > 0 ? gt : lt;
+            t2 *= sg[i] > 0 ? lt : gt;
+          }
         }
-        pmin = gm;
-        pmax = gM;
-      } else {
+        if (do_mm) {
+          pmin = gm;
+          pmax = gM;
+        }
+        if (do_sad) psad = t1 + t2;
+      } else if (do_mm || do_sad) {
         HistWalk nw[4];
         float Tw[4];
 #pragma unroll
@@ -305,12 +327,22 @@ __device__ __forceinline__ void process_tile(const Field &f, int ty0, int tx0, f
             h.init(nl[i], B, lo - lo1, (hi - lo) / (float)B, hi - lo1, T[i]);
           for (int g = 0; g <= B && h.nx <= 0.f && h.k < h.B; ++g) h.advance<HALO>(sm + 2 * HALO);
         }
-        hist_walk<HALO>(sm + 2 * HALO, l, B, hi1 - lo1, nw, Tw, f.cptypes, pmin, pmax);
+        if constexpr (!SADDLE) {
+          hist_walk<HALO>(sm + 2 * HALO, l, B, hi1 - lo1, nw, Tw, f.cptypes, pmin, pmax);
+        } else {
+          float t1, t2;
+          hist_walk<HALO, true>(sm + 2 * HALO, l, B, hi1 - lo1, nw, Tw, 0u, t1, t2, sg);
+          psad = t1 + t2;
+        }
       }
     }
     const long long gi = (long long)gy * f.W + gx;
-    if ((f.cptypes & kMin) && f.out_min) f.out_min[gi] = pmin;
-    if ((f.cptypes & kMax) && f.out_max) f.out_max[gi] = pmax;
+    if constexpr (SADDLE) {
+      if (f.out_saddle) f.out_saddle[gi] = psad;
+    } else {
+      if ((f.cptypes & kMin) && f.out_min) f.out_min[gi] = pmin;
+      if ((f.cptypes & kMax) && f.out_max) f.out_max[gi] = pmax;
+    }
     if (f.status) f.status[gi] = st;
   }
 }

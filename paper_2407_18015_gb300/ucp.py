@@ -75,6 +75,8 @@ def lib():
                 "ucp_probability": ([_P, _P, _I, _I, _I, D, ctypes.c_uint, _P, _P, _P, _P], _I),
                 "ucp_probability_host": ([_P, _P, _I, _I, _I, D, ctypes.c_uint, _P, _P, _P, _P],
                                          _I),
+                "ucp_saddle": ([_P, _P, _I, _I, _I, D, _P, _P, _P], _I),
+                "ucp_saddle_from_params": ([_P, _P, _I, _I, D, _P, _P, _P], _I),
                 "ucp_params_from_error_bound": ([_P, _P, ctypes.c_float, _I, _I, _P, _P], _I),
                 "ucp_backward": ([_P, _P, _I, _I, D, _I, _P, _P, _P], _I),
                 "ucp_backward_static": ([_P, _I, _I, D, _I, _P, _P, _P], _I),
@@ -194,6 +196,24 @@ def ucp_probability(ctx, ens, desc, cptypes, out_min, out_max, vertex_status=Non
         _ptr(out_min, torch.float32, name="out_min"), _ptr(out_max, torch.float32, name="out_max"),
         _ptr(vertex_status, torch.uint8, name="vertex_status"), _stream(stream, ens.device))
     _check(rc, "ucp_probability", ctx)
+
+
+def ucp_saddle(ctx, ens, desc, out_saddle, vertex_status=None, stream=None):
+    N, H, W = ens.shape
+    rc = lib().ucp_saddle(ctx, _ptr(ens, torch.float32, name="ens"), N, H, W, ctypes.byref(desc),
+                          _ptr(out_saddle, torch.float32, name="out_saddle"),
+                          _ptr(vertex_status, torch.uint8, name="vertex_status"),
+                          _stream(stream, ens.device))
+    _check(rc, "ucp_saddle", ctx)
+
+
+def ucp_saddle_from_params(ctx, params, desc, out_saddle, vertex_status=None, stream=None):
+    _, H, W = params.shape
+    rc = lib().ucp_saddle_from_params(
+        ctx, _ptr(params, torch.float32, name="params"), H, W, ctypes.byref(desc),
+        _ptr(out_saddle, torch.float32, name="out_saddle"),
+        _ptr(vertex_status, torch.uint8, name="vertex_status"), _stream(stream, params.device))
+    _check(rc, "ucp_saddle_from_params", ctx)
 
 
 def ucp_probability_host(ctx, ens_host, desc, cptypes, out_min_host, out_max_host,
@@ -317,6 +337,20 @@ class Context:
         pmin, pmax, st = self._outs(H, W, params.device, cptypes)
         ucp_probability_from_params(self.handle, params, desc, cptypes, pmin, pmax, st)
         return pmin, pmax, st
+
+    def saddle(self, ens, desc):
+        _, H, W = ens.shape
+        out = torch.empty((H, W), dtype=torch.float32, device=ens.device)
+        st = torch.empty((H, W), dtype=torch.uint8, device=ens.device)
+        ucp_saddle(self.handle, ens, desc, out, st)
+        return out, st
+
+    def saddle_from_params(self, params, desc):
+        _, H, W = params.shape
+        out = torch.empty((H, W), dtype=torch.float32, device=params.device)
+        st = torch.empty((H, W), dtype=torch.uint8, device=params.device)
+        ucp_saddle_from_params(self.handle, params, desc, out, st)
+        return out, st
 
     def backward(self, params, desc, cptype, weight):
         Q = desc.bins if desc.model == UCP_HISTOGRAM else 2
