@@ -165,6 +165,14 @@ HIST_FLOPS_PER_PIECE = 5 + 16 + 2 * (24 + 10 + 3)
 EPAN_FLOPS_PER_VERTEX_TYPE = 5 * 8 * (5 + 2 * 9 + 4)
 
 
+# DRAM bytes (read + write) per launch of each headline kernel from the ncu
+# capture summarised in profiles/tile_kernels_1024x1024x20.md; None once a
+# kernel has changed since its counters were taken
+TRAFFIC_BYTES = {"uniform": 83.920384e6 + 4.575744e6,
+                 "epanechnikov": 83.952640e6 + 4.481792e6,
+                 "histogram": 84.071424e6 + 5.210368e6}
+
+
 def work_of(model, N, HW, params=None, bins=BINS2):
     if model == "uniform":
         return "hbm", (4.0 * N + 8.0) * HW
@@ -343,7 +351,8 @@ def run_ours(args):
     dom = max(shares, key=shares.get)
     rf = dict(per_model[dom]["roofline"])
     rf["kernel"] = f"tile_kernel<{dom}, from members>"
-    rf["traffic"] = None
+    rf["traffic"] = TRAFFIC_BYTES.get(dom)
+    rf["traffic_source"] = "profiles/tile_kernels_1024x1024x20.md (ncu dram__bytes_read/write)"
     rf["peak_source"] = ("MEASURED_PEAKS.json hbm_gbs" if rf["bound"] == "hbm" else
                          f"152 SMs x 128 FP32 lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz")
     rf["share"] = shares[dom] / sum(shares.values())
