@@ -615,51 +615,37 @@ __device__ __forceinline__ bool saddle_signs(const bool *present, int H, int W, 
 // neighbour is the constant 1 (S = 1, slope 0, never advances); its "total"
 // is set to 2 so that the CDF complement T - G is 1 as well.
 struct HistWalk {
-  int off;          // shared-memory index of the neighbour's first mass
-  int B, k;         // k: -1 before the support, B after it
+  int ptr;          // shared-memory index of the next bin's mass
+  int left;         // edges still to cross (B + 1 before the support, 0 after)
+  float kf;         // index of the next edge
   float lam, h, invh, end;  // local support start, bin width, 1/h, local end
   float el, nx, S, sl;      // current segment: left edge, next edge, G(el), slope
+  bool point;       // a point mass: G jumps from T to 0 at its only edge
   __device__ __forceinline__ void init_absent() {
-    off = 0; B = 0; k = 0; lam = kFar; h = 1.f; invh = 0.f; end = kFar;
-    el = 0.f; nx = kFar; S = 1.f; sl = 0.f;
+    ptr = 0; left = 0; kf = 0.f; lam = kFar; h = 1.f; invh = 0.f; end = kFar;
+    el = 0.f; nx = kFar; S = 1.f; sl = 0.f; point = false;
   }
   __device__ __forceinline__ void init(int off_, int B_, float lam_, float h_, float end_,
                                        float T) {
-    off = off_; B = B_; k = -1;
+    ptr = off_; left = B_ + 1; kf = 0.f;
     lam = lam_; h = h_; invh = B_ > 0 ? frcp(h_) : 0.f; end = end_;
-    el = -kFar; nx = lam_; S = T; sl = 0.f;
+    el = -kFar; nx = lam_; S = T; sl = 0.f; point = B_ == 0;
   }
-  // move to the next segment; G is continuous at a bin edge, so the new left
-  // value is the current segment's value there (a point mass jumps to 0)
+  // cross the next edge, where G has the value g (G is continuous at a bin
+  // edge; a point mass drops to 0)
   template <int WS>
-  __device__ __forceinline__ void advance(const float *w) {
-    const float Sn = fmaxf(fmaf(-sl, nx - el, S), 0.f);
-    ++k;
-    const bool in = k < B;
-    S = in ? Sn : 0.f;
-    sl = in ? w[off + k * WS] * invh : 0.f;
+  __device__ __forceinline__ void cross(const float *w, float g) {
     el = nx;
-    nx = (k + 1 < B) ? fmaf((float)(k + 1), h, lam) : (in ? end : kFar);
+    S = point ? 0.f : g;
+    --left;
+    kf += 1.f;
+    sl = left > 0 ? w[ptr] * invh : 0.f;
+    ptr += WS;
+    nx = left > 1 ? fmaf(kf, h, lam) : (left == 1 ? end : kFar);
   }
-  // advance if the next edge is at or before x (straight-line code: the
-  // mass load always reads a valid address of this neighbour's planes)
   template <int WS>
-  __device__ __forceinline__ void advance_if(const float *w, float x) {
-    const bool a = nx <= x;
-    const float Sn = fmaxf(fmaf(-sl, nx - el, S), 0.f);
-    const int kn = a ? k + 1 : k;
-    const bool in = kn < B;
-    const float wv = w[off + max(min(kn, B - 1), 0) * WS];
-    const float nxn = (kn + 1 < B) ? fmaf((float)(kn + 1), h, lam) : (in ? end : kFar);
-    S = a ? (in ? Sn : 0.f) : S;
-    sl = a ? (in ? wv * invh : 0.f) : sl;
-    el = a ? nx : el;
-    nx = a ? nxn : nx;
-    k = kn;
-  }
-  __device__ __forceinline__ float G(float x) const {
-    return fmaxf(fmaf(-sl, x - el, S), 0.f);
-  }
+  __device__ __forceinline__ void advance(const float *w) { cross<WS>(w, G(nx)); }
+  __device__ __forceinline__ float G(float x) const { return fmaf(-sl, x - el, S); }
 };
 
 // Both probabilities of a non-degenerate histogram centre in one walk over
@@ -685,7 +671,7 @@ __device__ __forceinline__ void hist_walk(const float *w, int coff, int B, float
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     Gl[i] = nw[i].G(0.f);
-    Fl[i] = fmaxf(T[i] - Gl[i], 0.f);
+    Fl[i] = T[i] - Gl[i];
   }
   Kahan amin, amax;
   float bmin = 0.f, bmax = 0.f;
@@ -696,7 +682,7 @@ __device__ __forceinline__ void hist_walk(const float *w, int coff, int B, float
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       Gr[i] = nw[i].G(x1);
-      Fr[i] = fmaxf(T[i] - Gr[i], 0.f);
+      Fr[i] = T[i] - Gr[i];
     }
     const float len = x1 - x0;
     if constexpr (SADDLE) {
@@ -726,16 +712,20 @@ __device__ __forceinline__ void hist_walk(const float *w, int coff, int B, float
     if (last) break;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      // continuous at a bin edge, but a point mass jumps: the left value of
-      // the next piece is re-evaluated on the new segment
-      nw[i].advance_if<WS>(w, x1);
-      Gl[i] = nw[i].G(x1);
-      Fl[i] = fmaxf(T[i] - Gl[i], 0.f);
+      // the left value of the next piece is the new segment's value at x1
+      // (the right value, except after a point mass)
+      if (nw[i].nx <= x1) {
+        nw[i].cross<WS>(w, Gr[i]);
+        Gr[i] = nw[i].S;
+        Fr[i] = T[i] - Gr[i];
+      }
+      Gl[i] = Gr[i];
+      Fl[i] = Fr[i];
     }
     x0 = x1;
   }
-  pmin = amin.get();
-  pmax = amax.get();
+  pmin = fmaxf(amin.get(), 0.f);
+  pmax = fmaxf(amax.get(), 0.f);
 }
 
 // survival and CDF of a histogram neighbour at a point v (degenerate centre)

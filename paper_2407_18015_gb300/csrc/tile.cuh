@@ -325,7 +325,7 @@ __device__ __forceinline__ void process_tile(const Field &f, int ty0, int tx0, f
             h.init(nl[i], 0, lo - lo1, 1.f, lo - lo1, T[i]);
           else
             h.init(nl[i], B, lo - lo1, (hi - lo) / (float)B, hi - lo1, T[i]);
-          for (int g = 0; g <= B && h.nx <= 0.f && h.k < h.B; ++g) h.advance<HALO>(sm + 2 * HALO);
+          for (int g = 0; g <= B && h.nx <= 0.f && h.left > 0; ++g) h.advance<HALO>(sm + 2 * HALO);
         }
         if constexpr (!SADDLE) {
           hist_walk<HALO>(sm + 2 * HALO, l, B, hi1 - lo1, nw, Tw, f.cptypes, pmin, pmax);
