@@ -61,10 +61,13 @@ def lib():
             L.orc_saddle.argtypes = [_d, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      _i64, ctypes.c_int64, _d, _u8]
             L.orc_philox4x32_10.argtypes = [_u32, _u32, _u32]
+            L.orc_semi_at.argtypes = [_d, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      _i64, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64,
+                                      ctypes.c_uint32, _d, _d, _d, _d, _d]
             L.orc_grad.argtypes = [_d, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_int, ctypes.c_int, _d, _d]
             for fn in ("orc_fit", "orc_prob", "orc_prob_at", "orc_prob_hist_h5_at",
-                       "orc_mvn_mc_at", "orc_grad", "orc_saddle"):
+                       "orc_mvn_mc_at", "orc_grad", "orc_saddle", "orc_semi_at"):
                 getattr(L, fn).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -220,3 +223,19 @@ def grad(params, model, weight, cptype=1, bins=0, boundary=0):
     if rc != 0:
         raise ValueError("orc_grad rejected its arguments")
     return out
+
+
+def semi_at(params, bins, idx, samples, seed, field=0, boundary=0):
+    """Semianalytical histogram estimator at vertices idx: (P_min, P_max,
+    P_saddle, sd_min, sd_max) (sd: standard deviation of the mean)."""
+    params = _c64(params)
+    _, H, W = params.shape
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    n = idx.size
+    out = [np.empty(n, np.float64) for _ in range(5)]
+    rc = lib().orc_semi_at(_p(params, _d), H, W, bins, boundary, _p(idx, _i64), n, int(samples),
+                           int(seed) & 0xFFFFFFFFFFFFFFFF, int(field) & 0xFFFFFFFF,
+                           *[_p(o, _d) for o in out])
+    if rc != 0:
+        raise ValueError("orc_semi_at rejected its arguments")
+    return tuple(out)

@@ -900,6 +900,113 @@ int orc_mvn_mc_at(const double *params, int H, int W, int boundary, const int64_
 }
 
 /* ------------------------------------------------------------------------ */
+/* semianalytical histogram estimator (Sec. "Semianalytical Solution")       */
+/*                                                                          */
+/* c samples x_s are drawn from the centre's histogram; for each, the        */
+/* probability of being below (above) every neighbour is exact: the product */
+/* of the neighbours' mixture survivals G_n(x_s) (CDFs F_n(x_s)); the        */
+/* estimate is T_1 times the mean over the samples (T_1 = the centre's total */
+/* mass).  Sampling: sample s uses Philox4x32-10 with counter (s >> 1, i,    */
+/* field, 2) and the seed as key; words 0, 1 (even s) or 2, 3 (odd s) give    */
+/* uniforms ua, ub as for the Gaussian path.  The bin is an integer decision */
+/* taken in IEEE binary32 on both sides: t = ua * T_1 (T_1 summed in bin     */
+/* order in binary32), j = the number of running sums C_1..C_B (binary32,    */
+/* in bin order) that are <= t, clamped to B-1; then x = lo + (j + ub) h.    */
+/* A point-mass centre is exact (every sample is its position).             */
+
+static double semi_sample_x(const dist_t *v, float ua, float ub) {
+  float T = 0.0f, C = 0.0f, t;
+  int j, cnt = 0, B = v->B;
+  for (j = 0; j < B; ++j) T += (float)v->w[j];
+  t = ua * T;
+  for (j = 0; j < B; ++j) {
+    C += (float)v->w[j];
+    cnt += (C <= t);
+  }
+  if (cnt > B - 1) cnt = B - 1;
+  return v->lo + ((double)cnt + (double)ub) * (v->hi - v->lo) / (double)B;
+}
+
+/* Estimates of P_min, P_max, P_saddle at vertices idx (histogram params);
+ * sd_* (nullable) receive the sample standard deviation of each mean. */
+int orc_semi_at(const double *params, int H, int W, int B, int boundary, const int64_t *idx,
+                int64_t n, int c, uint64_t seed, uint32_t field, double *out_min,
+                double *out_max, double *out_saddle, double *sd_min, double *sd_max) {
+  int64_t t, plane = (int64_t)H * W;
+  if (c < 1 || B < 1 || B > MAXB) return -1;
+#pragma omp parallel for schedule(dynamic, 4) num_threads(orc_get_threads())
+  for (t = 0; t < n; ++t) {
+    int64_t i = idx[t], nidx[4];
+    int y = (int)(i / W), x = (int)(i % W), slot[4], k, q, st, ssg[4] = {0, 0, 0, 0}, has_sad;
+    double pv[2 + MAXB], smin = 0, smax = 0, ssad = 0, qmin = 0, qmax = 0;
+    dist_t v, nb[4];
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    k = neighbours(H, W, y, x, nidx, slot);
+    gather_params(params, plane, 2 + B, i, pv);
+    st = dist_make(ORC_HIST, pv, B, &v);
+    for (q = 0; q < k; ++q) {
+      double pn[2 + MAXB];
+      gather_params(params, plane, 2 + B, nidx[q], pn);
+      st |= dist_make(ORC_HIST, pn, B, &nb[q]);
+    }
+    if (st & (ST_NONFINITE | ST_BAD_PARAMS)) {
+      out_min[t] = out_max[t] = out_saddle[t] = NAN;
+      continue;
+    }
+    has_sad = (k == 4) || (k == 2 && (H == 1 || W == 1));
+    for (q = 0; q < k; ++q)
+      ssg[q] = (k == 4) ? ((slot[q] == 0 || slot[q] == 2) ? 1 : -1)
+                        : ((slot[q] == 0 || slot[q] == 3) ? 1 : -1);
+    if (v.point) {
+      double pm = v.total, pM = v.total, t1 = v.total, t2 = v.total;
+      for (q = 0; q < k; ++q) {
+        double g = prob_greater(&nb[q], v.lo), f = prob_less(&nb[q], v.lo);
+        pm *= g;
+        pM *= f;
+        t1 *= ssg[q] > 0 ? g : f;
+        t2 *= ssg[q] > 0 ? f : g;
+      }
+      smin = pm * c;
+      smax = pM * c;
+      ssad = has_sad ? (t1 + t2) * c : 0.0;
+      qmin = pm * pm * c;
+      qmax = pM * pM * c;
+    } else {
+      int s;
+      for (s = 0; s < c; ++s) {
+        uint32_t ctr[4] = {(uint32_t)(s >> 1), (uint32_t)i, field, 2u}, r[4];
+        float ua, ub;
+        double xs, pm = v.total, pM = v.total, t1 = v.total, t2 = v.total;
+        orc_philox4x32_10(ctr, key, r);
+        ua = (float)(((double)(r[(s & 1) * 2] >> 8) + 0.5) / 16777216.0);
+        ub = (float)(((double)(r[(s & 1) * 2 + 1] >> 8) + 0.5) / 16777216.0);
+        xs = semi_sample_x(&v, ua, ub);
+        for (q = 0; q < k; ++q) {
+          /* G_n(x) = Pr[X_n > x], F_n(x) = Pr[X_n < x] in the mixture form */
+          double g = prob_greater(&nb[q], xs), f = prob_less(&nb[q], xs);
+          pm *= g;
+          pM *= f;
+          t1 *= ssg[q] > 0 ? g : f;
+          t2 *= ssg[q] > 0 ? f : g;
+        }
+        smin += pm;
+        smax += pM;
+        qmin += pm * pm;
+        qmax += pM * pM;
+        if (has_sad) ssad += t1 + t2;
+      }
+    }
+    out_min[t] = smin / c;
+    out_max[t] = smax / c;
+    out_saddle[t] = ssad / c;
+    if (boundary == 1 && k < 4) out_min[t] = out_max[t] = 0.0;
+    if (sd_min) sd_min[t] = sqrt(fmax(qmin / c - (smin / c) * (smin / c), 0.0) / c);
+    if (sd_max) sd_max[t] = sqrt(fmax(qmax / c - (smax / c) * (smax / c), 0.0) / c);
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* gradients of L = sum_v W_v P_v with respect to every vertex's parameters  */
 /*                                                                          */
 /* P_v depends on the parameters of v and of its in-grid neighbours only.   */

@@ -542,3 +542,38 @@ def test_saddle_mvn_diagonal_quadrature(orc):
         return v * (g[0] * c[1] * g[2] * c[3] + c[0] * g[1] * c[2] * g[3])
     p = scipy_integrate.quad(integrand, -20, 20, epsabs=1e-13, limit=200)[0]
     assert abs(hs[0] / S - p) < 5 * math.sqrt(p * (1 - p) / S)
+
+
+# --------------------------------------------------------------------------
+# semianalytical histogram estimator (Sec. Semianalytical Solution)
+
+
+def test_semianalytical_converges_to_closed_form(orc):
+    rng = np.random.default_rng(91)
+    B = 6
+    p = H_.random_params(2, 5, 6, rng, bins=B)
+    idx = np.arange(30)
+    c = 100_000
+    smin, smax, ssad, sdmin, sdmax = orc.semi_at(p, B, idx, c, seed=17)
+    rmin, rmax, _ = orc.prob_at(p, 2, idx, bins=B)
+    rsad, _ = orc.saddle(p, 2, bins=B, idx=idx)
+    zmin = np.abs(smin - rmin) / np.maximum(sdmin, 1e-12)
+    zmax = np.abs(smax - rmax) / np.maximum(sdmax, 1e-12)
+    assert zmin.max() < 5.5 and zmax.max() < 5.5
+    # the saddle estimate: the per-sample terms lie in [0, 1]
+    assert np.abs(ssad - rsad).max() < 5.5 * 0.5 / np.sqrt(c)
+    # the error shrinks like 1/sqrt(c)
+    s2, _, _, _, _ = orc.semi_at(p, B, idx, c // 100, seed=17)
+    assert np.abs(s2 - rmin).mean() > 3 * np.abs(smin - rmin).mean()
+
+
+def test_semianalytical_point_mass_centre_is_exact(orc):
+    rng = np.random.default_rng(92)
+    B = 4
+    p = H_.random_params(2, 3, 3, rng, bins=B)
+    p[1, 1, 1] = p[0, 1, 1]           # centre is a point mass
+    smin, smax, ssad, sdmin, _ = orc.semi_at(p, B, [4], 7, seed=1)
+    rmin, rmax, _ = orc.prob_at(p, 2, [4], bins=B)
+    rsad, _ = orc.saddle(p, 2, bins=B, idx=[4])
+    assert abs(smin[0] - rmin[0]) < 1e-14 and abs(smax[0] - rmax[0]) < 1e-14
+    assert abs(ssad[0] - rsad[0]) < 1e-14 and sdmin[0] == 0.0
