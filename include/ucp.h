@@ -87,7 +87,21 @@ typedef enum {
    * factorisation fails, eps*I is added, eps = 1e-6 * trace / (k+1), times
    * 10 per retry, three retries (UCP_V_CHOL_JITTER), else UCP_V_CHOL_FAIL.
    * A zero-trace covariance is deterministic (UCP_V_DEGENERATE). */
-  UCP_MVN_MC = 3
+  UCP_MVN_MC = 3,
+  /* the histogram model (same parameters, same fit) evaluated by the paper's
+   * semianalytical estimator (Sec. "Semianalytical Solution"): mc_samples
+   * samples x_s from the centre's histogram; the probability of each being
+   * below (above) every neighbour is exact from the neighbours' histograms
+   * (bin of x_s plus the prefix sum of the masses); the estimate is the
+   * centre's total mass times the mean over the samples.  Sampling contract:
+   * sample s of the vertex with linear index i uses the Philox4x32-10 block
+   * with counter (s >> 1, i, field_id, 2) and the seed as key; words 0, 1 (s
+   * even) or 2, 3 (s odd) give uniforms ua, ub as above; the bin is the
+   * number of running mass sums C_1..C_B (IEEE binary32, bin order) that are
+   * <= ua * T (T = C_B), clamped to B-1; x_s = lo + (bin + ub) h.  A
+   * point-mass centre is exact.  Minimum, maximum and saddle; no adjoint,
+   * no batch. */
+  UCP_HISTOGRAM_SEMI = 4
 } ucp_model;
 
 typedef enum { UCP_MIN = 1, UCP_MAX = 2 } ucp_cptype; /* bit mask */
@@ -117,7 +131,7 @@ typedef struct {
   int model;              /* ucp_model                                          */
   int bins;               /* histogram bin count B, 1..64 (ignored otherwise)   */
   float epan_width_scale; /* Epanechnikov w = scale * std; <= 0 means sqrt(5)   */
-  int mc_samples;         /* MVN samples per vertex (>= 1)                      */
+  int mc_samples;         /* samples per vertex, MVN and semianalytical (>= 1)  */
   uint64_t seed;          /* MVN Philox key                                     */
   uint32_t field_id;      /* MVN Philox counter word 2                          */
   int boundary;           /* ucp_boundary                                       */
@@ -130,7 +144,8 @@ const char *ucp_status_string(int status);
 const char *ucp_version(void);
 
 /* Number of parameter planes P of a model: 2 (uniform, Epanechnikov),
- * 2 + bins (histogram), 20 (MVN); 0 for an invalid descriptor. */
+ * 2 + bins (histogram, both evaluations), 20 (MVN); 0 for an invalid
+ * descriptor. */
 int ucp_param_count(const ucp_model_desc *desc);
 
 /* Create a context bound to CUDA device `device`.  The context owns its

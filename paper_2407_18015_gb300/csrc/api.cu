@@ -41,12 +41,15 @@ struct DeviceGuard {
   }
 };
 
-int valid_desc(const ucp_model_desc *d, bool allow_mvn) {
+int valid_desc(const ucp_model_desc *d, bool allow_sampled) {
   if (!d) return UCP_ERR_ARG;
-  if (d->model < UCP_UNIFORM || d->model > UCP_MVN_MC) return UCP_ERR_ARG;
-  if (d->model == UCP_MVN_MC && !allow_mvn) return UCP_ERR_UNSUPPORTED;
-  if (d->model == UCP_HISTOGRAM && (d->bins < 1 || d->bins > kMaxBinsHost)) return UCP_ERR_ARG;
-  if (d->model == UCP_MVN_MC && d->mc_samples < 1) return UCP_ERR_ARG;
+  if (d->model < UCP_UNIFORM || d->model > UCP_HISTOGRAM_SEMI) return UCP_ERR_ARG;
+  const bool sampled = d->model == UCP_MVN_MC || d->model == UCP_HISTOGRAM_SEMI;
+  if (sampled && !allow_sampled) return UCP_ERR_UNSUPPORTED;
+  if ((d->model == UCP_HISTOGRAM || d->model == UCP_HISTOGRAM_SEMI) &&
+      (d->bins < 1 || d->bins > kMaxBinsHost))
+    return UCP_ERR_ARG;
+  if (sampled && d->mc_samples < 1) return UCP_ERR_ARG;
   if (d->boundary != UCP_BOUNDARY_INGRID && d->boundary != UCP_BOUNDARY_ZERO) return UCP_ERR_ARG;
   return UCP_OK;
 }
@@ -191,6 +194,10 @@ static int probability_impl(ucp_ctx *ctx, const float *ens, const float *params,
   f.boundary = desc->boundary;
   f.epan_scale = epan_scale(desc);
   f.cptypes = cptypes;
+  f.samples = desc->mc_samples;
+  f.seed_lo = (uint32_t)desc->seed;
+  f.seed_hi = (uint32_t)(desc->seed >> 32);
+  f.field_id = desc->field_id;
   cudaError_t e;
   if (desc->model == UCP_MVN_MC)
     e = launch_mvn_mc(f, ens != nullptr, desc->mc_samples, desc->seed, desc->field_id, stream);
@@ -241,6 +248,10 @@ static int saddle_impl(ucp_ctx *ctx, const float *ens, const float *params, int 
   f.boundary = desc->boundary;
   f.epan_scale = epan_scale(desc);
   f.cptypes = kSaddle;
+  f.samples = desc->mc_samples;
+  f.seed_lo = (uint32_t)desc->seed;
+  f.seed_hi = (uint32_t)(desc->seed >> 32);
+  f.field_id = desc->field_id;
   cudaError_t e;
   if (desc->model == UCP_MVN_MC)
     e = launch_mvn_mc(f, ens != nullptr, desc->mc_samples, desc->seed, desc->field_id, stream);

@@ -84,15 +84,23 @@ __global__ void __launch_bounds__(256) fit_kernel(Field f) {
 // resident CTAs per SM each model's register budget is tuned for
 template <int MODEL>
 struct TileOcc {
-  static constexpr int value = MODEL == kUniform ? 5 : (MODEL == kEpan ? 4 : 3);
+  static constexpr int value = MODEL == kUniform ? 5 : (MODEL == kEpan ? 4 : (MODEL == kHist ? 3 : 2));
+};
+
+// tile height: 16, or 8 for the estimator (whose shared tile also holds the
+// running mass sums and whose per-vertex work makes the halo negligible)
+template <int MODEL>
+struct TileH {
+  static constexpr int value = MODEL == kSemi ? 8 : TY;
 };
 
 template <int MODEL, bool FROM_MEMBERS, bool SADDLE = false>
 __global__ void __launch_bounds__(NTHREADS, TileOcc<MODEL>::value) tile_kernel(Field f, int tiles_x) {
   extern __shared__ float sm[];
   const int tile = blockIdx.x;
-  process_tile<MODEL, FROM_MEMBERS, TY, SADDLE>(f, f.y0 + (tile / tiles_x) * TY,
-                                                (tile % tiles_x) * TX, sm);
+  constexpr int TYm = TileH<MODEL>::value;
+  process_tile<MODEL, FROM_MEMBERS, TYm, SADDLE>(f, f.y0 + (tile / tiles_x) * TYm,
+                                                 (tile % tiles_x) * TX, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -123,7 +131,8 @@ cudaError_t launch_fit(const Field &f, int model, cudaStream_t s) {
   switch (model) {
     case kUniform: fit_kernel<kUniform><<<g, 256, 0, s>>>(f); break;
     case kEpan: fit_kernel<kEpan><<<g, 256, 0, s>>>(f); break;
-    case kHist: fit_kernel<kHist><<<g, 256, 0, s>>>(f); break;
+    case kHist:
+    case kSemi: fit_kernel<kHist><<<g, 256, 0, s>>>(f); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -131,23 +140,31 @@ cudaError_t launch_fit(const Field &f, int model, cudaStream_t s) {
 
 template <int MODEL, bool FM, bool SADDLE>
 static cudaError_t launch_tile(const Field &f, cudaStream_t s) {
-  const int P = (MODEL == kHist) ? 2 + f.B : 2;
-  const size_t smem = (size_t)P * HALO * sizeof(float);
+  constexpr int TYm = TileH<MODEL>::value;
+  constexpr int HALOm = (TYm + 2) * HX;
+  const int P = MODEL == kSemi ? 2 + 2 * f.B : (MODEL == kHist ? 2 + f.B : 2);
+  const size_t smem = (size_t)P * HALOm * sizeof(float);
   static bool attr_set[128] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
   if (!attr_set[dev]) {
+    // the largest parameter tile of this model (64 bins; the estimator also
+    // keeps the running mass sums): 158 KB at 18 x 34, 173 KB at 10 x 34
+    const int Pmax = MODEL == kSemi ? 2 + 2 * kMaxBins : (MODEL == kHist ? 2 + kMaxBins : 2);
     e = cudaFuncSetAttribute(tile_kernel<MODEL, FM, SADDLE>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)((2 + kMaxBins) * HALO * sizeof(float)));
-    if (e != cudaSuccess) return e;
+                             (int)((size_t)Pmax * HALOm * sizeof(float)));
+    if (e != cudaSuccess) {
+      cudaGetLastError();  // do not leave the failed call as the last error
+      return e;
+    }
     attr_set[dev] = true;
   }
   Field g = f;
   g.vec4 = (f.ens != nullptr) && (f.W % 4 == 0) && ((reinterpret_cast<uintptr_t>(f.ens) & 15) == 0);
-  const int tiles_x = (f.W + TX - 1) / TX, tiles_y = (f.y1 - f.y0 + TY - 1) / TY;
+  const int tiles_x = (f.W + TX - 1) / TX, tiles_y = (f.y1 - f.y0 + TYm - 1) / TYm;
   if (tiles_y <= 0) return cudaSuccess;
   const long long tiles = (long long)tiles_x * tiles_y;
   if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
@@ -163,6 +180,8 @@ static cudaError_t launch_closed_t(const Field &f, int model, bool fm, cudaStrea
                                 : launch_tile<kEpan, false, SADDLE>(f, s);
   if (model == kHist) return fm ? launch_tile<kHist, true, SADDLE>(f, s)
                                 : launch_tile<kHist, false, SADDLE>(f, s);
+  if (model == kSemi) return fm ? launch_tile<kSemi, true, SADDLE>(f, s)
+                                : launch_tile<kSemi, false, SADDLE>(f, s);
   return cudaErrorInvalidValue;
 }
 

@@ -21,7 +21,10 @@
 
 namespace ucp {
 
-constexpr int kUniform = 0, kEpan = 1, kHist = 2, kMvn = 3;
+constexpr int kUniform = 0, kEpan = 1, kHist = 2, kMvn = 3, kSemi = 4;
+
+// histogram parameters (lo, hi, masses): the closed form and the estimator
+__host__ __device__ constexpr bool hist_params(int model) { return model == kHist || model == kSemi; }
 constexpr unsigned kMin = 1u, kMax = 2u, kSaddle = 4u;
 constexpr int kMaxBins = 64;
 
@@ -604,6 +607,156 @@ __device__ __forceinline__ bool saddle_signs(const bool *present, int H, int W, 
     return true;
   }
   return false;
+}
+
+// ---------------------------------------------------------------------------
+// counter-based generator: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+
+// key schedule (Weyl sequence), computed once per vertex
+struct PhiloxKeys {
+  uint32_t k0[10], k1[10];
+  __device__ __forceinline__ PhiloxKeys(uint32_t a, uint32_t b) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+      k0[r] = a;
+      k1[r] = b;
+      a += 0x9E3779B9u;
+      b += 0xBB67AE85u;
+    }
+  }
+};
+
+__device__ __forceinline__ void philox_round(uint4 &c, uint32_t k0, uint32_t k1) {
+  const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+  const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+  c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+}
+
+__device__ __forceinline__ uint4 philox_block(uint4 c, const PhiloxKeys &K) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) philox_round(c, K.k0[r], K.k1[r]);
+  return c;
+}
+
+__device__ __forceinline__ float u01(uint32_t r) {
+  // ((r >> 8) + 0.5) * 2^-24, exact in binary32
+  return fmaf(__uint2float_rn(r >> 8), 0x1p-24f, 0x1p-25f);
+}
+
+// ---------------------------------------------------------------------------
+// semianalytical histogram estimator (Sec. "Semianalytical Solution")
+//
+// c samples from the centre's histogram; for each sample x the probability
+// of being below (above) every neighbour is exact -- the neighbours' mixture
+// survivals G_n(x) (CDFs F_n(x)) from their bin and prefix mass -- and the
+// estimate is T_1 times the mean of the products.  Sample s of vertex i uses
+// the Philox block with counter (s >> 1, i, field, 2): words 0, 1 (s even) or
+// 2, 3 (s odd) are (ua, ub).  Bin: the number of running mass sums C_1..C_B
+// (binary32, bin order) that are <= ua * T_1, clamped to B - 1 (binary
+// search over the prefix planes); position: (j + ub) h inside the bin.
+
+struct SemiNb {
+  float lam, ih, T;  // local support start, B / (hi - lo), total mass
+  int off;           // shared-memory index of the vertex
+  int kind;          // 0 absent, 1 bins, 2 point mass
+};
+
+// F_n(x) and G_n(x) = T_n - F_n(x) of a neighbour at the local position x
+template <int WS>
+__device__ __forceinline__ void semi_tails(const float *w, const float *C, const SemiNb &n, int B,
+                                           float x, float &G, float &F) {
+  if (n.kind == 0) {
+    G = F = 1.f;
+    return;
+  }
+  if (n.kind == 2) {
+    G = x < n.lam ? n.T : 0.f;
+    F = x > n.lam ? n.T : 0.f;
+    return;
+  }
+  const float v = (x - n.lam) * n.ih;
+  const float fk = floorf(v);
+  if (fk < 0.f) {
+    G = n.T;
+    F = 0.f;
+  } else if (fk >= (float)B) {
+    G = 0.f;
+    F = n.T;
+  } else {
+    const int k = (int)fk;
+    const float Ck = k > 0 ? C[(k - 1) * WS + n.off] : 0.f;
+    F = fmaf(w[k * WS + n.off], v - fk, Ck);
+    G = n.T - F;
+  }
+}
+
+template <int WS, bool SADDLE>
+__device__ __forceinline__ void semi_vertex(const float *w, const float *C, int l, float lo1,
+                                            float hi1, const SemiNb *nb, int B, int S,
+                                            const PhiloxKeys &K, uint32_t vid, uint32_t field,
+                                            const int *sg, float &pmin, float &pmax,
+                                            float &psad) {
+  const float T1 = C[(B - 1) * WS + l];
+  if (lo1 == hi1) {  // point-mass centre: every sample is its position
+    float gm = T1, gM = T1, t1 = T1, t2 = T1;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float G, F;
+      semi_tails<WS>(w, C, nb[i], B, 0.f, G, F);
+      gm *= G;
+      gM *= F;
+      if (SADDLE && sg[i] != 0) {
+        t1 *= sg[i] > 0 ? G : F;
+        t2 *= sg[i] > 0 ? F : G;
+      }
+    }
+    pmin = gm;
+    pmax = gM;
+    psad = t1 + t2;
+    return;
+  }
+  const float h1 = (hi1 - lo1) / (float)B;
+  Kahan amin, amax;
+  for (int s = 0; s < S; s += 2) {
+    const uint4 r = philox_block(make_uint4((uint32_t)(s >> 1), vid, field, 2u), K);
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      if (s + half >= S) break;
+      const float ua = u01(half ? r.z : r.x), ub = u01(half ? r.w : r.y);
+      const float t = ua * T1;
+      int lo = 0, hi = B;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (C[mid * WS + l] <= t) lo = mid + 1;
+        else hi = mid;
+      }
+      const int j = min(lo, B - 1);
+      const float x = ((float)j + ub) * h1;
+      float pm = T1, pM = T1, t1 = T1, t2 = T1;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        float G, F;
+        semi_tails<WS>(w, C, nb[i], B, x, G, F);
+        if (SADDLE) {
+          t1 *= sg[i] > 0 ? G : (sg[i] < 0 ? F : 1.f);
+          t2 *= sg[i] > 0 ? F : (sg[i] < 0 ? G : 1.f);
+        } else {
+          pm *= G;
+          pM *= F;
+        }
+      }
+      if (SADDLE) {
+        amin.add(t1 + t2);
+      } else {
+        amin.add(pm);
+        amax.add(pM);
+      }
+    }
+  }
+  const float inv = 1.f / (float)S;
+  pmin = amin.get() * inv;
+  pmax = amax.get() * inv;
+  psad = pmin;
 }
 
 // ---------------------------------------------------------------------------

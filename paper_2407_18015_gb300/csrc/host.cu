@@ -86,6 +86,10 @@ int ucp_host_pipeline(ucp_ctx *ctx, const float *ens_host, int N, int H, int W,
   f.boundary = desc->boundary;
   f.epan_scale = desc->epan_width_scale > 0.f ? desc->epan_width_scale : 2.2360679774997896f;
   f.cptypes = cptypes;
+  f.samples = desc->mc_samples;
+  f.seed_lo = (uint32_t)desc->seed;
+  f.seed_hi = (uint32_t)(desc->seed >> 32);
+  f.field_id = desc->field_id;
 
   int i = 0;
   for (int r0 = 0; r0 < H && e == cudaSuccess; r0 += rows, ++i) {

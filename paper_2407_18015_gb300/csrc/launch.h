@@ -22,12 +22,16 @@ struct Field {
   float epan_scale;
   unsigned cptypes;     // bit 1 min, bit 2 max, bit 4 saddle
   bool vec4;            // members may be read as aligned float4 (W % 4 == 0, 16B base)
+  int samples;          // Monte Carlo / semianalytical samples per vertex
+  uint32_t seed_lo, seed_hi, field_id;
 };
 
 // Tile of the closed-form kernels: TY x TX vertices plus a one-vertex halo.
 constexpr int TY = 16, TX = 32, HY = TY + 2, HX = TX + 2, HALO = HY * HX, NTHREADS = 256;
 
-inline int param_planes(int model, int B) { return model == 2 ? 2 + B : (model == 3 ? 20 : 2); }
+inline int param_planes(int model, int B) {
+  return (model == 2 || model == 4) ? 2 + B : (model == 3 ? 20 : 2);
+}
 
 cudaError_t launch_fit(const Field &f, int model, cudaStream_t s);
 cudaError_t launch_closed(const Field &f, int model, bool from_members, cudaStream_t s);

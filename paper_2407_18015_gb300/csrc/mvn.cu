@@ -15,26 +15,6 @@
 
 namespace ucp {
 
-// Philox4x32-10 key schedule (Weyl sequence), computed once per vertex
-struct PhiloxKeys {
-  uint32_t k0[10], k1[10];
-  __device__ __forceinline__ PhiloxKeys(uint32_t a, uint32_t b) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-      k0[r] = a;
-      k1[r] = b;
-      a += 0x9E3779B9u;
-      b += 0xBB67AE85u;
-    }
-  }
-};
-
-__device__ __forceinline__ void philox_round(uint4 &c, uint32_t k0, uint32_t k1) {
-  const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-  const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-  c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-}
-
 // The two blocks of one sample: counters (s, v, field, 0) and (s, v, field, 1)
 // differ only in the last word, so the first round's products are shared.
 __device__ __forceinline__ void philox_pair(uint32_t s, uint32_t v, uint32_t field,
@@ -49,11 +29,6 @@ __device__ __forceinline__ void philox_pair(uint32_t s, uint32_t v, uint32_t fie
     philox_round(r0, K.k0[r], K.k1[r]);
     philox_round(r1, K.k0[r], K.k1[r]);
   }
-}
-
-__device__ __forceinline__ float u01(uint32_t r) {
-  // ((r >> 8) + 0.5) * 2^-24, exact in binary32
-  return fmaf(__uint2float_rn(r >> 8), 0x1p-24f, 0x1p-25f);
 }
 
 // Box-Muller: radius sqrt(-2 ln ua), angle 2 pi ub.  The angle is taken as

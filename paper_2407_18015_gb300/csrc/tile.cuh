@@ -89,7 +89,7 @@ __device__ __forceinline__ void stage_members(const Field &f, float *sm, int l, 
       sm[l + q] = nf[q] ? qnan() : mn[q];
       sm[HALO + l + q] = nf[q] ? qnan() : mx[q];
     }
-    if constexpr (MODEL == kHist) {
+    if constexpr (hist_params(MODEL)) {
       const int B = f.B;
       float sc[V];
       bool bin[V];
@@ -129,7 +129,7 @@ template <int MODEL, bool FROM_MEMBERS, int HALO>
 __device__ __forceinline__ void stage_vertex(const Field &f, float *sm, int l, long long gi) {
   const long long plane = f.plane;
   if (!FROM_MEMBERS) {
-    const int P = (MODEL == kHist) ? 2 + f.B : 2;
+    const int P = hist_params(MODEL) ? 2 + f.B : 2;
     for (int q = 0; q < P; ++q) sm[q * HALO + l] = __ldg(f.params + q * plane + gi);
     return;
   }
@@ -235,6 +235,17 @@ __device__ __forceinline__ void process_tile(const Field &f, int ty0, int tx0, f
     }
   }
   __syncthreads();
+  if constexpr (MODEL == kSemi) {
+    // running mass sums C_1..C_B of every staged vertex, in bin order
+    for (int l = threadIdx.x; l < HALO; l += NTHREADS) {
+      float c = 0.f;
+      for (int q = 0; q < f.B; ++q) {
+        c += sm[(2 + q) * HALO + l];
+        sm[(2 + f.B + q) * HALO + l] = c;
+      }
+    }
+    __syncthreads();
+  }
 
   for (int v = threadIdx.x; v < TY * TX; v += NTHREADS) {
     const int r = v / TX + 1, c = v % TX + 1;
@@ -266,6 +277,30 @@ __device__ __forceinline__ void process_tile(const Field &f, int ty0, int tx0, f
     for (int i = 0; i < 4; ++i) sg2[i] = SADDLE ? -sg[i] : 0;
     if (bad) {
       pmin = pmax = psad = qnan();
+    } else if constexpr (MODEL == kSemi) {
+      SemiNb nb[4];
+      const float lo1 = sm[l];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        nb[i].off = nl[i];
+        nb[i].T = T[i];
+        if (!present[i]) {
+          nb[i].kind = 0;
+          nb[i].lam = 0.f;
+          nb[i].ih = 0.f;
+          continue;
+        }
+        const float lo = sm[nl[i]], hi = sm[HALO + nl[i]];
+        nb[i].lam = lo - lo1;
+        nb[i].kind = lo == hi ? 2 : 1;
+        nb[i].ih = lo == hi ? 0.f : (float)f.B / (hi - lo);
+      }
+      const PhiloxKeys K(f.seed_lo, f.seed_hi);
+      if (!SADDLE || has_saddle)
+        semi_vertex<HALO, SADDLE>(sm + 2 * HALO, sm + (2 + f.B) * HALO, l, lo1, sm[HALO + l], nb,
+                                  f.B, f.samples, K, (uint32_t)((long long)gy * f.W + gx),
+                                  f.field_id, sg, pmin, pmax, psad);
+      if (!SADDLE && f.boundary == 1 && k < 4) pmin = pmax = 0.f;
     } else if (MODEL == kUniform) {
       UniParams cp{sm[l], sm[HALO + l]}, nb[4];
 #pragma unroll

@@ -17,7 +17,7 @@ import torch
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libucp.so")
 
-UCP_UNIFORM, UCP_EPANECHNIKOV, UCP_HISTOGRAM, UCP_MVN_MC = 0, 1, 2, 3
+UCP_UNIFORM, UCP_EPANECHNIKOV, UCP_HISTOGRAM, UCP_MVN_MC, UCP_HISTOGRAM_SEMI = 0, 1, 2, 3, 4
 UCP_MIN, UCP_MAX = 1, 2
 UCP_BOUNDARY_INGRID, UCP_BOUNDARY_ZERO = 0, 1
 UCP_OK, UCP_ERR_ARG, UCP_ERR_SHAPE, UCP_ERR_CUDA, UCP_ERR_NOMEM, UCP_ERR_TIMEOUT, \
@@ -26,7 +26,8 @@ UCP_V_DEGENERATE, UCP_V_NONFINITE, UCP_V_BAD_PARAMS, UCP_V_CHOL_JITTER, UCP_V_CH
     1, 2, 4, 8, 16
 
 MODELS = {"uniform": UCP_UNIFORM, "epanechnikov": UCP_EPANECHNIKOV,
-          "histogram": UCP_HISTOGRAM, "mvn": UCP_MVN_MC}
+          "histogram": UCP_HISTOGRAM, "mvn": UCP_MVN_MC,
+          "histogram_semi": UCP_HISTOGRAM_SEMI}
 
 
 class ucp_model_desc(ctypes.Structure):
@@ -353,7 +354,7 @@ class Context:
         return out, st
 
     def backward(self, params, desc, cptype, weight):
-        Q = desc.bins if desc.model == UCP_HISTOGRAM else 2
+        Q = desc.bins if desc.model in (UCP_HISTOGRAM, UCP_HISTOGRAM_SEMI) else 2
         _, H, W = params.shape
         grad = torch.empty((Q, H, W), dtype=torch.float32, device=params.device)
         ucp_backward(self.handle, params, desc, cptype, weight.contiguous(), grad)
