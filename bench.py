@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-rows", action="store_true", help="headline workload only")
-    ap.add_argument("--rows", default="mvn,fwdbwd,batch")
+    ap.add_argument("--rows", default="mvn,fwdbwd,batch,saddle,gmm")
     return ap.parse_args()
 
 
@@ -458,7 +458,51 @@ def other_rows(torch, ucp, ctx, dev, args, flush, peaks):
         del e4
     if "batch" in want:
         rows["batch_64_fields"] = batch_row(torch, ucp, ctx, dev, steps, flush)
+    if "saddle" in want:
+        e2 = torch.from_numpy(synth.ensemble_bimodal(H2, W2, N2, seed=SEED2)).to(dev)
+        out = torch.empty((H2, W2), device=dev)
+        r = {}
+        for m, b in MODELS2:
+            d = ucp.make_desc(m, bins=b or 8)
+            ms, _ = timed_steps(torch, lambda ev, d=d: ucp.ucp_saddle(ctx.handle, e2, d, out),
+                                steps, 2, flush)
+            r[m] = {"ms": ms / steps, "vertices_per_s": H2 * W2 / (ms / steps / 1e3)}
+        d = ucp.make_desc("histogram_semi", bins=BINS2, mc_samples=1000)
+        pm, px = torch.empty((H2, W2), device=dev), torch.empty((H2, W2), device=dev)
+        ms, _ = timed_steps(torch, lambda ev: ucp.ucp_probability(ctx.handle, e2, d, 3, pm, px),
+                            steps, 2, flush)
+        rows["saddle_1024x1024x20"] = r
+        rows["semianalytical_hist8_c1000_1024x1024x20"] = {
+            "ms": ms / steps, "vertices_per_s": H2 * W2 / (ms / steps / 1e3), "min_and_max": True}
+        del e2
+    if "gmm" in want:
+        rows["gmm_outliers_64x64x50_max"] = gmm_row(torch, ucp, ctx, dev, steps, flush)
     return rows
+
+
+def gmm_row(torch, ucp, ctx, dev, steps, flush):
+    """The model comparison of the paper on the outlier ensemble: local
+    maximum probability per model, the time of each, and the probability
+    near the true and the outlier peaks."""
+    from paper_2407_18015_gb300 import synth
+    ens_np, tp, op = synth.ensemble_gmm_outliers()
+    ens = torch.from_numpy(ens_np).to(dev)
+    H, W = ens_np.shape[1:]
+    out = {}
+    for model, bins, S in (("uniform", 0, 0), ("epanechnikov", 0, 0), ("histogram", 5, 0),
+                           ("histogram_semi", 5, 1000), ("mvn", 0, 2000)):
+        d = ucp.make_desc(model, bins=bins or 8, mc_samples=S or 1000)
+        pm = torch.empty((H, W), device=dev)
+        ms, _ = timed_steps(torch, lambda ev, d=d, pm=pm: ucp.ucp_probability(
+            ctx.handle, ens, d, ucp.UCP_MAX, None, pm), steps, 2, flush)
+        P = pm.cpu().numpy()
+
+        def near(pts):
+            return [float(P[y - 2:y + 3, x - 2:x + 3].max()) for (y, x) in pts]
+        out[model + (str(bins) if bins else "")] = {
+            "ms": ms / steps, "p_max_near_true_peaks": near(tp),
+            "p_max_near_outlier_peaks": near(op)}
+    return out
 
 
 def batch_row(torch, ucp, ctx, dev, steps, flush):

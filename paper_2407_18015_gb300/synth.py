@@ -23,6 +23,9 @@ smooth multi-scale base fields, tens of members, unimodal/bimodal noise):
   batch_specs       64 fields: H, W log-uniform integers in [128, 2048],
                     N in {10, 20, 50, 100}, model in {uniform, Epanechnikov,
                     histogram-16}, type in {min, max}
+  ensemble_gmm_outliers  50 members with two sharp Gaussian peaks on the NW-SE
+                    diagonal, the last 10 rotated by 90 degrees (outliers), as
+                    in the paper's model-comparison ensemble
 """
 import math
 
@@ -119,3 +122,34 @@ def batch_field(spec, scale=1.0):
     H = max(1, int(round(spec["H"] * scale)))
     W = max(1, int(round(spec["W"] * scale)))
     return ensemble_bimodal(H, W, spec["N"], seed=spec["seed"])
+
+
+def ensemble_gmm_outliers(H=64, W=64, N=50, outliers=10, seed=6, amp=1.0, width=0.025,
+                          noise=0.01, jitter=0.0):
+    """Two-peak Gaussian-mixture ensemble with rotated outlier members (the
+    structure of the paper's model-comparison ensemble): the first N -
+    outliers members have their two peaks on the NW-SE diagonal at (0.3, 0.3)
+    and (0.7, 0.7) of the unit square (row y grows southwards); the last
+    `outliers` members are the same field rotated by 90 degrees (peaks on the
+    NE-SW diagonal).  Peak positions are jittered per member by N(0, jitter^2),
+    and i.i.d. N(0, noise^2) is added.  Returns (ens, true_peaks, outlier_peaks)
+    with the peaks as (y, x) grid indices."""
+    rng = np.random.default_rng(seed)
+    yy = (np.arange(H, dtype=np.float64)[:, None] + 0.5) / H
+    xx = (np.arange(W, dtype=np.float64)[None, :] + 0.5) / W
+    true_c = [(0.3, 0.3), (0.7, 0.7)]
+    out_c = [(0.3, 0.7), (0.7, 0.3)]
+    ens = np.empty((N, H, W), np.float32)
+    for k in range(N):
+        cs = out_c if k >= N - outliers else true_c
+        f = np.zeros((H, W))
+        for (cy, cx) in cs:
+            cy += rng.normal(0, jitter)
+            cx += rng.normal(0, jitter)
+            f += amp * np.exp(-((yy - cy) ** 2 + (xx - cx) ** 2) / (2 * width ** 2))
+        f += rng.normal(0, noise, (H, W))
+        ens[k] = f.astype(np.float32)
+
+    def idx(cs):
+        return [(int(cy * H), int(cx * W)) for (cy, cx) in cs]
+    return ens, idx(true_c), idx(out_c)
