@@ -182,15 +182,19 @@ struct ucp_batch {
 namespace {
 
 size_t tile_smem(const BatchItem &b) {
-  const int P = b.model == kHist ? 2 + b.f.B : 2;
-  const int TYv = kTileHeights[b.th];
-  return (size_t)P * (TYv + 2) * 34 * sizeof(float);
+  return (size_t)tile_floats(b.model, b.f.B, kTileHeights[b.th]) * sizeof(float);
 }
 
-// order, tile and upload a list (synchronous: not inside a stream capture)
+// dynamic shared memory one CTA may use on this architecture (227 KB)
+constexpr size_t kSmemPerBlock = 227 * 1024;
+
+// order, tile and upload a list (synchronous: not inside a stream capture);
+// an item whose tile at the requested height would not fit in shared memory
+// (histograms with many bins) takes the next lower height
 int finalize(ucp_batch *b, std::vector<BatchItem> list, const int *th) {
   for (auto &it : list) {
     it.th = th[it.model];
+    while (it.th > 0 && tile_smem(it) > kSmemPerBlock) --it.th;
     it.tiles_x = (it.f.W + 31) / 32;
   }
   std::stable_sort(list.begin(), list.end(), [](const BatchItem &x, const BatchItem &y) {

@@ -141,21 +141,19 @@ cudaError_t launch_fit(const Field &f, int model, cudaStream_t s) {
 template <int MODEL, bool FM, bool SADDLE>
 static cudaError_t launch_tile(const Field &f, cudaStream_t s) {
   constexpr int TYm = TileH<MODEL>::value;
-  constexpr int HALOm = (TYm + 2) * HX;
-  const int P = MODEL == kSemi ? 2 + 2 * f.B : (MODEL == kHist ? 2 + f.B : 2);
-  const size_t smem = (size_t)P * HALOm * sizeof(float);
+  const size_t smem = (size_t)tile_floats(MODEL, f.B, TYm) * sizeof(float);
   static bool attr_set[128] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
   if (!attr_set[dev]) {
-    // the largest parameter tile of this model (64 bins; the estimator also
-    // keeps the running mass sums): 158 KB at 18 x 34, 173 KB at 10 x 34
-    const int Pmax = MODEL == kSemi ? 2 + 2 * kMaxBins : (MODEL == kHist ? 2 + kMaxBins : 2);
+    // the largest tile of this model (64 bins; the histogram adds its tail
+    // table, total, status and ordering scratch, the estimator its running
+    // mass sums): 169 KB at 18 x 34, 173 KB at 10 x 34
     e = cudaFuncSetAttribute(tile_kernel<MODEL, FM, SADDLE>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)((size_t)Pmax * HALOm * sizeof(float)));
+                             (int)((size_t)tile_floats(MODEL, kMaxBins, TYm) * sizeof(float)));
     if (e != cudaSuccess) {
       cudaGetLastError();  // do not leave the failed call as the last error
       return e;

@@ -762,82 +762,107 @@ __device__ __forceinline__ void semi_vertex(const float *w, const float *C, int 
 // ---------------------------------------------------------------------------
 // closed-form integration, histogram model (breakpoint merge)
 
-// A neighbour's survival G(x) (mixture form) as a walk over its segments:
-// before the support G = T; on bin k G = S_k - w_k (x - e_k) / h; after it 0.
-// A point mass is a histogram without bins (one jump from T to 0).  An absent
-// neighbour is the constant 1 (S = 1, slope 0, never advances); its "total"
-// is set to 2 so that the CDF complement T - G is 1 as well.
-struct HistWalk {
-  int ptr;          // shared-memory index of the next bin's mass
-  int left;         // edges still to cross (B + 1 before the support, 0 after)
-  float kf;         // index of the next edge
-  float lam, h, invh, end;  // local support start, bin width, 1/h, local end
-  float el, nx, S, sl;      // current segment: left edge, next edge, G(el), slope
-  bool point;       // a point mass: G jumps from T to 0 at its only edge
-  __device__ __forceinline__ void init_absent() {
-    ptr = 0; left = 0; kf = 0.f; lam = kFar; h = 1.f; invh = 0.f; end = kFar;
-    el = 0.f; nx = kFar; S = 1.f; sl = 0.f; point = false;
-  }
-  __device__ __forceinline__ void init(int off_, int B_, float lam_, float h_, float end_,
-                                       float T) {
-    ptr = off_; left = B_ + 1; kf = 0.f;
-    lam = lam_; h = h_; invh = B_ > 0 ? frcp(h_) : 0.f; end = end_;
-    el = -kFar; nx = lam_; S = T; sl = 0.f; point = B_ == 0;
-  }
-  // cross the next edge, where G has the value g (G is continuous at a bin
-  // edge; a point mass drops to 0)
-  template <int WS>
-  __device__ __forceinline__ void cross(const float *w, float g) {
-    el = nx;
-    S = point ? 0.f : g;
-    --left;
-    kf += 1.f;
-    sl = left > 0 ? w[ptr] * invh : 0.f;
-    ptr += WS;
-    nx = left > 1 ? fmaf(kf, h, lam) : (left == 1 ? end : kFar);
+// Shared-memory layout of a staged histogram vertex after the tail-table pass
+// (row r at sm[r * WS + l]): 0 lo, 1 hi, 2 + k the tail S_k = T - (m_0 + ...
+// + m_{k-1}) for k = 0..B+1 (S_0 = T, S_B = S_{B+1} = 0; all 0 for a point
+// mass), 4 + B the total mass T, 5 + B the status bits.  On bin k the
+// survival is G(x) = S_k - (S_k - S_{k+1}) (x - e_k) / h.
+__host__ __device__ constexpr int hist_rows(int B) { return B + 6; }
+
+// buckets of the per-tile ordering of histogram walks by length (a walk has
+// at most B + 4 (B + 1) pieces)
+constexpr int kSortBuckets = 5 * kMaxBins + 8;
+
+// A neighbour's survival G(x) (mixture form) walked segment by segment over
+// its edges lam + j h, j = 0..B: before the support G = T, on bin k the
+// segment above, after the support 0.  A point mass has h = 0: all its edges
+// coincide and G jumps from T to 0 there.  An absent neighbour is the
+// constant 1 that never reaches an edge.
+struct HistSeg {
+  int addr;                 // table index of the tail read at the next crossing
+  float kf;                 // index of the next edge (B + 1: none left)
+  float lam, h, invh;       // support start, bin width, 1/h (0 for a point mass)
+  float el, nx, s, sn, sl;  // segment start, next edge, S_k, S_{k+1}, slope
+  __device__ __forceinline__ void init_absent(int off, float Bf) {
+    addr = off; kf = Bf + 1.f; lam = h = invh = 0.f;
+    el = -kFar; nx = kFar; s = sn = 1.f; sl = 0.f;
   }
   template <int WS>
-  __device__ __forceinline__ void advance(const float *w) { cross<WS>(w, G(nx)); }
-  __device__ __forceinline__ float G(float x) const { return fmaf(-sl, x - el, S); }
+  __device__ __forceinline__ void init(const float *S0, int off, float lam_, float h_, float T) {
+    addr = off + WS; kf = 0.f;
+    lam = lam_; h = h_; invh = h_ > 0.f ? frcp(h_) : 0.f;
+    el = -kFar; nx = lam_; s = T; sn = S0[off]; sl = 0.f;
+  }
+  // One merge step at x1 (x1 < kFar): cross the next edge if it is at or
+  // below x1 (then enter the next bin: S_k <- S_{k+1}, read S_{k+2}), else
+  // keep the segment.  No branch; the table read always has a valid address:
+  // after its last edge nx = kFar, so a walker crosses at most B + 1 edges,
+  // and the table ends two rows after S_B.  Returns whether it crossed.
+  template <int WS>
+  __device__ __forceinline__ bool step(const float *S0, float x1, float Bf) {
+    const bool c = nx <= x1;
+    const float t = S0[addr];
+    s = c ? sn : s;
+    sn = c ? t : sn;
+    addr += c ? WS : 0;
+    sl = (s - sn) * invh;
+    el = c ? x1 : el;
+    kf = c ? kf + 1.f : kf;
+    nx = c ? (kf <= Bf ? fmaf(kf, h, lam) : kFar) : nx;
+    return c;
+  }
+  __device__ __forceinline__ float G(float x) const { return fmaf(-sl, x - el, s); }
 };
 
 // Both probabilities of a non-degenerate histogram centre in one walk over
-// [0, W1] (local frame at lo1): all bin edges of the centre and of the
-// neighbours are merged in increasing order; on each piece the centre pdf is
-// the constant w_j / h1 and each factor is linear, so the piece integral is
-// the Bernstein mean of the factor end values.  Beyond a neighbour's support
-// its survival is 0, before it its CDF is 0, so both integrals can run over
-// the centre's whole support.  Pieces are summed per centre bin and the bin
-// sums (times the bin density) with Kahan compensation.
+// [0, W1] (local frame at lo1, centre tail table Sc): all bin edges of the
+// centre and of the neighbours are merged in increasing order; on each piece
+// the centre pdf is the constant m_j / h1 and each factor is linear, so the
+// piece integral is the Bernstein mean of the factor end values.  Beyond a
+// neighbour's support its survival is 0, before it its CDF is 0, so both
+// integrals run over the centre's whole support.  Every lane executes the
+// same instructions on every step (the crossings are predicated, one edge or
+// a tie per step), so a warp stays converged until its lanes run out of
+// pieces.
 // SADDLE = false: (pmin, pmax) = (int pdf prod G, int pdf prod F).
 // SADDLE = true:  (pmin, pmax) = (t1, t2) with factor i = G_i if sg[i] > 0
 // else F_i for t1, and the other one for t2 (absent neighbours are 1 in both).
 template <int WS, bool SADDLE = false>
-__device__ __forceinline__ void hist_walk(const float *w, int coff, int B, float W1,
-                                          HistWalk *nw, const float *T, unsigned want,
+__device__ __forceinline__ void hist_walk(const float *S0, int coff, int B, float W1,
+                                          HistSeg *nw, const float *T, unsigned want,
                                           float &pmin, float &pmax, const int *sg = nullptr) {
-  const float h1 = W1 / (float)B, ih1 = frcp(h1);
-  int j1 = 0;
-  float e1 = (B > 1) ? h1 : W1;
-  float x0 = 0.f;
+  // every breakpoint of the walk is at most W1, below kFar
+  if (!(W1 <= 1e38f)) {
+    pmin = pmax = __int_as_float(0x7fc00000);
+    return;
+  }
+  const float Bf = (float)B;
+  const float h1 = W1 / Bf, ih1 = frcp(h1);
+  // centre: tails sc = S_k, scn = S_{k+1} of its bin k, next edge index kcf
+  int addr_c = coff + 2 * WS;
+  float kcf = 1.f;
+  float sc = S0[coff], scn = S0[coff + WS];
+  float dens = (sc - scn) * ih1;
+  float nxc = B > 1 ? h1 : W1;
   float Gl[4], Fl[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     Gl[i] = nw[i].G(0.f);
     Fl[i] = T[i] - Gl[i];
   }
-  Kahan amin, amax;
-  float bmin = 0.f, bmax = 0.f;
+  float amin = 0.f, amax = 0.f;
+  float x0 = 0.f;
   const int max_steps = 5 * (B + 2) + 4;
-  for (int step = 0; step < max_steps; ++step) {
-    float x1 = fminf(fminf(e1, W1), fminf(fminf(nw[0].nx, nw[1].nx), fminf(nw[2].nx, nw[3].nx)));
+  for (int step = 0; step < max_steps && x0 < W1; ++step) {
+    float x1 = fminf(fminf(nw[0].nx, nw[1].nx), fminf(nw[2].nx, nw[3].nx));
+    x1 = fmaxf(fminf(x1, nxc), x0);
     float Gr[4], Fr[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       Gr[i] = nw[i].G(x1);
       Fr[i] = T[i] - Gr[i];
     }
-    const float len = x1 - x0;
+    const float wgt = (x1 - x0) * dens;
     if constexpr (SADDLE) {
       float L1[4], R1[4], L2[4], R2[4];
 #pragma unroll
@@ -847,42 +872,39 @@ __device__ __forceinline__ void hist_walk(const float *w, int coff, int B, float
         L2[i] = sg[i] > 0 ? Fl[i] : Gl[i];
         R2[i] = sg[i] > 0 ? Fr[i] : Gr[i];
       }
-      bmin = fmaf(len, bern_mean<4>(L1, R1), bmin);
-      bmax = fmaf(len, bern_mean<4>(L2, R2), bmax);
+      amin = fmaf(wgt, bern_mean<4>(L1, R1), amin);
+      amax = fmaf(wgt, bern_mean<4>(L2, R2), amax);
     } else {
-      if (want & kMin) bmin = fmaf(len, bern_mean<4>(Gl, Gr), bmin);
-      if (want & kMax) bmax = fmaf(len, bern_mean<4>(Fl, Fr), bmax);
+      if (want & kMin) amin = fmaf(wgt, bern_mean<4>(Gl, Gr), amin);
+      if (want & kMax) amax = fmaf(wgt, bern_mean<4>(Fl, Fr), amax);
     }
-    const bool last = x1 >= W1;
-    if (last || e1 <= x1) {
-      const float p1 = w[coff + j1 * WS] * ih1;
-      amin.add(bmin * p1);
-      amax.add(bmax * p1);
-      bmin = bmax = 0.f;
-      ++j1;
-      e1 = (j1 + 1 < B) ? (float)(j1 + 1) * h1 : W1;
-    }
-    if (last) break;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       // the left value of the next piece is the new segment's value at x1
       // (the right value, except after a point mass)
-      if (nw[i].nx <= x1) {
-        nw[i].cross<WS>(w, Gr[i]);
-        Gr[i] = nw[i].S;
-        Fr[i] = T[i] - Gr[i];
-      }
-      Gl[i] = Gr[i];
-      Fl[i] = Fr[i];
+      const bool c = nw[i].step<WS>(S0, x1, Bf);
+      Gl[i] = c ? nw[i].s : Gr[i];
+      Fl[i] = T[i] - Gl[i];
+    }
+    {
+      const bool c = nxc <= x1;
+      const float t = S0[addr_c];
+      sc = c ? scn : sc;
+      scn = c ? t : scn;
+      addr_c += c ? WS : 0;
+      kcf = c ? kcf + 1.f : kcf;
+      nxc = c ? (kcf < Bf ? kcf * h1 : (kcf == Bf ? W1 : kFar)) : nxc;
+      dens = (sc - scn) * ih1;
     }
     x0 = x1;
   }
-  pmin = fmaxf(amin.get(), 0.f);
-  pmax = fmaxf(amax.get(), 0.f);
+  pmin = fmaxf(amin, 0.f);
+  pmax = fmaxf(amax, 0.f);
 }
 
-// survival and CDF of a histogram neighbour at a point v (degenerate centre)
-__device__ __forceinline__ void hist_tails_at(const float *w, int ws, int B, float lo, float hi,
+// survival and CDF of a histogram neighbour (tail table S, total T) at a
+// point v (degenerate centre)
+__device__ __forceinline__ void hist_tails_at(const float *S, int ws, int B, float lo, float hi,
                                               float T, float v, float &gt, float &lt) {
   if (lo == hi) {
     gt = lo > v ? T : 0.f;
@@ -898,13 +920,11 @@ __device__ __forceinline__ void hist_tails_at(const float *w, int ws, int B, flo
     return;
   }
   const float h = (hi - lo) / (float)B;
-  int j = min(max((int)floorf((v - lo) / h), 0), B - 1);
-  float C = 0.f;
-  for (int q = 0; q < j; ++q) C += w[q * ws];
-  const float wj = w[j * ws];
-  const float part = fminf(fmaxf((v - lo - (float)j * h) / h, 0.f), 1.f) * wj;
-  lt = C + part;
-  gt = fmaxf(T - lt, 0.f);
+  const int j = min(max((int)floorf((v - lo) / h), 0), B - 1);
+  const float fr = fminf(fmaxf((v - lo - (float)j * h) / h, 0.f), 1.f);
+  const float sj = S[j * ws], sj1 = S[(j + 1) * ws];
+  gt = fmaxf(fmaf(-fr, sj - sj1, sj), 0.f);
+  lt = fmaxf(T - gt, 0.f);
 }
 
 }  // namespace ucp

@@ -11,6 +11,119 @@ namespace ucp {
 
 __device__ __forceinline__ float qnan() { return __int_as_float(0x7fc00000); }
 
+// shared-memory floats of one tile of height TYv: the parameter rows of the
+// (TYv + 2) x 34 halo tile and, for the histogram, the tail-table rows and the
+// scratch of the walk ordering (buckets, then two 16-bit arrays of TYv x 32)
+__host__ __device__ constexpr long long tile_floats(int model, int B, int TYv) {
+  const long long halo = (long long)(TYv + 2) * 34;
+  return model == kSemi   ? (2 + 2LL * B) * halo
+         : model == kHist ? hist_rows(B) * halo + kSortBuckets + TYv * 32
+                          : 2 * halo;
+}
+
+// Number of pieces of the histogram walk of a tile vertex (0 for a vertex
+// that does not walk): the centre's B bins plus every neighbour edge inside
+// the centre's support.
+template <int HALO>
+__device__ __forceinline__ int hist_pieces(const float *sm, int B, int l, const bool *present,
+                                           const int *nl) {
+  const float lo1 = sm[l], hi1 = sm[HALO + l];
+  const int st = (int)sm[(5 + B) * HALO + l];
+  if (st != 0) return 0;
+  int c = B;
+  const float fb = (float)B;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if (!present[i]) continue;
+    const float lo = sm[nl[i]], hi = sm[HALO + nl[i]];
+    if (lo == hi) {
+      c += (lo > lo1 && lo < hi1) ? 1 : 0;
+      continue;
+    }
+    const float ih = fb / (hi - lo);
+    const float a = fminf(fmaxf((lo1 - lo) * ih, -1.f), fb + 1.f);
+    const float b = fminf(fmaxf((hi1 - lo) * ih, -1.f), fb + 1.f);
+    const int first = max((int)floorf(a) + 1, 0), last = min((int)ceilf(b) - 1, B);
+    c += max(last - first + 1, 0);
+  }
+  return min(c, 5 * B + 4);
+}
+
+// Orders the tile's vertices by decreasing walk length (a counting sort in
+// shared memory), so that the lanes of a warp take walks of about the same
+// number of pieces; returns the order (tile vertex indices).
+template <int TY, int HALO>
+__device__ __forceinline__ const unsigned short *hist_order(const Field &f, float *sm, int ty0,
+                                                           int tx0) {
+  constexpr int TX = 32, HX = TX + 2, NV = TY * TX;
+  static_assert(NV % NTHREADS == 0, "whole warps per pass");
+  const int B = f.B, NB = 5 * B + 5;
+  int *bucket = reinterpret_cast<int *>(sm + (long long)hist_rows(B) * HALO);
+  unsigned short *cnt = reinterpret_cast<unsigned short *>(bucket + kSortBuckets);
+  unsigned short *order = cnt + NV;
+  const int lane = threadIdx.x & 31;
+  for (int q = threadIdx.x; q < NB; q += NTHREADS) bucket[q] = 0;
+  __syncthreads();
+  for (int v = threadIdx.x; v < NV; v += NTHREADS) {
+    const int r = v / TX + 1, c = v % TX + 1;
+    const int gy = ty0 + r - 1, gx = tx0 + c - 1;
+    int n = 0;
+    if (gy < f.y1 && gx < f.W) {
+      const int l = r * HX + c;
+      bool present[4];
+      int nl[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int yy = gy + kDy[i], xx = gx + kDx[i];
+        present[i] = (yy >= 0 && yy < f.H && xx >= 0 && xx < f.W);
+        nl[i] = l + kDy[i] * HX + kDx[i];
+      }
+      n = hist_pieces<HALO>(sm, B, l, present, nl);
+    }
+    cnt[v] = (unsigned short)n;
+    const unsigned peers = __match_any_sync(0xffffffffu, n);
+    if (lane == __ffs(peers) - 1) atomicAdd(&bucket[n], __popc(peers));
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    // exclusive offsets in decreasing length order: lane takes `per`
+    // consecutive buckets from the top
+    const int per = (NB + 31) / 32;
+    int sum = 0;
+    for (int j = 0; j < per; ++j) {
+      const int b = NB - 1 - (lane * per + j);
+      if (b >= 0) sum += bucket[b];
+    }
+    int inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    int run = inc - sum;
+    for (int j = 0; j < per; ++j) {
+      const int b = NB - 1 - (lane * per + j);
+      if (b >= 0) {
+        const int k = bucket[b];
+        bucket[b] = run;
+        run += k;
+      }
+    }
+  }
+  __syncthreads();
+  for (int v = threadIdx.x; v < NV; v += NTHREADS) {
+    const int n = cnt[v];
+    const unsigned peers = __match_any_sync(0xffffffffu, n);
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&bucket[n], __popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    order[base + __popc(peers & ((1u << lane) - 1u))] = (unsigned short)v;
+  }
+  __syncthreads();
+  return order;
+}
+
 // Statistics of V consecutive vertices of one row (V = 1, or 4 with one
 // 16-byte load per member), written to the shared parameter tile at l.
 template <int V>
@@ -177,6 +290,11 @@ __device__ __forceinline__ void stage_vertex(const Field &f, float *sm, int l, l
 // histogram total mass
 template <int MODEL, int HALO>
 __device__ __forceinline__ uint8_t check_params(const float *sm, int l, int B, float &T) {
+  if constexpr (MODEL == kHist) {
+    // precomputed by the tail-table pass
+    T = sm[(4 + B) * HALO + l];
+    return (uint8_t)sm[(5 + B) * HALO + l];
+  }
   const float a = sm[l], b = sm[HALO + l];
   T = 1.f;
   if (!isfinite(a) || !isfinite(b)) return V_NONFINITE;
@@ -235,6 +353,36 @@ __device__ __forceinline__ void process_tile(const Field &f, int ty0, int tx0, f
     }
   }
   __syncthreads();
+  if constexpr (MODEL == kHist) {
+    // tail tables S_0..S_{B+1} in place of the masses, total mass and
+    // status of every staged vertex (rows 2..3+B, 4+B, 5+B)
+    const int B = f.B;
+    for (int l = threadIdx.x; l < HALO; l += NTHREADS) {
+      const float a = sm[l], b = sm[HALO + l];
+      uint8_t st = (!isfinite(a) || !isfinite(b)) ? V_NONFINITE
+                                                 : (a > b ? V_BAD : (a == b ? V_DEGENERATE : 0));
+      float t = 0.f;
+      for (int q = 0; q < B; ++q) {
+        const float w = sm[(2 + q) * HALO + l];
+        if (!isfinite(w)) st |= V_NONFINITE;
+        else if (w < 0.f) st |= V_BAD;
+        t += w;
+      }
+      const bool point = a == b;
+      float c = 0.f;
+      for (int q = 0; q < B; ++q) {
+        float *r = sm + (2 + q) * HALO + l;
+        const float w = *r;
+        *r = point ? 0.f : t - c;
+        c += w;
+      }
+      sm[(2 + B) * HALO + l] = 0.f;
+      sm[(3 + B) * HALO + l] = 0.f;
+      sm[(4 + B) * HALO + l] = t;
+      sm[(5 + B) * HALO + l] = (float)st;
+    }
+    __syncthreads();
+  }
   if constexpr (MODEL == kSemi) {
     // running mass sums C_1..C_B of every staged vertex, in bin order
     for (int l = threadIdx.x; l < HALO; l += NTHREADS) {
@@ -247,7 +395,12 @@ __device__ __forceinline__ void process_tile(const Field &f, int ty0, int tx0, f
     __syncthreads();
   }
 
-  for (int v = threadIdx.x; v < TY * TX; v += NTHREADS) {
+  [[maybe_unused]] const unsigned short *order = nullptr;
+  if constexpr (MODEL == kHist) order = hist_order<TY, HALO>(f, sm, ty0, tx0);
+
+  for (int it = threadIdx.x; it < TY * TX; it += NTHREADS) {
+    int v = it;
+    if constexpr (MODEL == kHist) v = order[it];
     const int r = v / TX + 1, c = v % TX + 1;
     const int gy = ty0 + r - 1, gx = tx0 + c - 1;
     if (gy >= f.y1 || gx >= f.W) continue;
@@ -344,29 +497,29 @@ __device__ __forceinline__ void process_tile(const Field &f, int ty0, int tx0, f
         }
         if (do_sad) psad = t1 + t2;
       } else if (do_mm || do_sad) {
-        HistWalk nw[4];
+        const float *S0 = sm + 2 * HALO;
+        HistSeg nw[4];
         float Tw[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          HistWalk &h = nw[i];
+          HistSeg &h = nw[i];
           if (!present[i]) {
-            h.init_absent();
+            h.init_absent(l, (float)B);
             Tw[i] = 2.f;  // CDF complement 2 - 1 = 1 for an absent neighbour
             continue;
           }
           Tw[i] = T[i];
           const float lo = sm[nl[i]], hi = sm[HALO + nl[i]];
-          if (lo == hi)
-            h.init(nl[i], 0, lo - lo1, 1.f, lo - lo1, T[i]);
-          else
-            h.init(nl[i], B, lo - lo1, (hi - lo) / (float)B, hi - lo1, T[i]);
-          for (int g = 0; g <= B && h.nx <= 0.f && h.left > 0; ++g) h.advance<HALO>(sm + 2 * HALO);
+          h.init<HALO>(S0, nl[i], lo - lo1, lo == hi ? 0.f : (hi - lo) / (float)B, T[i]);
+          // move to the segment that contains x = 0
+          for (int g = 0; g <= B && h.nx <= 0.f; ++g)
+            if (!h.step<HALO>(S0, h.nx, (float)B)) break;
         }
         if constexpr (!SADDLE) {
-          hist_walk<HALO>(sm + 2 * HALO, l, B, hi1 - lo1, nw, Tw, f.cptypes, pmin, pmax);
+          hist_walk<HALO>(S0, l, B, hi1 - lo1, nw, Tw, f.cptypes, pmin, pmax);
         } else {
           float t1, t2;
-          hist_walk<HALO, true>(sm + 2 * HALO, l, B, hi1 - lo1, nw, Tw, 0u, t1, t2, sg);
+          hist_walk<HALO, true>(S0, l, B, hi1 - lo1, nw, Tw, 0u, t1, t2, sg);
           psad = t1 + t2;
         }
       }
