@@ -66,8 +66,12 @@ def lib():
                                       ctypes.c_uint32, _d, _d, _d, _d, _d]
             L.orc_grad.argtypes = [_d, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_int, ctypes.c_int, _d, _d]
+            L.orc_prob_stencil.argtypes = [_d, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           _i64, ctypes.c_int64, _d, _d, _u8]
             for fn in ("orc_fit", "orc_prob", "orc_prob_at", "orc_prob_hist_h5_at",
-                       "orc_mvn_mc_at", "orc_grad", "orc_saddle", "orc_semi_at"):
+                       "orc_mvn_mc_at", "orc_grad", "orc_saddle", "orc_semi_at",
+                       "orc_prob_stencil"):
                 getattr(L, fn).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -138,6 +142,38 @@ def prob_at(params, model, idx, bins=0, boundary=0):
                            _p(pmin, _d), _p(pmax, _d), _p(st, _u8))
     if rc != 0:
         raise ValueError("orc_prob_at rejected its arguments")
+    return pmin, pmax, st
+
+
+STENCIL_4, STENCIL_6, STENCIL_8, STENCIL_3D6 = 0, 1, 2, 3
+
+
+def prob_stencil(params, model, stencil, bins=0, boundary=0, idx=None):
+    """P_min, P_max and status with the neighbour set of a stencil.  params:
+    [P][H][W] (2D stencils) or [P][D][H][W] (any stencil; D > 1 only for the
+    3D one).  Whole field (outputs shaped like one plane) or, with idx, the
+    linear vertex indices idx (outputs 1D)."""
+    params = _c64(params)
+    if params.ndim == 3:
+        D, (H, W) = 1, params.shape[1:]
+    else:
+        D, H, W = params.shape[1:]
+    if idx is None:
+        shape = params.shape[1:]
+        n = D * H * W
+        ip = None
+    else:
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        shape = (idx.size,)
+        n = idx.size
+        ip = _p(idx, _i64)
+    pmin = np.empty(shape, np.float64)
+    pmax = np.empty(shape, np.float64)
+    st = np.empty(shape, np.uint8)
+    rc = lib().orc_prob_stencil(_p(params, _d), D, H, W, model, bins, stencil, boundary, ip, n,
+                                _p(pmin, _d), _p(pmax, _d), _p(st, _u8))
+    if rc != 0:
+        raise ValueError("orc_prob_stencil rejected its arguments")
     return pmin, pmax, st
 
 

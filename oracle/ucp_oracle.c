@@ -38,6 +38,11 @@
  *   two-neighbour form (Eq. 1D-saddleProb) is used with X_2 the next
  *   neighbour (e, or s on a column) and X_3 the previous one (w, or n).
  *
+ * Larger neighbourhoods and 3D grids (the extension named in Sec.
+ * "Conclusion"): orc_prob_stencil evaluates the same P_min / P_max with the
+ * neighbour set of a 6- or 8-neighbour 2D stencil or of the 6 axis
+ * neighbours of a 3D grid (offsets listed at that function).
+ *
  * Distribution models (Sec. "Parametric Noise Models",
  * Sec. "Nonparametric Noise Models"):
  *   uniform      params (a, b):     pdf 1/(b-a) on [a, b]
@@ -83,7 +88,8 @@
 #define MAXB 64
 #define MAXE (MAXB + 1)
 #define MAXC 4   /* a factor is a polynomial of degree <= 3 on each interval */
-#define MAXPROD 24
+#define MAXK 8   /* neighbours per vertex, largest stencil                */
+#define MAXPROD 32  /* Epanechnikov with 8 neighbours: degree 2 + 3*8 = 26 */
 
 /* ------------------------------------------------------------------------ */
 /* threads                                                                  */
@@ -193,7 +199,7 @@ static int cmp_double(const void *a, const void *b) {
 
 /* integral over [lo, hi] of the product of nf piecewise polynomials */
 static double integrate_product(const pw_t *const *f, int nf, double lo, double hi) {
-  double pts[2 + 5 * MAXE + 8];
+  double pts[2 + (1 + MAXK) * MAXE + 8];
   int np = 0, i, j, k;
   double total = 0.0;
   if (!(hi > lo)) return 0.0;
@@ -347,7 +353,7 @@ static double prob_less(const dist_t *d, double c) {
 
 /* P_min (want_max = 0) or P_max (want_max = 1) of a centre with k neighbours */
 static double prob_vertex(const dist_t *v, const dist_t *nb, int k, int want_max) {
-  const pw_t *f[5];
+  const pw_t *f[1 + MAXK];
   int n;
   if (v->point) {
     double p = v->total;
@@ -522,6 +528,102 @@ int orc_saddle(const double *params, int H, int W, int model, int B, const int64
     int64_t i = idx ? idx[t] : t;
     out[t] = vertex_saddle(params, H, W, model, B, (int)(i / W), (int)(i % W),
                            status ? status + t : NULL);
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* larger neighbourhoods and 3D grids                                        */
+/*                                                                          */
+/* The paper's stated extension (Sec. "Conclusion"): six- or eight-pixel     */
+/* neighbourhoods of a triangulated 2D grid, and 3D grids.  The definition   */
+/* is unchanged -- P_min = int pdf_v prod_{n in N(v)} G_n, P_max with F_n -- */
+/* only the neighbour set N(v) comes from a stencil.  A D x H x W grid is    */
+/* stored slice-major ([P][D][H][W]); offsets are (dz, dy, dx):              */
+/*   stencil 0 (4):  e (0,0,1), n (0,-1,0), w (0,0,-1), s (0,1,0)           */
+/*   stencil 1 (6):  the 4 axis ones, ne (0,-1,1), sw (0,1,-1): the grid    */
+/*                   triangulated by cutting every cell along its           */
+/*                   lower-left to upper-right diagonal                     */
+/*   stencil 2 (8):  the 4 axis ones, ne, nw (0,-1,-1), sw, se (0,1,1)      */
+/*   stencil 3 (3D6): the 4 axis ones, below (-1,0,0), above (1,0,0)        */
+/* In-grid neighbours only (boundary mode 0), or 0 wherever the stencil is  */
+/* incomplete (boundary mode 1).                                            */
+
+static int stencil_offsets(int stencil, int off[MAXK][3]) {
+  static const int o4[4][3] = {{0, 0, 1}, {0, -1, 0}, {0, 0, -1}, {0, 1, 0}};
+  static const int o6[2][3] = {{0, -1, 1}, {0, 1, -1}};
+  static const int o8[4][3] = {{0, -1, 1}, {0, -1, -1}, {0, 1, -1}, {0, 1, 1}};
+  static const int oz[2][3] = {{-1, 0, 0}, {1, 0, 0}};
+  int k = 0, i, j;
+  if (stencil < 0 || stencil > 3) return -1;
+  for (i = 0; i < 4; ++i, ++k)
+    for (j = 0; j < 3; ++j) off[k][j] = o4[i][j];
+  if (stencil == 1)
+    for (i = 0; i < 2; ++i, ++k)
+      for (j = 0; j < 3; ++j) off[k][j] = o6[i][j];
+  if (stencil == 2)
+    for (i = 0; i < 4; ++i, ++k)
+      for (j = 0; j < 3; ++j) off[k][j] = o8[i][j];
+  if (stencil == 3)
+    for (i = 0; i < 2; ++i, ++k)
+      for (j = 0; j < 3; ++j) off[k][j] = oz[i][j];
+  return k;
+}
+
+static void vertex_min_max_stencil(const double *params, int D, int H, int W, int model, int B,
+                                   int stencil, int boundary, int64_t i, double *pmin,
+                                   double *pmax, uint8_t *status) {
+  int64_t plane = (int64_t)D * H * W, nidx[MAXK];
+  int off[MAXK][3], kfull = stencil_offsets(stencil, off), k = 0, n, st;
+  int z = (int)(i / ((int64_t)H * W)), y = (int)((i / W) % H), x = (int)(i % W);
+  int np = nparams(model, B);
+  double pv[2 + MAXB];
+  dist_t v, nb[MAXK];
+  for (n = 0; n < kfull; ++n) {
+    int zz = z + off[n][0], yy = y + off[n][1], xx = x + off[n][2];
+    if (zz < 0 || zz >= D || yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+    nidx[k++] = ((int64_t)zz * H + yy) * W + xx;
+  }
+  gather_params(params, plane, np, i, pv);
+  st = dist_make(model, pv, B, &v);
+  for (n = 0; n < k; ++n) {
+    double pn[2 + MAXB];
+    gather_params(params, plane, np, nidx[n], pn);
+    st |= dist_make(model, pn, B, &nb[n]) & (ST_NONFINITE | ST_BAD_PARAMS);
+  }
+  if (status) *status = (uint8_t)st;
+  if (st & (ST_NONFINITE | ST_BAD_PARAMS)) {
+    *pmin = *pmax = NAN;
+    return;
+  }
+  if (boundary == 1 && k < kfull) {
+    *pmin = *pmax = 0.0;
+    return;
+  }
+  *pmin = prob_vertex(&v, nb, k, 0);
+  *pmax = prob_vertex(&v, nb, k, 1);
+}
+
+/* Minimum and maximum probability with a stencil on a D x H x W grid
+ * (params [P][D][H][W] doubles), at every vertex (idx == NULL, outputs
+ * [D][H][W]) or at the linear indices idx[0..n-1].  Closed-form models
+ * only.  Returns -1 for an invalid model, stencil or shape. */
+int orc_prob_stencil(const double *params, int D, int H, int W, int model, int B, int stencil,
+                     int boundary, const int64_t *idx, int64_t n, double *out_min,
+                     double *out_max, uint8_t *status) {
+  int64_t t, total = (int64_t)D * H * W;
+  if (model != ORC_UNIFORM && model != ORC_EPAN && model != ORC_HIST) return -1;
+  if (stencil < 0 || stencil > 3 || D < 1 || H < 1 || W < 1) return -1;
+  if (stencil != 3 && D != 1) return -1;
+  if (!idx) n = total;
+#pragma omp parallel for schedule(dynamic, 64) num_threads(orc_get_threads())
+  for (t = 0; t < n; ++t) {
+    int64_t i = idx ? idx[t] : t;
+    double a, b;
+    vertex_min_max_stencil(params, D, H, W, model, B, stencil, boundary, i, &a, &b,
+                           status ? status + t : NULL);
+    if (out_min) out_min[t] = a;
+    if (out_max) out_max[t] = b;
   }
   return 0;
 }
