@@ -108,6 +108,28 @@ typedef enum { UCP_MIN = 1, UCP_MAX = 2 } ucp_cptype; /* bit mask */
 
 typedef enum { UCP_BOUNDARY_INGRID = 0, UCP_BOUNDARY_ZERO = 1 } ucp_boundary;
 
+/* Neighbour set of a vertex.  UCP_STENCIL_4 is the paper's (e, n, w, s).
+ * The others are the extension the paper names in Sec. "Conclusion"
+ * (six- or eight-pixel neighbourhoods of a triangulated grid, and 3D
+ * grids); offsets (dz, dy, dx):
+ *   UCP_STENCIL_6:   e, n, w, s, ne (0,-1,+1), sw (0,+1,-1) -- the grid with
+ *                    every cell cut along its lower-left to upper-right
+ *                    diagonal (y grows southwards)
+ *   UCP_STENCIL_8:   e, n, w, s, ne, nw (0,-1,-1), sw, se (0,+1,+1)
+ *   UCP_STENCIL_3D6: e, n, w, s, below (-1,0,0), above (+1,0,0) on a
+ *                    D x H x W grid (ucp_model_desc.depth = D)
+ * The larger stencils give P_min / P_max of the closed-form models
+ * (uniform, Epanechnikov, histogram) through ucp_probability,
+ * ucp_probability_from_params and ucp_fit; other entry points and models
+ * return UCP_ERR_UNSUPPORTED for them.  UCP_BOUNDARY_ZERO writes 0 wherever
+ * the stencil is incomplete. */
+typedef enum {
+  UCP_STENCIL_4 = 0,
+  UCP_STENCIL_6 = 1,
+  UCP_STENCIL_8 = 2,
+  UCP_STENCIL_3D6 = 3
+} ucp_stencil;
+
 typedef enum {
   UCP_OK = 0,
   UCP_ERR_ARG = 1,         /* null pointer, bad enum, bins/samples out of range */
@@ -135,6 +157,12 @@ typedef struct {
   uint64_t seed;          /* MVN Philox key                                     */
   uint32_t field_id;      /* MVN Philox counter word 2                          */
   int boundary;           /* ucp_boundary                                       */
+  int stencil;            /* ucp_stencil (0 = the paper's four neighbours)      */
+  int depth;              /* slices D of a 3D grid (UCP_STENCIL_3D6 only; 0 or
+                             1 = a 2D grid).  With D > 1 every array of a call
+                             has D slices: ens[N][D][H][W], params[P][D][H][W],
+                             outputs and status [D][H][W]; H and W are the
+                             slice sizes.                                       */
 } ucp_model_desc;
 
 /* Text of a status code (static storage). */

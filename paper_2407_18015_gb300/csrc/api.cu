@@ -51,8 +51,17 @@ int valid_desc(const ucp_model_desc *d, bool allow_sampled) {
     return UCP_ERR_ARG;
   if (sampled && d->mc_samples < 1) return UCP_ERR_ARG;
   if (d->boundary != UCP_BOUNDARY_INGRID && d->boundary != UCP_BOUNDARY_ZERO) return UCP_ERR_ARG;
+  if (d->stencil < UCP_STENCIL_4 || d->stencil > UCP_STENCIL_3D6 || d->depth < 0)
+    return UCP_ERR_ARG;
+  if (d->depth > 1 && d->stencil != UCP_STENCIL_3D6) return UCP_ERR_ARG;
+  if (d->stencil != UCP_STENCIL_4 && d->model > UCP_HISTOGRAM) return UCP_ERR_UNSUPPORTED;
   return UCP_OK;
 }
+
+// the larger-stencil path (stencil.cu) instead of the four-neighbour one
+bool uses_stencil(const ucp_model_desc *d) { return d->stencil != UCP_STENCIL_4; }
+
+int slices(const ucp_model_desc *d) { return d->depth > 1 ? d->depth : 1; }
 
 int valid_shape(long long N, long long H, long long W) {
   if (N < 1 || H < 1 || W < 1) return UCP_ERR_SHAPE;
@@ -162,7 +171,8 @@ int ucp_fit(ucp_ctx *ctx, const float *ens, int N, int H, int W, const ucp_model
   if (!ctx || !ens || !params) return UCP_ERR_ARG;
   int rc = valid_desc(desc, true);
   if (rc) return rc;
-  if ((rc = valid_shape(N, H, W))) return rc;
+  if ((rc = valid_shape(N, (long long)slices(desc) * H, W))) return rc;
+  H *= slices(desc);  // the fit is per vertex: D slices are D * H rows
   DeviceGuard g(ctx->device);
   if (g.err != cudaSuccess) return ucp_set_error(ctx, g.err);
   Field f{};
@@ -206,16 +216,66 @@ static int probability_impl(ucp_ctx *ctx, const float *ens, const float *params,
   return ucp_set_error(ctx, e);
 }
 
+// minimum / maximum with a larger stencil: statistics pass into workspace
+// (from members), tail tables (histogram), then one thread per vertex
+static int stencil_impl(ucp_ctx *ctx, const float *ens, const float *params, int N, int H,
+                        int W, const ucp_model_desc *desc, unsigned cptypes, float *out_min,
+                        float *out_max, uint8_t *vertex_status, cudaStream_t stream) {
+  const int D = slices(desc);
+  const long long V = (long long)D * H * W;
+  const int B = desc->bins;
+  const int P = param_planes(desc->model, B);
+  const size_t fit_floats = ens ? (size_t)P * V : 0;
+  const size_t tab_floats = desc->model == UCP_HISTOGRAM ? (size_t)(B + 4) * V : 0;
+  int rc = ucp_ensure_work(ctx, (fit_floats + tab_floats) * sizeof(float) + 256);
+  if (rc) return rc;
+  float *work = static_cast<float *>(ctx->work);
+  cudaError_t e = cudaSuccess;
+  if (ens) {
+    Field f{};
+    f.ens = ens;
+    f.params = work;
+    f.plane = V;
+    f.N = N; f.H = D * H; f.W = W; f.B = B;
+    f.y0 = 0; f.y1 = D * H;
+    f.epan_scale = epan_scale(desc);
+    e = launch_fit(f, desc->model, stream);
+    params = work;
+  }
+  float *tab = nullptr;
+  if (e == cudaSuccess && desc->model == UCP_HISTOGRAM) {
+    tab = work + fit_floats;
+    e = launch_hist_table(params, V, B, tab, ctx->sm_count, stream);
+  }
+  if (e == cudaSuccess) {
+    StencilField s{};
+    s.params = params;
+    s.tab = tab;
+    s.out_min = out_min;
+    s.out_max = out_max;
+    s.status = vertex_status;
+    s.V = V;
+    s.D = D; s.H = H; s.W = W; s.B = B;
+    s.boundary = desc->boundary;
+    s.cptypes = cptypes;
+    e = launch_stencil(s, desc->model, desc->stencil, ctx->sm_count, stream);
+  }
+  return ucp_set_error(ctx, e);
+}
+
 int ucp_probability_from_params(ucp_ctx *ctx, const float *params, int H, int W,
                                 const ucp_model_desc *desc, unsigned cptypes, float *out_min,
                                 float *out_max, uint8_t *vertex_status, ucp_stream stream) {
   if (!ctx || !params) return UCP_ERR_ARG;
   int rc = valid_desc(desc, true);
   if (rc) return rc;
-  if ((rc = valid_shape(1, H, W))) return rc;
+  if ((rc = valid_shape(1, (long long)slices(desc) * H, W))) return rc;
   if ((rc = valid_types(cptypes, out_min, out_max))) return rc;
   DeviceGuard g(ctx->device);
   if (g.err != cudaSuccess) return ucp_set_error(ctx, g.err);
+  if (uses_stencil(desc))
+    return stencil_impl(ctx, nullptr, params, 1, H, W, desc, cptypes, out_min, out_max,
+                        vertex_status, (cudaStream_t)stream);
   return probability_impl(ctx, nullptr, params, 1, H, W, desc, cptypes, out_min, out_max,
                           vertex_status, (cudaStream_t)stream);
 }
@@ -226,10 +286,13 @@ int ucp_probability(ucp_ctx *ctx, const float *ens, int N, int H, int W,
   if (!ctx || !ens) return UCP_ERR_ARG;
   int rc = valid_desc(desc, true);
   if (rc) return rc;
-  if ((rc = valid_shape(N, H, W))) return rc;
+  if ((rc = valid_shape(N, (long long)slices(desc) * H, W))) return rc;
   if ((rc = valid_types(cptypes, out_min, out_max))) return rc;
   DeviceGuard g(ctx->device);
   if (g.err != cudaSuccess) return ucp_set_error(ctx, g.err);
+  if (uses_stencil(desc))
+    return stencil_impl(ctx, ens, nullptr, N, H, W, desc, cptypes, out_min, out_max,
+                        vertex_status, (cudaStream_t)stream);
   return probability_impl(ctx, ens, nullptr, N, H, W, desc, cptypes, out_min, out_max,
                           vertex_status, (cudaStream_t)stream);
 }
@@ -265,6 +328,7 @@ int ucp_saddle(ucp_ctx *ctx, const float *ens, int N, int H, int W, const ucp_mo
   if (!ctx || !ens || !out_saddle) return UCP_ERR_ARG;
   int rc = valid_desc(desc, true);
   if (rc) return rc;
+  if (uses_stencil(desc)) return UCP_ERR_UNSUPPORTED;
   if ((rc = valid_shape(N, H, W))) return rc;
   DeviceGuard g(ctx->device);
   if (g.err != cudaSuccess) return ucp_set_error(ctx, g.err);
@@ -278,6 +342,7 @@ int ucp_saddle_from_params(ucp_ctx *ctx, const float *params, int H, int W,
   if (!ctx || !params || !out_saddle) return UCP_ERR_ARG;
   int rc = valid_desc(desc, true);
   if (rc) return rc;
+  if (uses_stencil(desc)) return UCP_ERR_UNSUPPORTED;
   if ((rc = valid_shape(1, H, W))) return rc;
   DeviceGuard g(ctx->device);
   if (g.err != cudaSuccess) return ucp_set_error(ctx, g.err);
@@ -291,6 +356,7 @@ int ucp_probability_host(ucp_ctx *ctx, const float *ens_host, int N, int H, int 
   if (!ctx || !ens_host) return UCP_ERR_ARG;
   int rc = valid_desc(desc, true);
   if (rc) return rc;
+  if (uses_stencil(desc)) return UCP_ERR_UNSUPPORTED;
   if ((rc = valid_shape(N, H, W))) return rc;
   if ((rc = valid_types(cptypes, out_min_host, out_max_host))) return rc;
   DeviceGuard g(ctx->device);
@@ -316,6 +382,7 @@ int ucp_backward(ucp_ctx *ctx, const float *params, int H, int W, const ucp_mode
   if (!ctx || !params || !weight || !grad_params) return UCP_ERR_ARG;
   int rc = valid_desc(desc, false);
   if (rc) return rc;
+  if (uses_stencil(desc)) return UCP_ERR_UNSUPPORTED;
   if (cptype != UCP_MIN && cptype != UCP_MAX) return UCP_ERR_ARG;
   if ((rc = valid_shape(1, H, W))) return rc;
   DeviceGuard g(ctx->device);

@@ -290,6 +290,7 @@ int ucp_batch_add(ucp_batch *batch, const float *ens, int N, int H, int W,
     return UCP_ERR_ARG;
   if (desc->boundary != UCP_BOUNDARY_INGRID && desc->boundary != UCP_BOUNDARY_ZERO)
     return UCP_ERR_ARG;
+  if (desc->stencil != UCP_STENCIL_4 || desc->depth > 1) return UCP_ERR_UNSUPPORTED;
   if (N < 1 || H < 1 || W < 1 || (long long)H * W > 0xFFFFFFFFLL) return UCP_ERR_SHAPE;
   if (cptypes == 0 || (cptypes & ~3u)) return UCP_ERR_ARG;
   if (((cptypes & 1u) && !out_min) || ((cptypes & 2u) && !out_max)) return UCP_ERR_ARG;

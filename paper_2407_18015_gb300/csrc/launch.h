@@ -43,6 +43,25 @@ cudaError_t launch_mvn_fit(const Field &f, cudaStream_t s);
 cudaError_t launch_mvn_mc(const Field &f, bool from_members, int samples, uint64_t seed,
                           uint32_t field_id, cudaStream_t s);
 
+// Larger neighbour sets (stencil.cu): one thread per vertex of a D x H x W
+// grid, parameters [P][D][H][W] in global memory, histogram tail tables
+// [D*H*W][B+4] (see stencil.cuh).
+struct StencilField {
+  const float *params;  // [P][D][H][W]
+  const float *tab;     // histogram tail-table rows, or nullptr
+  float *out_min;       // [D][H][W] or nullptr
+  float *out_max;       // [D][H][W] or nullptr
+  uint8_t *status;      // [D][H][W] or nullptr
+  long long V;          // D * H * W
+  int D, H, W, B;
+  int boundary;
+  unsigned cptypes;
+};
+cudaError_t launch_hist_table(const float *params, long long V, int B, float *tab, int sm_count,
+                              cudaStream_t s);
+cudaError_t launch_stencil(const StencilField &f, int model, int stencil, int sm_count,
+                           cudaStream_t s);
+
 // Adjoint: partial rows into `rows` ([5][Q][H][W]) then the gather into grad.
 cudaError_t launch_backward(const Field &f, int model, int cptype, const float *weight,
                             float *rows, float *grad, cudaStream_t s);

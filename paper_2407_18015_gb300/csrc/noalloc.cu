@@ -69,6 +69,7 @@ extern "C" int ucp_backward_static(const float *params, int H, int W,
     return UCP_ERR_ARG;
   if (desc->boundary != UCP_BOUNDARY_INGRID && desc->boundary != UCP_BOUNDARY_ZERO)
     return UCP_ERR_ARG;
+  if (desc->stencil != UCP_STENCIL_4 || desc->depth > 1) return UCP_ERR_UNSUPPORTED;
   if (cptype != UCP_MIN && cptype != UCP_MAX) return UCP_ERR_ARG;
   if (H < 1 || W < 1) return UCP_ERR_SHAPE;
   const size_t Q = desc->model == UCP_HISTOGRAM ? (size_t)desc->bins : 2;

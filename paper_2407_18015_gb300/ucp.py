@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(HERE, "libucp.so")
 UCP_UNIFORM, UCP_EPANECHNIKOV, UCP_HISTOGRAM, UCP_MVN_MC, UCP_HISTOGRAM_SEMI = 0, 1, 2, 3, 4
 UCP_MIN, UCP_MAX = 1, 2
 UCP_BOUNDARY_INGRID, UCP_BOUNDARY_ZERO = 0, 1
+UCP_STENCIL_4, UCP_STENCIL_6, UCP_STENCIL_8, UCP_STENCIL_3D6 = 0, 1, 2, 3
 UCP_OK, UCP_ERR_ARG, UCP_ERR_SHAPE, UCP_ERR_CUDA, UCP_ERR_NOMEM, UCP_ERR_TIMEOUT, \
     UCP_ERR_UNSUPPORTED = range(7)
 UCP_V_DEGENERATE, UCP_V_NONFINITE, UCP_V_BAD_PARAMS, UCP_V_CHOL_JITTER, UCP_V_CHOL_FAIL = \
@@ -34,7 +35,7 @@ class ucp_model_desc(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int), ("bins", ctypes.c_int),
                 ("epan_width_scale", ctypes.c_float), ("mc_samples", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("field_id", ctypes.c_uint32),
-                ("boundary", ctypes.c_int)]
+                ("boundary", ctypes.c_int), ("stencil", ctypes.c_int), ("depth", ctypes.c_int)]
 
 
 class UcpError(RuntimeError):
@@ -137,11 +138,24 @@ def _stream(stream=None, device=None):
 
 
 def make_desc(model="uniform", bins=8, epan_width_scale=0.0, mc_samples=10000, seed=0x5EED,
-              field_id=0, boundary=UCP_BOUNDARY_INGRID):
+              field_id=0, boundary=UCP_BOUNDARY_INGRID, stencil=UCP_STENCIL_4, depth=0):
     m = MODELS[model] if isinstance(model, str) else int(model)
     return ucp_model_desc(m, int(bins), float(epan_width_scale), int(mc_samples),
                           int(seed) & 0xFFFFFFFFFFFFFFFF, int(field_id) & 0xFFFFFFFF,
-                          int(boundary))
+                          int(boundary), int(stencil), int(depth))
+
+
+def _grid(t, desc, name):
+    """(H, W) of a [lead][H][W] or [lead][D][H][W] tensor; D must be the
+    descriptor's depth (a 2D tensor needs depth 0 or 1)."""
+    D = desc.depth if desc.depth > 1 else 1
+    if t.dim() == 4:
+        if t.shape[1] != D:
+            raise ValueError(f"{name}: {t.shape[1]} slices but desc.depth = {desc.depth}")
+        return t.shape[2], t.shape[3]
+    if t.dim() != 3 or D != 1:
+        raise ValueError(f"{name}: expected [.][H][W] or [.][D][H][W] with D = desc.depth")
+    return t.shape[1], t.shape[2]
 
 
 def _check(rc, where, ctx=None):
@@ -171,7 +185,8 @@ def ucp_param_count(desc):
 
 
 def ucp_fit(ctx, ens, desc, params, vertex_status=None, stream=None):
-    N, H, W = ens.shape
+    N = ens.shape[0]
+    H, W = _grid(ens, desc, "ens")
     rc = lib().ucp_fit(ctx, _ptr(ens, torch.float32, name="ens"), N, H, W, ctypes.byref(desc),
                        _ptr(params, torch.float32, name="params"),
                        _ptr(vertex_status, torch.uint8, name="vertex_status"),
@@ -181,7 +196,7 @@ def ucp_fit(ctx, ens, desc, params, vertex_status=None, stream=None):
 
 def ucp_probability_from_params(ctx, params, desc, cptypes, out_min, out_max,
                                 vertex_status=None, stream=None):
-    _, H, W = params.shape
+    H, W = _grid(params, desc, "params")
     rc = lib().ucp_probability_from_params(
         ctx, _ptr(params, torch.float32, name="params"), H, W, ctypes.byref(desc), int(cptypes),
         _ptr(out_min, torch.float32, name="out_min"), _ptr(out_max, torch.float32, name="out_max"),
@@ -191,7 +206,8 @@ def ucp_probability_from_params(ctx, params, desc, cptypes, out_min, out_max,
 
 def ucp_probability(ctx, ens, desc, cptypes, out_min, out_max, vertex_status=None,
                     stream=None):
-    N, H, W = ens.shape
+    N = ens.shape[0]
+    H, W = _grid(ens, desc, "ens")
     rc = lib().ucp_probability(
         ctx, _ptr(ens, torch.float32, name="ens"), N, H, W, ctypes.byref(desc), int(cptypes),
         _ptr(out_min, torch.float32, name="out_min"), _ptr(out_max, torch.float32, name="out_max"),
@@ -314,28 +330,26 @@ class Context:
             pass
 
     def fit(self, ens, desc, with_status=False):
-        _, H, W = ens.shape
-        params = torch.empty((ucp_param_count(desc), H, W), dtype=torch.float32,
+        grid = tuple(ens.shape[1:])
+        params = torch.empty((ucp_param_count(desc),) + grid, dtype=torch.float32,
                              device=ens.device)
-        st = torch.empty((H, W), dtype=torch.uint8, device=ens.device) if with_status else None
+        st = torch.empty(grid, dtype=torch.uint8, device=ens.device) if with_status else None
         ucp_fit(self.handle, ens, desc, params, st)
         return (params, st) if with_status else params
 
-    def _outs(self, H, W, device, cptypes):
-        pmin = torch.empty((H, W), dtype=torch.float32, device=device) if cptypes & 1 else None
-        pmax = torch.empty((H, W), dtype=torch.float32, device=device) if cptypes & 2 else None
-        st = torch.empty((H, W), dtype=torch.uint8, device=device)
+    def _outs(self, grid, device, cptypes):
+        pmin = torch.empty(grid, dtype=torch.float32, device=device) if cptypes & 1 else None
+        pmax = torch.empty(grid, dtype=torch.float32, device=device) if cptypes & 2 else None
+        st = torch.empty(grid, dtype=torch.uint8, device=device)
         return pmin, pmax, st
 
     def probability(self, ens, desc, cptypes=UCP_MIN | UCP_MAX):
-        _, H, W = ens.shape
-        pmin, pmax, st = self._outs(H, W, ens.device, cptypes)
+        pmin, pmax, st = self._outs(tuple(ens.shape[1:]), ens.device, cptypes)
         ucp_probability(self.handle, ens, desc, cptypes, pmin, pmax, st)
         return pmin, pmax, st
 
     def probability_from_params(self, params, desc, cptypes=UCP_MIN | UCP_MAX):
-        _, H, W = params.shape
-        pmin, pmax, st = self._outs(H, W, params.device, cptypes)
+        pmin, pmax, st = self._outs(tuple(params.shape[1:]), params.device, cptypes)
         ucp_probability_from_params(self.handle, params, desc, cptypes, pmin, pmax, st)
         return pmin, pmax, st
 
