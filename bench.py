@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-rows", action="store_true", help="headline workload only")
-    ap.add_argument("--rows", default="mvn,fwdbwd,batch,saddle,gmm")
+    ap.add_argument("--rows", default="mvn,fwdbwd,batch,saddle,gmm,stencil")
     return ap.parse_args()
 
 
@@ -154,23 +154,21 @@ def hist_piece_counts(params, bins):
     return cnt
 
 
-# flops per merged piece of the histogram walk with both types: merge (5
-# compares), four linear factors at the new breakpoint and their CDF
-# complements (16), and for each type the Bernstein product of four linear
-# factors (24), its mean (10), scale and accumulate (3)
-HIST_FLOPS_PER_PIECE = 5 + 16 + 2 * (24 + 10 + 3)
-# Epanechnikov, per vertex and type: 5 pieces x 8 Gauss-Legendre nodes, the
-# density (5) and on average two active cubic survivals (2 x 9) per node,
-# product and weighted sum (4)
-EPAN_FLOPS_PER_VERTEX_TYPE = 5 * 8 * (5 + 2 * 9 + 4)
+# Algorithmic work per unit (the scope table's figures): a histogram piece
+# costs 3 Gauss-Legendre nodes x ~25 flops per type, an Epanechnikov vertex
+# 5 pieces x 8 nodes x ~35 flops per type; the uniform model is counted in
+# bytes (4N read + 4 per output type written).  Histogram pieces are counted
+# exactly from the data (hist_piece_counts).
+HIST_FLOPS_PER_PIECE_TYPE = 3 * 25
+EPAN_FLOPS_PER_VERTEX_TYPE = 5 * 8 * 35
 
 
 # DRAM bytes (read + write) per launch of each headline kernel from the ncu
-# capture summarised in profiles/tile_kernels_1024x1024x20.md; None once a
-# kernel has changed since its counters were taken
+# capture summarised in profiles/; None once a kernel has changed since its
+# counters were taken
 TRAFFIC_BYTES = {"uniform": 83.920384e6 + 4.575744e6,
                  "epanechnikov": 83.952640e6 + 4.481792e6,
-                 "histogram": 84.071424e6 + 5.210368e6}
+                 "histogram": None}
 
 
 def work_of(model, N, HW, params=None, bins=BINS2):
@@ -179,7 +177,7 @@ def work_of(model, N, HW, params=None, bins=BINS2):
     if model == "epanechnikov":
         return "alu", 2.0 * EPAN_FLOPS_PER_VERTEX_TYPE * HW
     pieces = float(hist_piece_counts(params, bins).sum().item())
-    return "alu", HIST_FLOPS_PER_PIECE * pieces
+    return "alu", 2.0 * HIST_FLOPS_PER_PIECE_TYPE * pieces
 
 
 # ---------------------------------------------------------------------------
@@ -477,7 +475,34 @@ def other_rows(torch, ucp, ctx, dev, args, flush, peaks):
         del e2
     if "gmm" in want:
         rows["gmm_outliers_64x64x50_max"] = gmm_row(torch, ucp, ctx, dev, steps, flush)
+    if "stencil" in want:
+        rows.update(stencil_rows(torch, ucp, ctx, dev, steps, flush))
     return rows
+
+
+def stencil_rows(torch, ucp, ctx, dev, steps, flush):
+    """Larger neighbour sets, fused fit + probability (min and max): the 6-
+    and 8-neighbour 2D stencils on the 1024x1024x20 workload and the 3D
+    axis stencil on a 64x128x128 grid (20 members, the same generator)."""
+    from paper_2407_18015_gb300 import synth
+    out = {}
+    for name, stencil, (D, H, W) in (("stencil6_1024x1024x20", ucp.UCP_STENCIL_6, (1, H2, W2)),
+                                     ("stencil8_1024x1024x20", ucp.UCP_STENCIL_8, (1, H2, W2)),
+                                     ("stencil3d6_64x128x128x20", ucp.UCP_STENCIL_3D6,
+                                      (64, 128, 128))):
+        e = synth.ensemble_bimodal(D * H, W, N2, seed=SEED2)
+        ens = torch.from_numpy(e.reshape((N2, D, H, W)) if D > 1 else e).to(dev)
+        grid = (D, H, W) if D > 1 else (H, W)
+        pm, px = torch.empty(grid, device=dev), torch.empty(grid, device=dev)
+        r = {}
+        for m, b in MODELS2:
+            d = ucp.make_desc(m, bins=b or 8, stencil=stencil, depth=D)
+            ms, _ = timed_steps(torch, lambda ev, d=d: ucp.ucp_probability(
+                ctx.handle, ens, d, 3, pm, px), steps, 2, flush)
+            r[m] = {"ms": ms / steps, "vertices_per_s": D * H * W / (ms / steps / 1e3)}
+        out[name] = r
+        del ens
+    return out
 
 
 def gmm_row(torch, ucp, ctx, dev, steps, flush):
