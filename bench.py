@@ -166,9 +166,9 @@ EPAN_FLOPS_PER_VERTEX_TYPE = 5 * 8 * 35
 # DRAM bytes (read + write) per launch of each headline kernel from the ncu
 # capture summarised in profiles/; None once a kernel has changed since its
 # counters were taken
-TRAFFIC_BYTES = {"uniform": 83.920384e6 + 4.575744e6,
-                 "epanechnikov": 83.952640e6 + 4.481792e6,
-                 "histogram": None}
+TRAFFIC_BYTES = {"uniform": 83.917568e6 + 4.117248e6,
+                 "epanechnikov": 83.953664e6 + 4.737536e6,
+                 "histogram": 83.976960e6 + 5.427968e6}
 
 
 def work_of(model, N, HW, params=None, bins=BINS2):
