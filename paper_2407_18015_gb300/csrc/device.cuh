@@ -117,6 +117,29 @@ __device__ __forceinline__ float bern_mean(const float *L, const float *R) {
   }
 }
 
+// bern_mean<4> of two products at once, one in each half of a float2, with
+// the packed FP32 instructions (each half rounds exactly as the scalar form)
+__device__ __forceinline__ float2 bern_mean4_x2(const float2 *L, const float2 *R) {
+  float2 e0 = L[0], e1 = R[0], e2, e3, e4;
+  e2 = __fmul2_rn(e1, R[1]);
+  e1 = __ffma2_rn(e0, R[1], __fmul2_rn(e1, L[1]));
+  e0 = __fmul2_rn(e0, L[1]);
+  e3 = __fmul2_rn(e2, R[2]);
+  e2 = __ffma2_rn(e1, R[2], __fmul2_rn(e2, L[2]));
+  e1 = __ffma2_rn(e0, R[2], __fmul2_rn(e1, L[2]));
+  e0 = __fmul2_rn(e0, L[2]);
+  e4 = __fmul2_rn(e3, R[3]);
+  e3 = __ffma2_rn(e2, R[3], __fmul2_rn(e3, L[3]));
+  e2 = __ffma2_rn(e1, R[3], __fmul2_rn(e2, L[3]));
+  e1 = __ffma2_rn(e0, R[3], __fmul2_rn(e1, L[3]));
+  e0 = __fmul2_rn(e0, L[3]);
+  const float2 w0 = make_float2(BernW<4, 0>::value, BernW<4, 0>::value);
+  const float2 w1 = make_float2(BernW<4, 1>::value, BernW<4, 1>::value);
+  const float2 w2 = make_float2(BernW<4, 2>::value, BernW<4, 2>::value);
+  return __ffma2_rn(__fadd2_rn(e0, e4), w0,
+                    __ffma2_rn(__fadd2_rn(e1, e3), w1, __fmul2_rn(e2, w2)));
+}
+
 // Sort four (key, payload...) tuples ascending by key with a 5-exchange network.
 template <int NP>
 __device__ __forceinline__ void cswap(float *k, float (*p)[4], int a, int b) {
@@ -844,47 +867,38 @@ __device__ __forceinline__ void hist_walk(const float *S0, int coff, int B, floa
   float sc = S0[coff], scn = S0[coff + WS];
   float dens = (sc - scn) * ih1;
   float nxc = B > 1 ? h1 : W1;
-  float Gl[4], Fl[4];
+  // factor end values, two products per float2: (G, F) for the minimum and
+  // maximum, (t1 factor, t2 factor) for the saddle
+  auto pair = [&](int i, float g, float f) {
+    if constexpr (SADDLE) return sg[i] > 0 ? make_float2(g, f) : make_float2(f, g);
+    else return make_float2(g, f);
+  };
+  float2 Pl[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    Gl[i] = nw[i].G(0.f);
-    Fl[i] = T[i] - Gl[i];
+    const float g = nw[i].G(0.f);
+    Pl[i] = pair(i, g, T[i] - g);
   }
-  float amin = 0.f, amax = 0.f;
+  float2 acc = make_float2(0.f, 0.f);
   float x0 = 0.f;
   const int max_steps = 5 * (B + 2) + 4;
   for (int step = 0; step < max_steps && x0 < W1; ++step) {
     float x1 = fminf(fminf(nw[0].nx, nw[1].nx), fminf(nw[2].nx, nw[3].nx));
     x1 = fmaxf(fminf(x1, nxc), x0);
-    float Gr[4], Fr[4];
+    float2 Pr[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      Gr[i] = nw[i].G(x1);
-      Fr[i] = T[i] - Gr[i];
+      const float g = nw[i].G(x1);
+      Pr[i] = pair(i, g, T[i] - g);
     }
     const float wgt = (x1 - x0) * dens;
-    if constexpr (SADDLE) {
-      float L1[4], R1[4], L2[4], R2[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        L1[i] = sg[i] > 0 ? Gl[i] : Fl[i];
-        R1[i] = sg[i] > 0 ? Gr[i] : Fr[i];
-        L2[i] = sg[i] > 0 ? Fl[i] : Gl[i];
-        R2[i] = sg[i] > 0 ? Fr[i] : Gr[i];
-      }
-      amin = fmaf(wgt, bern_mean<4>(L1, R1), amin);
-      amax = fmaf(wgt, bern_mean<4>(L2, R2), amax);
-    } else {
-      if (want & kMin) amin = fmaf(wgt, bern_mean<4>(Gl, Gr), amin);
-      if (want & kMax) amax = fmaf(wgt, bern_mean<4>(Fl, Fr), amax);
-    }
+    acc = __ffma2_rn(make_float2(wgt, wgt), bern_mean4_x2(Pl, Pr), acc);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       // the left value of the next piece is the new segment's value at x1
       // (the right value, except after a point mass)
       const bool c = nw[i].step<WS>(S0, x1, Bf);
-      Gl[i] = c ? nw[i].s : Gr[i];
-      Fl[i] = T[i] - Gl[i];
+      Pl[i] = c ? pair(i, nw[i].s, T[i] - nw[i].s) : Pr[i];
     }
     {
       const bool c = nxc <= x1;
@@ -898,8 +912,9 @@ __device__ __forceinline__ void hist_walk(const float *S0, int coff, int B, floa
     }
     x0 = x1;
   }
-  pmin = fmaxf(amin, 0.f);
-  pmax = fmaxf(amax, 0.f);
+  (void)want;
+  pmin = fmaxf(acc.x, 0.f);
+  pmax = fmaxf(acc.y, 0.f);
 }
 
 // survival and CDF of a histogram neighbour (tail table S, total T) at a

@@ -400,7 +400,14 @@ __device__ __forceinline__ void process_tile(const Field &f, int ty0, int tx0, f
 
   for (int it = threadIdx.x; it < TY * TX; it += NTHREADS) {
     int v = it;
-    if constexpr (MODEL == kHist) v = order[it];
+    if constexpr (MODEL == kHist) {
+      // pass j of warp w takes the j-th group of eight 32-vertex blocks of
+      // the ordered list, in reverse on odd passes, so that every warp gets
+      // about the same total length
+      const int j = it / NTHREADS, w = (threadIdx.x >> 5), nw = NTHREADS / 32;
+      const int blk = j * nw + ((j & 1) ? nw - 1 - w : w);
+      v = order[blk * 32 + (threadIdx.x & 31)];
+    }
     const int r = v / TX + 1, c = v % TX + 1;
     const int gy = ty0 + r - 1, gx = tx0 + c - 1;
     if (gy >= f.y1 || gx >= f.W) continue;
