@@ -6,7 +6,7 @@ package, and this package never imports the product package.
 
 Functions whose parity is pinned by the CPU test-suite (tests/test_oracle_*):
   fit, prob, prob_at, prob_hist_h5_at, mvn_mc_at, philox4x32_10, grad, saddle, semi_at,
-  prob_stencil.
+  prob_stencil, gauss.
 """
 from .oracle import (  # noqa: F401
     UNIFORM, EPANECHNIKOV, HISTOGRAM, MVN,
@@ -14,5 +14,5 @@ from .oracle import (  # noqa: F401
     build, lib, set_threads, get_threads,
     fit, prob, prob_at, prob_hist_h5_at, mvn_mc_at, philox4x32_10, grad,
     nparams, saddle, semi_at,
-    STENCIL_4, STENCIL_6, STENCIL_8, STENCIL_3D6, prob_stencil,
+    STENCIL_4, STENCIL_6, STENCIL_8, STENCIL_3D6, prob_stencil, GAUSSIAN, gauss,
 )

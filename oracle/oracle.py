@@ -12,6 +12,7 @@ import threading
 import numpy as np
 
 UNIFORM, EPANECHNIKOV, HISTOGRAM, MVN = 0, 1, 2, 3
+GAUSSIAN = 5
 ST_DEGENERATE, ST_NONFINITE, ST_BAD_PARAMS, ST_CHOL_JITTER, ST_CHOL_FAIL = 1, 2, 4, 8, 16
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -66,12 +67,14 @@ def lib():
                                       ctypes.c_uint32, _d, _d, _d, _d, _d]
             L.orc_grad.argtypes = [_d, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_int, ctypes.c_int, _d, _d]
+            L.orc_gauss.argtypes = [_d, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i64,
+                                    ctypes.c_int64, _d, _d, _d, _u8]
             L.orc_prob_stencil.argtypes = [_d, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            _i64, ctypes.c_int64, _d, _d, _u8]
             for fn in ("orc_fit", "orc_prob", "orc_prob_at", "orc_prob_hist_h5_at",
                        "orc_mvn_mc_at", "orc_grad", "orc_saddle", "orc_semi_at",
-                       "orc_prob_stencil"):
+                       "orc_prob_stencil", "orc_gauss"):
                 getattr(L, fn).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -175,6 +178,25 @@ def prob_stencil(params, model, stencil, bins=0, boundary=0, idx=None):
     if rc != 0:
         raise ValueError("orc_prob_stencil rejected its arguments")
     return pmin, pmax, st
+
+
+def gauss(params, boundary=0, idx=None):
+    """Independent-Gaussian P_min, P_max, P_saddle and status (params (m, s)
+    planes [2][H][W]); whole field, or at the linear indices idx (1D)."""
+    params = _c64(params)
+    _, H, W = params.shape
+    if idx is None:
+        shape, n, ip = (H, W), H * W, None
+    else:
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        shape, n, ip = (idx.size,), idx.size, _p(idx, _i64)
+    out = [np.empty(shape, np.float64) for _ in range(3)]
+    st = np.empty(shape, np.uint8)
+    rc = lib().orc_gauss(_p(params, _d), H, W, boundary, ip, n, _p(out[0], _d), _p(out[1], _d),
+                         _p(out[2], _d), _p(st, _u8))
+    if rc != 0:
+        raise ValueError("orc_gauss rejected its arguments")
+    return out[0], out[1], out[2], st
 
 
 def prob_hist_h5_at(params, bins, idx):

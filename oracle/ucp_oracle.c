@@ -38,6 +38,9 @@
  *   two-neighbour form (Eq. 1D-saddleProb) is used with X_2 the next
  *   neighbour (e, or s on a column) and X_3 the previous one (w, or n).
  *
+ * Independent Gaussians (the parametric model the paper compares with):
+ * orc_gauss, the same integrals over the real line by adaptive quadrature.
+ *
  * Larger neighbourhoods and 3D grids (the extension named in Sec.
  * "Conclusion"): orc_prob_stencil evaluates the same P_min / P_max with the
  * neighbour set of a 6- or 8-neighbour 2D stencil or of the 6 axis
@@ -78,6 +81,7 @@
 #define ORC_EPAN 1
 #define ORC_HIST 2
 #define ORC_MVN 3
+#define ORC_GAUSS 5
 
 #define ST_DEGENERATE 1
 #define ST_NONFINITE 2
@@ -628,6 +632,154 @@ int orc_prob_stencil(const double *params, int D, int H, int W, int model, int B
   return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* independent Gaussians                                                     */
+/*                                                                          */
+/* The parametric model the paper compares its closed forms with (Sec.       */
+/* "Comparison of Parametric Vs. Nonparametric Models", there evaluated by   */
+/* Monte Carlo): X_i ~ N(m_i, s_i^2) independent.  The definition is the     */
+/* same integral, P_min = int pdf_v(x) prod_n Pr[X_n > x] dx (P_max with     */
+/* Pr[X_n < x]), over the real line.  It is evaluated by adaptive Simpson    */
+/* quadrature on [m_v - 12 s_v, m_v + 12 s_v] (the centre's mass outside is  */
+/* below 1e-32), cut at m_v and at every neighbour's m_n and m_n +- 4 s_n,   */
+/* with 16 starting panels per piece.  A point-mass centre (s_v = 0) gives   */
+/* the product of the strict tail probabilities at m_v; a point-mass         */
+/* neighbour is a step at its mean.  params: (m, s) planes.                  */
+
+typedef struct {
+  double m1, s1;
+  int k;
+  double m[4], s[4];
+  int sign[4]; /* +1: Pr[X_n > x], -1: Pr[X_n < x] */
+} gint_t;
+
+static double g_tail(double m, double s, double x, int sign) {
+  if (s == 0.0) return sign > 0 ? (m > x ? 1.0 : 0.0) : (m < x ? 1.0 : 0.0);
+  /* Pr[X > x] = erfc((x - m) / (s sqrt 2)) / 2, Pr[X < x] = erfc((m - x) / (s sqrt 2)) / 2 */
+  return 0.5 * erfc((sign > 0 ? (x - m) : (m - x)) / (s * sqrt(2.0)));
+}
+
+static double g_integrand(const gint_t *g, double x) {
+  double z = (x - g->m1) / g->s1, f = exp(-0.5 * z * z) / (g->s1 * sqrt(2.0 * 3.14159265358979323846));
+  int n;
+  for (n = 0; n < g->k; ++n) f *= g_tail(g->m[n], g->s[n], x, g->sign[n]);
+  return f;
+}
+
+static double g_simpson(const gint_t *g, double a, double b, double fa, double fm, double fb,
+                        double whole, double tol, int depth) {
+  double m = 0.5 * (a + b), lm = 0.5 * (a + m), rm = 0.5 * (m + b);
+  double flm = g_integrand(g, lm), frm = g_integrand(g, rm);
+  double left = (m - a) / 6.0 * (fa + 4.0 * flm + fm);
+  double right = (b - m) / 6.0 * (fm + 4.0 * frm + fb);
+  double delta = left + right - whole;
+  if (depth <= 0 || fabs(delta) <= 15.0 * tol) return left + right + delta / 15.0;
+  return g_simpson(g, a, m, fa, flm, fm, left, 0.5 * tol, depth - 1) +
+         g_simpson(g, m, b, fm, frm, fb, right, 0.5 * tol, depth - 1);
+}
+
+static double g_integral(const gint_t *g) {
+  double lo = g->m1 - 12.0 * g->s1, hi = g->m1 + 12.0 * g->s1;
+  double pts[3 + 3 * 4];
+  int np = 0, n, i, j;
+  double total = 0.0;
+  pts[np++] = lo;
+  pts[np++] = hi;
+  pts[np++] = g->m1;
+  for (n = 0; n < g->k; ++n) {
+    double c[3] = {g->m[n] - 4.0 * g->s[n], g->m[n], g->m[n] + 4.0 * g->s[n]};
+    for (i = 0; i < 3; ++i)
+      if (c[i] > lo && c[i] < hi) pts[np++] = c[i];
+  }
+  qsort(pts, (size_t)np, sizeof(double), cmp_double);
+  for (i = 0; i + 1 < np; ++i) {
+    double a = pts[i], b = pts[i + 1];
+    if (!(b > a)) continue;
+    for (j = 0; j < 16; ++j) {
+      double x0 = a + (b - a) * j / 16.0, x1 = a + (b - a) * (j + 1) / 16.0;
+      double f0 = g_integrand(g, x0), f1 = g_integrand(g, x1), fm = g_integrand(g, 0.5 * (x0 + x1));
+      double whole = (x1 - x0) / 6.0 * (f0 + 4.0 * fm + f1);
+      total += g_simpson(g, x0, x1, f0, fm, f1, whole, 1e-15, 40);
+    }
+  }
+  return total;
+}
+
+static int g_status(double m, double s) {
+  if (!isfinite(m) || !isfinite(s)) return ST_NONFINITE;
+  return s < 0.0 ? ST_BAD_PARAMS : (s == 0.0 ? ST_DEGENERATE : 0);
+}
+
+/* the integral with the given signs, or the product of tails at a
+ * point-mass centre */
+static double g_prob(gint_t *g) {
+  int n;
+  if (g->s1 == 0.0) {
+    double p = 1.0;
+    for (n = 0; n < g->k; ++n) p *= g_tail(g->m[n], g->s[n], g->m1, g->sign[n]);
+    return p;
+  }
+  return g_integral(g);
+}
+
+/* Minimum, maximum and saddle probabilities of independent Gaussians at
+ * every vertex (idx == NULL) or at idx[0..n-1]; any output may be NULL.
+ * Neighbours and boundary modes as for the closed-form models. */
+int orc_gauss(const double *params, int H, int W, int boundary, const int64_t *idx, int64_t n,
+              double *out_min, double *out_max, double *out_saddle, uint8_t *status) {
+  int64_t t, plane = (int64_t)H * W;
+  if (H < 1 || W < 1) return -1;
+  if (!idx) n = plane;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(orc_get_threads())
+  for (t = 0; t < n; ++t) {
+    int64_t i = idx ? idx[t] : t, nidx[4];
+    int y = (int)(i / W), x = (int)(i % W), slot[4];
+    int k = neighbours(H, W, y, x, nidx, slot), q, st;
+    gint_t g;
+    double pmin, pmax, psad = 0.0;
+    g.m1 = params[i];
+    g.s1 = params[plane + i];
+    g.k = k;
+    st = g_status(g.m1, g.s1);
+    for (q = 0; q < k; ++q) {
+      g.m[q] = params[nidx[q]];
+      g.s[q] = params[plane + nidx[q]];
+      st |= g_status(g.m[q], g.s[q]) & (ST_NONFINITE | ST_BAD_PARAMS);
+    }
+    if (status) status[t] = (uint8_t)st;
+    if (st & (ST_NONFINITE | ST_BAD_PARAMS)) {
+      if (out_min) out_min[t] = NAN;
+      if (out_max) out_max[t] = NAN;
+      if (out_saddle) out_saddle[t] = NAN;
+      continue;
+    }
+    for (q = 0; q < k; ++q) g.sign[q] = 1;
+    pmin = g_prob(&g);
+    for (q = 0; q < k; ++q) g.sign[q] = -1;
+    pmax = g_prob(&g);
+    if (boundary == 1 && k < 4) pmin = pmax = 0.0;
+    if (out_saddle) {
+      /* Eq. saddleProb: e, w below / n, s above, and the reverse; the line
+       * case with the next (e, or s) and previous (w, or n) neighbour */
+      int ok = k == 4 || (k == 2 && (H == 1 || W == 1));
+      if (ok) {
+        double t1, t2;
+        for (q = 0; q < k; ++q)
+          g.sign[q] = k == 4 ? ((slot[q] == 0 || slot[q] == 2) ? 1 : -1)
+                             : ((slot[q] == 0 || slot[q] == 3) ? 1 : -1);
+        t1 = g_prob(&g);
+        for (q = 0; q < k; ++q) g.sign[q] = -g.sign[q];
+        t2 = g_prob(&g);
+        psad = t1 + t2;
+      }
+      out_saddle[t] = psad;
+    }
+    if (out_min) out_min[t] = pmin;
+    if (out_max) out_max[t] = pmax;
+  }
+  return 0;
+}
+
 /* The paper's second route for histograms, Eq. (localMinProbHistogram):
  * sum over every combination of one bin per variable of the product of the
  * bin masses times the uniform-kernel probability of that combination.
@@ -727,7 +879,8 @@ int orc_fit(const float *ens, int N, int H, int W, int model, int B, double epan
       } else if (model == ORC_UNIFORM) {
         params[i] = mn;
         params[plane + i] = mx;
-      } else if (model == ORC_EPAN) {
+      } else if (model == ORC_EPAN || model == ORC_GAUSS) {
+        /* Gaussian: m = mean, s = sample std (the scale is 1) */
         double s = 0.0, m, ss = 0.0;
         for (k = 0; k < N; ++k) s += ens[(int64_t)k * plane + i];
         m = s / N;
@@ -740,7 +893,7 @@ int orc_fit(const float *ens, int N, int H, int W, int model, int B, double epan
           params[plane + i] = 0.0;
         } else {
           params[i] = m;
-          params[plane + i] = epan_scale * sqrt(ss / (N - 1));
+          params[plane + i] = (model == ORC_GAUSS ? 1.0 : epan_scale) * sqrt(ss / (N - 1));
         }
       } else if (model == ORC_HIST) {
         int cnt[MAXB], j;
