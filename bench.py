@@ -514,17 +514,30 @@ def gmm_row(torch, ucp, ctx, dev, steps, flush):
     ens = torch.from_numpy(ens_np).to(dev)
     H, W = ens_np.shape[1:]
     out = {}
+    diag_mvn = None
     for model, bins, S in (("uniform", 0, 0), ("epanechnikov", 0, 0), ("histogram", 5, 0),
-                           ("histogram_semi", 5, 1000), ("mvn", 0, 2000)):
-        d = ucp.make_desc(model, bins=bins or 8, mc_samples=S or 1000)
+                           ("histogram_semi", 5, 1000), ("mvn", 0, 2000), ("gaussian", 0, 0),
+                           ("gaussian_mc", 0, 1000)):
         pm = torch.empty((H, W), device=dev)
-        ms, _ = timed_steps(torch, lambda ev, d=d, pm=pm: ucp.ucp_probability(
-            ctx.handle, ens, d, ucp.UCP_MAX, None, pm), steps, 2, flush)
+        if model == "gaussian_mc":
+            # independent Gaussians by Monte Carlo: the multivariate model with
+            # its covariance reduced to the diagonal
+            d = ucp.make_desc("mvn", mc_samples=S)
+            diag_mvn = ctx.fit(ens, d)
+            for q in range(5, 20):
+                if q not in (5, 7, 10, 14, 19):
+                    diag_mvn[q].zero_()
+            ms, _ = timed_steps(torch, lambda ev, d=d, pm=pm: ucp.ucp_probability_from_params(
+                ctx.handle, diag_mvn, d, ucp.UCP_MAX, None, pm), steps, 2, flush)
+        else:
+            d = ucp.make_desc(model, bins=bins or 8, mc_samples=S or 1000)
+            ms, _ = timed_steps(torch, lambda ev, d=d, pm=pm: ucp.ucp_probability(
+                ctx.handle, ens, d, ucp.UCP_MAX, None, pm), steps, 2, flush)
         P = pm.cpu().numpy()
 
         def near(pts):
             return [float(P[y - 2:y + 3, x - 2:x + 3].max()) for (y, x) in pts]
-        out[model + (str(bins) if bins else "")] = {
+        out[model + (str(bins) if bins else "") + (str(S) if model == "gaussian_mc" else "")] = {
             "ms": ms / steps, "p_max_near_true_peaks": near(tp),
             "p_max_near_outlier_peaks": near(op)}
     return out

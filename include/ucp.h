@@ -101,7 +101,17 @@ typedef enum {
    * <= ua * T (T = C_B), clamped to B-1; x_s = lo + (bin + ub) h.  A
    * point-mass centre is exact.  Minimum, maximum and saddle; no adjoint,
    * no batch. */
-  UCP_HISTOGRAM_SEMI = 4
+  UCP_HISTOGRAM_SEMI = 4,
+  /* independent Gaussian, params (m, s): pdf N(m, s^2) -- the parametric
+   * model the paper compares the closed forms with (Sec. "Comparison of
+   * Parametric Vs. Nonparametric Models", there by Monte Carlo).  Fit:
+   * m = sample mean, s = sample std (N-1 divisor).  Without a finite support
+   * the integral over t = (x - m_v)/s_v is taken by quadrature: |t| <= 8,
+   * cut at -3, 0, 3 and at every neighbour's centre and centre +- 8 of its
+   * standard deviations (in t), the 16-point Gauss-Legendre rule on each
+   * piece (|dP| ~ 1e-6 in FP32).  Minimum, maximum and saddle; no adjoint,
+   * no batch, four-neighbour stencil only. */
+  UCP_GAUSSIAN = 5
 } ucp_model;
 
 typedef enum { UCP_MIN = 1, UCP_MAX = 2 } ucp_cptype; /* bit mask */

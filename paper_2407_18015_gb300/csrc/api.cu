@@ -43,7 +43,7 @@ struct DeviceGuard {
 
 int valid_desc(const ucp_model_desc *d, bool allow_sampled) {
   if (!d) return UCP_ERR_ARG;
-  if (d->model < UCP_UNIFORM || d->model > UCP_HISTOGRAM_SEMI) return UCP_ERR_ARG;
+  if (d->model < UCP_UNIFORM || d->model > UCP_GAUSSIAN) return UCP_ERR_ARG;
   const bool sampled = d->model == UCP_MVN_MC || d->model == UCP_HISTOGRAM_SEMI;
   if (sampled && !allow_sampled) return UCP_ERR_UNSUPPORTED;
   if ((d->model == UCP_HISTOGRAM || d->model == UCP_HISTOGRAM_SEMI) &&
@@ -382,6 +382,7 @@ int ucp_backward(ucp_ctx *ctx, const float *params, int H, int W, const ucp_mode
   if (!ctx || !params || !weight || !grad_params) return UCP_ERR_ARG;
   int rc = valid_desc(desc, false);
   if (rc) return rc;
+  if (desc->model == UCP_GAUSSIAN) return UCP_ERR_UNSUPPORTED;
   if (uses_stencil(desc)) return UCP_ERR_UNSUPPORTED;
   if (cptype != UCP_MIN && cptype != UCP_MAX) return UCP_ERR_ARG;
   if ((rc = valid_shape(1, H, W))) return rc;

@@ -284,7 +284,9 @@ int ucp_batch_create(ucp_ctx *ctx, ucp_batch **batch) {
 int ucp_batch_add(ucp_batch *batch, const float *ens, int N, int H, int W,
                   const ucp_model_desc *desc, unsigned cptypes, float *out_min, float *out_max) {
   if (!batch || !ens || !desc) return UCP_ERR_ARG;
-  if (desc->model == UCP_MVN_MC || desc->model == UCP_HISTOGRAM_SEMI) return UCP_ERR_UNSUPPORTED;
+  if (desc->model == UCP_MVN_MC || desc->model == UCP_HISTOGRAM_SEMI ||
+      desc->model == UCP_GAUSSIAN)
+    return UCP_ERR_UNSUPPORTED;
   if (desc->model < UCP_UNIFORM || desc->model > UCP_HISTOGRAM) return UCP_ERR_ARG;
   if (desc->model == UCP_HISTOGRAM && (desc->bins < 1 || desc->bins > kMaxBinsHost))
     return UCP_ERR_ARG;

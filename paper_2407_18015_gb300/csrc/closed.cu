@@ -38,10 +38,10 @@ __global__ void __launch_bounds__(256) fit_kernel(Field f) {
       }
       out[i] = mn;
       out[plane + i] = mx;
-    } else if (MODEL == kEpan) {
+    } else if (MODEL == kEpan || MODEL == kGauss) {
       float m, w, mn, mx;
       bool nf;
-      members_epan(p, plane, f.N, f.epan_scale, m, w, mn, mx, nf);
+      members_epan(p, plane, f.N, MODEL == kGauss ? 1.f : f.epan_scale, m, w, mn, mx, nf);
       if (nf) {
         m = w = __int_as_float(0x7fc00000);
         st |= V_NONFINITE;
@@ -131,6 +131,7 @@ cudaError_t launch_fit(const Field &f, int model, cudaStream_t s) {
   switch (model) {
     case kUniform: fit_kernel<kUniform><<<g, 256, 0, s>>>(f); break;
     case kEpan: fit_kernel<kEpan><<<g, 256, 0, s>>>(f); break;
+    case kGauss: fit_kernel<kGauss><<<g, 256, 0, s>>>(f); break;
     case kHist:
     case kSemi: fit_kernel<kHist><<<g, 256, 0, s>>>(f); break;
     default: return cudaErrorInvalidValue;
@@ -176,6 +177,8 @@ static cudaError_t launch_closed_t(const Field &f, int model, bool fm, cudaStrea
                                    : launch_tile<kUniform, false, SADDLE>(f, s);
   if (model == kEpan) return fm ? launch_tile<kEpan, true, SADDLE>(f, s)
                                 : launch_tile<kEpan, false, SADDLE>(f, s);
+  if (model == kGauss) return fm ? launch_tile<kGauss, true, SADDLE>(f, s)
+                                 : launch_tile<kGauss, false, SADDLE>(f, s);
   if (model == kHist) return fm ? launch_tile<kHist, true, SADDLE>(f, s)
                                 : launch_tile<kHist, false, SADDLE>(f, s);
   if (model == kSemi) return fm ? launch_tile<kSemi, true, SADDLE>(f, s)

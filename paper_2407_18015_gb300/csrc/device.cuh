@@ -21,7 +21,7 @@
 
 namespace ucp {
 
-constexpr int kUniform = 0, kEpan = 1, kHist = 2, kMvn = 3, kSemi = 4;
+constexpr int kUniform = 0, kEpan = 1, kHist = 2, kMvn = 3, kSemi = 4, kGauss = 5;
 
 // histogram parameters (lo, hi, masses): the closed form and the estimator
 __host__ __device__ constexpr bool hist_params(int model) { return model == kHist || model == kSemi; }
@@ -468,6 +468,157 @@ __device__ __forceinline__ void epan_vertex(EpanParams c, const EpanParams *nb,
     }
     pmax = epan_side(w1, -w1, R, al, d, iw);
   }
+}
+
+// nodes (positive half, ascending) and weights of the 16-point rule on
+// [-1, 1]: the roots of the Legendre polynomial P_16 and 2 / ((1 - x^2)
+// P_16'(x)^2)
+__device__ __constant__ const float kGL16x[8] = {
+    0.095012509837637441f, 0.28160355077925892f, 0.45801677765722737f, 0.61787624440264377f,
+    0.755404408355003f,    0.86563120238783176f, 0.9445750230732326f,  0.98940093499164994f};
+__device__ __constant__ const float kGL16w[8] = {
+    0.18945061045506864f, 0.18260341504492364f, 0.16915651939500265f, 0.14959598881657671f,
+    0.12462897125553407f, 0.095158511682492605f, 0.062253523938647456f, 0.027152459411754176f};
+
+// ---------------------------------------------------------------------------
+// independent Gaussians (the parametric model the paper compares with by
+// Monte Carlo, Sec. "Comparison of Parametric Vs. Nonparametric Models"):
+// no finite support, so the one-dimensional integral
+//   P = int phi(t) prod_n f_n(t) dt,  t = (x - m1) / s1,
+// f_n = Q((t - a_n) / r_n) (survival) or Phi((t - a_n) / r_n) (CDF),
+// a_n = (m_n - m1) / s1, r_n = s_n / s1, is evaluated by quadrature: the
+// range |t| <= 8 (mass beyond it 1.2e-15) is cut at -3, 0, 3 and at every
+// neighbour's a_n and a_n +- 8 r_n, and each piece takes the 16-point
+// Gauss-Legendre rule (on such pieces the integrand is smooth and the rule
+// converges to ~1e-15 in exact arithmetic).
+
+struct GaussParams {
+  float m, s;
+};
+
+constexpr float kGaussR = 8.f;
+constexpr int kGaussBp = 5 + 3 * 4;
+
+// 0.5 erfc(|z| / sqrt 2): the smaller of Q(z) and Phi(z), accurate in both
+// tails; returns (Q(z), Phi(z))
+__device__ __forceinline__ float2 gauss_tails(float z) {
+  const float e = 0.5f * erfcf(fabsf(z) * 0.70710678118654752f);
+  return z >= 0.f ? make_float2(e, 1.f - e) : make_float2(1.f - e, e);
+}
+
+// The minimum and maximum (SADDLE = false) or the saddle terms t1, t2
+// (SADDLE = true, sg as in the mixed products) of a centre with sigma > 0.
+template <bool SADDLE>
+__device__ __forceinline__ float2 gauss_quad(GaussParams c, const GaussParams *nb,
+                                             const bool *present, const int *sg) {
+  float a[4], ir[4];
+  bool step[4];
+  float bp[kGaussBp];
+  int nbp = 0;
+  bp[nbp++] = -kGaussR; bp[nbp++] = -3.f; bp[nbp++] = 0.f; bp[nbp++] = 3.f; bp[nbp++] = kGaussR;
+  const float is1 = 1.f / c.s;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const bool on = present[i] && (!SADDLE || sg[i] != 0);
+    a[i] = on ? (nb[i].m - c.m) * is1 : 0.f;
+    const float r = on ? nb[i].s * is1 : 0.f;
+    step[i] = r == 0.f;
+    ir[i] = step[i] ? 0.f : 1.f / r;
+    const float lo = on ? fminf(fmaxf(a[i] - kGaussR * r, -kGaussR), kGaussR) : -kGaussR;
+    const float mid = on ? fminf(fmaxf(a[i], -kGaussR), kGaussR) : -kGaussR;
+    const float hi = on ? fminf(fmaxf(a[i] + kGaussR * r, -kGaussR), kGaussR) : -kGaussR;
+    bp[nbp++] = lo; bp[nbp++] = mid; bp[nbp++] = hi;
+  }
+  // insertion sort of the breakpoints (kGaussBp values)
+#pragma unroll
+  for (int i = 1; i < kGaussBp; ++i)
+#pragma unroll
+    for (int j = i; j > 0; --j) {
+      const float x = bp[j - 1], y = bp[j];
+      bp[j - 1] = fminf(x, y);
+      bp[j] = fmaxf(x, y);
+    }
+  const float inv_sqrt_2pi = 0.39894228040143268f;
+  float2 tot = make_float2(0.f, 0.f), comp = make_float2(0.f, 0.f);
+  for (int k = 0; k + 1 < kGaussBp; ++k) {
+    const float x0 = bp[k], x1 = bp[k + 1];
+    if (!(x1 > x0)) continue;
+    const float half = 0.5f * (x1 - x0), mid = 0.5f * (x0 + x1);
+    float2 sum = make_float2(0.f, 0.f);
+    for (int q = 0; q < 16; ++q) {
+      const float xi = (q < 8) ? -kGL16x[7 - q] : kGL16x[q - 8];
+      const float wi = (q < 8) ? kGL16w[7 - q] : kGL16w[q - 8];
+      const float t = fmaf(half, xi, mid);
+      const float ph = inv_sqrt_2pi * expf(-0.5f * t * t);
+      float u = ph, v = ph;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (!(present[i] && (!SADDLE || sg[i] != 0))) continue;
+        float2 qp;
+        if (step[i]) qp = t < a[i] ? make_float2(1.f, 0.f) : make_float2(0.f, 1.f);
+        else qp = gauss_tails((t - a[i]) * ir[i]);
+        if (SADDLE && sg[i] < 0) qp = make_float2(qp.y, qp.x);
+        u *= qp.x;  // min: survival (saddle t1: its factor)
+        v *= qp.y;  // max: CDF (saddle t2: the other factor)
+      }
+      sum.x = fmaf(wi, u, sum.x);
+      sum.y = fmaf(wi, v, sum.y);
+    }
+    // Kahan over the pieces
+    const float yx = sum.x * half - comp.x, yy = sum.y * half - comp.y;
+    const float tx = tot.x + yx, ty = tot.y + yy;
+    comp.x = (tx - tot.x) - yx;
+    comp.y = (ty - tot.y) - yy;
+    tot.x = tx;
+    tot.y = ty;
+  }
+  return tot;
+}
+
+__device__ __forceinline__ void gauss_vertex(GaussParams c, const GaussParams *nb,
+                                             const bool *present, float &pmin, float &pmax) {
+  if (c.s == 0.f) {
+    float gm = 1.f, gM = 1.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (!present[i]) continue;
+      float2 qp;
+      if (nb[i].s == 0.f)
+        qp = make_float2(nb[i].m > c.m ? 1.f : 0.f, nb[i].m < c.m ? 1.f : 0.f);
+      else
+        qp = gauss_tails((c.m - nb[i].m) / nb[i].s);
+      gm *= qp.x;
+      gM *= qp.y;
+    }
+    pmin = gm;
+    pmax = gM;
+    return;
+  }
+  const float2 r = gauss_quad<false>(c, nb, present, nullptr);
+  pmin = fminf(fmaxf(r.x, 0.f), 1.f);
+  pmax = fminf(fmaxf(r.y, 0.f), 1.f);
+}
+
+// saddle t1 + t2 (sg: +1 survival, -1 CDF, 0 absent, for t1)
+__device__ __forceinline__ float gauss_saddle(GaussParams c, const GaussParams *nb,
+                                              const bool *present, const int *sg) {
+  if (c.s == 0.f) {
+    float t1 = 1.f, t2 = 1.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (sg[i] == 0) continue;
+      float2 qp;
+      if (nb[i].s == 0.f)
+        qp = make_float2(nb[i].m > c.m ? 1.f : 0.f, nb[i].m < c.m ? 1.f : 0.f);
+      else
+        qp = gauss_tails((c.m - nb[i].m) / nb[i].s);
+      t1 *= sg[i] > 0 ? qp.x : qp.y;
+      t2 *= sg[i] > 0 ? qp.y : qp.x;
+    }
+    return t1 + t2;
+  }
+  const float2 r = gauss_quad<true>(c, nb, present, sg);
+  return fmaxf(r.x, 0.f) + fmaxf(r.y, 0.f);
 }
 
 // ---------------------------------------------------------------------------

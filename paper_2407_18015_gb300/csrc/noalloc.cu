@@ -63,8 +63,10 @@ extern "C" int ucp_backward_static(const float *params, int H, int W,
   if (!params || !weight || !grad_params || !desc) return UCP_ERR_ARG;
   if (desc->model != UCP_UNIFORM && desc->model != UCP_EPANECHNIKOV &&
       desc->model != UCP_HISTOGRAM)
-    return (desc->model == UCP_MVN_MC || desc->model == UCP_HISTOGRAM_SEMI) ? UCP_ERR_UNSUPPORTED
-                                                                           : UCP_ERR_ARG;
+    return (desc->model == UCP_MVN_MC || desc->model == UCP_HISTOGRAM_SEMI ||
+            desc->model == UCP_GAUSSIAN)
+               ? UCP_ERR_UNSUPPORTED
+               : UCP_ERR_ARG;
   if (desc->model == UCP_HISTOGRAM && (desc->bins < 1 || desc->bins > kMaxBinsHost))
     return UCP_ERR_ARG;
   if (desc->boundary != UCP_BOUNDARY_INGRID && desc->boundary != UCP_BOUNDARY_ZERO)

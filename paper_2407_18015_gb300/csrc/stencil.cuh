@@ -184,16 +184,6 @@ __device__ __forceinline__ void uniform_vertex_k(UniParams c, const UniParams *n
 // Epanechnikov: with K neighbours the integrand has degree <= 2 + 3K = 26 on
 // a piece; the 16-point Gauss-Legendre rule is exact to degree 31
 
-// nodes (positive half, ascending) and weights of the 16-point rule on
-// [-1, 1]: the roots of the Legendre polynomial P_16 and 2 / ((1 - x^2)
-// P_16'(x)^2)
-__device__ __constant__ const float kGL16x[8] = {
-    0.095012509837637441f, 0.28160355077925892f, 0.45801677765722737f, 0.61787624440264377f,
-    0.755404408355003f,    0.86563120238783176f, 0.9445750230732326f,  0.98940093499164994f};
-__device__ __constant__ const float kGL16w[8] = {
-    0.18945061045506864f, 0.18260341504492364f, 0.16915651939500265f, 0.14959598881657671f,
-    0.12462897125553407f, 0.095158511682492605f, 0.062253523938647456f, 0.027152459411754176f};
-
 // epan_side with K factors (same frame and arguments)
 template <int K>
 __device__ __forceinline__ float epan_side_k(float w1, float L, float R, const float *al,

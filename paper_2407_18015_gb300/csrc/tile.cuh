@@ -143,7 +143,7 @@ __device__ __forceinline__ void stage_members(const Field &f, float *sm, int l, 
   const int N = f.N;
   float mn[V], mx[V];
   bool nf[V];
-  if constexpr (MODEL == kEpan) {
+  if constexpr (MODEL == kEpan || MODEL == kGauss) {
     // one pass, shifted by the first member (see members_epan)
     float x0[V];
     Kahan s1[V], s2[V];
@@ -174,7 +174,8 @@ __device__ __forceinline__ void stage_members(const Field &f, float *sm, int l, 
         const float S1 = s1[q].get(), S2 = s2[q].get();
         const float md = S1 / (float)N;
         m = x0[q] + md;
-        w = f.epan_scale * sqrtf(fmaxf(S2 - S1 * md, 0.f) / (float)(N - 1));
+        const float scale = MODEL == kGauss ? 1.f : f.epan_scale;
+        w = scale * sqrtf(fmaxf(S2 - S1 * md, 0.f) / (float)(N - 1));
       }
       sm[l + q] = nf[q] ? qnan() : m;
       sm[HALO + l + q] = nf[q] ? qnan() : w;
@@ -253,10 +254,10 @@ __device__ __forceinline__ void stage_vertex(const Field &f, float *sm, int l, l
     members_minmax(p, plane, f.N, mn, mx, nf);
     sm[l] = nf ? qnan() : mn;
     sm[HALO + l] = nf ? qnan() : mx;
-  } else if (MODEL == kEpan) {
+  } else if (MODEL == kEpan || MODEL == kGauss) {
     float m, w, mn, mx;
     bool nf;
-    members_epan(p, plane, f.N, f.epan_scale, m, w, mn, mx, nf);
+    members_epan(p, plane, f.N, MODEL == kGauss ? 1.f : f.epan_scale, m, w, mn, mx, nf);
     sm[l] = nf ? qnan() : m;
     sm[HALO + l] = nf ? qnan() : w;
   } else {
@@ -299,7 +300,7 @@ __device__ __forceinline__ uint8_t check_params(const float *sm, int l, int B, f
   T = 1.f;
   if (!isfinite(a) || !isfinite(b)) return V_NONFINITE;
   if (MODEL == kUniform) return a > b ? V_BAD : (a == b ? V_DEGENERATE : 0);
-  if (MODEL == kEpan) return b < 0.f ? V_BAD : (b == 0.f ? V_DEGENERATE : 0);
+  if (MODEL == kEpan || MODEL == kGauss) return b < 0.f ? V_BAD : (b == 0.f ? V_DEGENERATE : 0);
   uint8_t st = a > b ? V_BAD : (a == b ? V_DEGENERATE : 0);
   float t = 0.f;
   for (int q = 0; q < B; ++q) {
@@ -469,6 +470,15 @@ __device__ __forceinline__ void process_tile(const Field &f, int ty0, int tx0, f
         if (!(f.boundary == 1 && k < 4)) uniform_vertex(cp, nb, present, f.cptypes, pmin, pmax);
       } else if (has_saddle) {
         psad = uniform_mixed(cp, nb, sg) + uniform_mixed(cp, nb, sg2);
+      }
+    } else if (MODEL == kGauss) {
+      GaussParams cp{sm[l], sm[HALO + l]}, nb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) nb[i] = GaussParams{sm[nl[i]], sm[HALO + nl[i]]};
+      if constexpr (!SADDLE) {
+        if (!(f.boundary == 1 && k < 4)) gauss_vertex(cp, nb, present, pmin, pmax);
+      } else if (has_saddle) {
+        psad = gauss_saddle(cp, nb, present, sg);
       }
     } else if (MODEL == kEpan) {
       EpanParams cp{sm[l], sm[HALO + l]}, nb[4];

@@ -18,6 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libucp.so")
 
 UCP_UNIFORM, UCP_EPANECHNIKOV, UCP_HISTOGRAM, UCP_MVN_MC, UCP_HISTOGRAM_SEMI = 0, 1, 2, 3, 4
+UCP_GAUSSIAN = 5
 UCP_MIN, UCP_MAX = 1, 2
 UCP_BOUNDARY_INGRID, UCP_BOUNDARY_ZERO = 0, 1
 UCP_STENCIL_4, UCP_STENCIL_6, UCP_STENCIL_8, UCP_STENCIL_3D6 = 0, 1, 2, 3
@@ -28,7 +29,7 @@ UCP_V_DEGENERATE, UCP_V_NONFINITE, UCP_V_BAD_PARAMS, UCP_V_CHOL_JITTER, UCP_V_CH
 
 MODELS = {"uniform": UCP_UNIFORM, "epanechnikov": UCP_EPANECHNIKOV,
           "histogram": UCP_HISTOGRAM, "mvn": UCP_MVN_MC,
-          "histogram_semi": UCP_HISTOGRAM_SEMI}
+          "histogram_semi": UCP_HISTOGRAM_SEMI, "gaussian": UCP_GAUSSIAN}
 
 
 class ucp_model_desc(ctypes.Structure):

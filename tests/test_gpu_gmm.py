@@ -31,7 +31,7 @@ def test_gmm_outliers_model_comparison(ucp, orc):
     ctx = ucp.Context(0)
     res = {}
     for model, bins in (("uniform", 0), ("epanechnikov", 0), ("histogram", 5),
-                        ("histogram_semi", 5), ("mvn", 0)):
+                        ("histogram_semi", 5), ("mvn", 0), ("gaussian", 0)):
         desc = ucp.make_desc(model, bins=bins or 8, mc_samples=2000, seed=11)
         _, pmax, st = ctx.probability(ens, desc, ucp.UCP_MAX)
         torch.cuda.synchronize()
@@ -41,7 +41,24 @@ def test_gmm_outliers_model_comparison(ucp, orc):
             torch.cuda.synchronize()
             _, rmax, _ = orc.prob(params.double().cpu().numpy(), desc.model, bins=desc.bins)
             assert np.abs(res[model] - rmax).max() <= 1e-5
+    # independent Gaussians by Monte Carlo with 1000 samples (the paper's
+    # comparison): the multivariate Gaussian with its covariance reduced to
+    # the diagonal, against the quadrature
+    mdesc = ucp.make_desc("mvn", mc_samples=1000, seed=12)
+    mp = ctx.fit(ens, mdesc)
+    for q in range(5, 20):
+        if q not in (5, 7, 10, 14, 19):
+            mp[q].zero_()
+    _, pmc, _ = ctx.probability_from_params(mp, mdesc, ucp.UCP_MAX)
+    torch.cuda.synchronize()
+    res["gaussian_mc1000"] = pmc.cpu().numpy()
+    gp = ctx.fit(ens, ucp.make_desc("gaussian"))
+    torch.cuda.synchronize()
+    _, gmax, _, _ = orc.gauss(gp.double().cpu().numpy())
+    assert np.abs(res["gaussian"] - gmax).max() <= 1e-5
     ctx.close()
+    sd = np.sqrt(np.maximum(res["gaussian"] * (1 - res["gaussian"]), 1e-6) / 1000)
+    assert (np.abs(res["gaussian_mc1000"] - res["gaussian"]) <= 6 * sd + 1e-3).all()
     t = {m: _near_max(P, true_pk) for m, P in res.items()}
     o = {m: _near_max(P, out_pk) for m, P in res.items()}
     # histogram: true peaks likely, outlier peaks suppressed
