@@ -352,11 +352,76 @@ __device__ __constant__ const float kGLx[4] = {0.18343464249564978f, 0.525532409
 __device__ __constant__ const float kGLw[4] = {0.36268378337836166f, 0.3137066458778869f,
                                                0.22238103445337443f, 0.10122853629037706f};
 
+// Gauss-Legendre rules on [-1, 1] with 2, 3, 5 and 6 nodes (all nodes,
+// ascending: the roots of P_n, weights 2 / ((1 - x^2) P_n'(x)^2)); the n-point
+// rule is exact for polynomials of degree <= 2n - 1.
+__device__ __constant__ const float kGL2x[2] = {-0.57735026918962573f, 0.57735026918962573f};
+__device__ __constant__ const float kGL2w[2] = {1.f, 1.f};
+__device__ __constant__ const float kGL3x[3] = {-0.7745966692414834f, 0.f, 0.7745966692414834f};
+__device__ __constant__ const float kGL3w[3] = {0.55555555555555569f, 0.88888888888888884f,
+                                                0.55555555555555569f};
+__device__ __constant__ const float kGL5x[5] = {-0.90617984593866396f, -0.53846931010568311f, 0.f,
+                                                0.53846931010568311f, 0.90617984593866396f};
+__device__ __constant__ const float kGL5w[5] = {0.23692688505618928f, 0.4786286704993663f,
+                                                0.56888888888888867f, 0.4786286704993663f,
+                                                0.23692688505618928f};
+__device__ __constant__ const float kGL6x[6] = {-0.93246951420315194f, -0.66120938646626448f,
+                                                -0.2386191860831969f,  0.2386191860831969f,
+                                                0.66120938646626448f,  0.93246951420315194f};
+__device__ __constant__ const float kGL6w[6] = {0.17132449237917027f, 0.36076157304813872f,
+                                                0.46791393457269104f, 0.46791393457269104f,
+                                                0.36076157304813872f, 0.17132449237917027f};
+
+// node / weight q (ascending) of the NG-point rule, NG in {2, 3, 5, 6, 8}
+template <int NG>
+__device__ __forceinline__ float gl_x(int q) {
+  if constexpr (NG == 2) return kGL2x[q];
+  else if constexpr (NG == 3) return kGL3x[q];
+  else if constexpr (NG == 5) return kGL5x[q];
+  else if constexpr (NG == 6) return kGL6x[q];
+  else return q < 4 ? -kGLx[3 - q] : kGLx[q - 4];
+}
+template <int NG>
+__device__ __forceinline__ float gl_w(int q) {
+  if constexpr (NG == 2) return kGL2w[q];
+  else if constexpr (NG == 3) return kGL3w[q];
+  else if constexpr (NG == 5) return kGL5w[q];
+  else if constexpr (NG == 6) return kGL6w[q];
+  else return q < 4 ? kGLw[3 - q] : kGLw[q - 4];
+}
+
 // survival of the standard Epanechnikov kernel on [-1,1]: (1-u)^2 (2+u) / 4
 __device__ __forceinline__ float epan_surv(float u) {
   u = fminf(fmaxf(u, -1.f), 1.f);
   const float q = 1.f - u;
   return 0.25f * q * q * (2.f + u);
+}
+
+// Piece J of epan_side: on [x[J], x[J+1]] the centre density (degree 2)
+// times the J started survivals (degree 3 each) has degree 2 + 3J, so the
+// n-point rule with 2n - 1 >= 2 + 3J is exact: n = 2, 3, 5, 6, 8.
+template <int J>
+struct EpanNodes {
+  static constexpr int value = J == 0 ? 2 : (J == 1 ? 3 : (J == 2 ? 5 : (J == 3 ? 6 : 8)));
+};
+template <int J>
+__device__ __forceinline__ void epan_pieces(const float *x, const float (*pay)[4], float iw1,
+                                            float c1, Kahan &acc) {
+  constexpr int NG = EpanNodes<J>::value;
+  const float x0 = x[J], x1 = x[J + 1];
+  const float half = 0.5f * (x1 - x0), mid = 0.5f * (x0 + x1);
+  float s = 0.f;
+#pragma unroll
+  for (int q = 0; q < NG; ++q) {
+    const float xx = fmaf(half, gl_x<NG>(q), mid);
+    const float u1 = xx * iw1;
+    float f = c1 * fmaxf(fmaf(-u1, u1, 1.f), 0.f);
+#pragma unroll
+    for (int i = 0; i < J; ++i) f *= epan_surv((xx - pay[0][i]) * pay[1][i]);
+    s = fmaf(gl_w<NG>(q), f, s);
+  }
+  acc.add(s * half);
+  if constexpr (J < 4) epan_pieces<J + 1>(x, pay, iw1, c1, acc);
 }
 
 // One-sided problem in the centre's frame (origin m1): centre pdf
@@ -379,24 +444,7 @@ __device__ __forceinline__ float epan_side(float w1, float L, float R, float al[
   const float iw1 = frcp(w1);
   const float c1 = 0.75f * iw1;
   Kahan acc;
-#pragma unroll
-  for (int j = 0; j <= 4; ++j) {
-    const float x0 = x[j], x1 = x[j + 1];
-    const float half = 0.5f * (x1 - x0), mid = 0.5f * (x0 + x1);
-    float s = 0.f;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const float xi = (q < 4) ? -kGLx[3 - q] : kGLx[q - 4];
-      const float wi = (q < 4) ? kGLw[3 - q] : kGLw[q - 4];
-      const float xx = fmaf(half, xi, mid);
-      const float u1 = xx * iw1;
-      float f = c1 * fmaxf(fmaf(-u1, u1, 1.f), 0.f);
-#pragma unroll
-      for (int i = 0; i < j; ++i) f *= epan_surv((xx - pay[0][i]) * pay[1][i]);
-      s = fmaf(wi, f, s);
-    }
-    acc.add(s * half);
-  }
+  epan_pieces<0>(x, pay, iw1, c1, acc);
   return acc.get();
 }
 
