@@ -36,7 +36,7 @@
  *     ran.  UCP_ERR_CUDA keeps the CUDA error text (ucp_last_error).
  *     Per-vertex numerical problems never fail a call: they set bits of the
  *     optional vertex_status array (ucp_vertex_flag); P is NaN only for
- *     UCP_V_NONFINITE, UCP_V_BAD_PARAMS and UCP_V_CHOL_FAIL.
+ *     UCP_V_NONFINITE, UCP_V_BAD_PARAMS, UCP_V_CHOL_FAIL and UCP_V_TIMEOUT.
  *   - No kernel of this library traps, asserts or waits without a bound.
  */
 #ifndef UCP_H
@@ -156,7 +156,9 @@ typedef enum {
   UCP_V_BAD_PARAMS = 4,  /* a participating parameter set is invalid
                             (a > b, w < 0, lo > hi, a negative mass)            */
   UCP_V_CHOL_JITTER = 8, /* MVN covariance needed diagonal jitter               */
-  UCP_V_CHOL_FAIL = 16   /* MVN covariance could not be factorised              */
+  UCP_V_CHOL_FAIL = 16,  /* MVN covariance could not be factorised              */
+  UCP_V_TIMEOUT = 32     /* a bounded device-side wait while staging this
+                            vertex's tile expired; P is NaN                     */
 } ucp_vertex_flag;
 
 typedef struct {

@@ -9,6 +9,8 @@
 // four neighbours' parameters from shared memory (the neighbourhood access
 // of the paper's VTK-m worklet, Sec. "Integration with VTK-m and ParaView")
 // and integrates P_min / P_max exactly (device.cuh).
+#include <cudaTypedefs.h>
+
 #include "device.cuh"
 #include "launch.h"
 #include "tile.cuh"
@@ -103,6 +105,23 @@ __global__ void __launch_bounds__(NTHREADS, TileOcc<MODEL>::value) tile_kernel(F
                                                  (tile % tiles_x) * TX, sm);
 }
 
+// The same with the members staged by the tensor memory accelerator: shared
+// memory holds the member box (nc x (TYm + 2) x 40 floats, 128-byte
+// aligned), then the parameter tile, then the mbarrier.
+template <int MODEL, bool SADDLE = false>
+__global__ void __launch_bounds__(NTHREADS, TileOcc<MODEL>::value)
+    tile_kernel_tma(Field f, int tiles_x, const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ __align__(128) float smem[];
+  const int tile = blockIdx.x;
+  constexpr int TYm = TileH<MODEL>::value;
+  const int box_floats = f.tma_nc * (TYm + 2) * kBoxW;
+  float *sm = smem + box_floats;
+  const long long tile_f = tile_floats(MODEL, f.B, TYm);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sm + ((tile_f + 1) & ~1LL));
+  process_tile<MODEL, true, TYm, SADDLE, true>(f, f.y0 + (tile / tiles_x) * TYm,
+                                               (tile % tiles_x) * TX, sm, &tmap, smem, bar);
+}
+
 // ---------------------------------------------------------------------------
 // uniform parameters from a decompressed field and an error bound
 
@@ -139,6 +158,73 @@ cudaError_t launch_fit(const Field &f, int model, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// cuTensorMapEncodeTiled, from the driver (no link-time dependency)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+// Launch with TMA member staging when the members allow it (W % 4 == 0, a
+// 16-byte aligned base) and a box of at least one member fits next to the
+// parameter tile at the model's occupancy; returns false to fall back.
+template <int MODEL, bool SADDLE>
+static bool launch_tile_tma(const Field &f, int tiles_x, int tiles, cudaStream_t s,
+                            cudaError_t *err) {
+  constexpr int TYm = TileH<MODEL>::value;
+  if (f.W % 4 != 0 || (reinterpret_cast<uintptr_t>(f.ens) & 15) != 0) return false;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const size_t tile_b = (size_t)((tile_floats(MODEL, f.B, TYm) + 1) & ~1LL) * sizeof(float) + 16;
+  const size_t per_member = (size_t)(TYm + 2) * kBoxW * sizeof(float);
+  const size_t budget = (size_t)227 * 1024 / TileOcc<MODEL>::value - 1024;
+  if (budget < tile_b + per_member) return false;
+  int nc = (int)((budget - tile_b) / per_member);
+  if (nc > f.N) nc = f.N;
+  if (nc > 256) nc = 256;
+  CUtensorMap map;
+  const cuuint64_t dims[3] = {(cuuint64_t)f.W, (cuuint64_t)f.H, (cuuint64_t)f.N};
+  const cuuint64_t strides[2] = {(cuuint64_t)f.W * sizeof(float),
+                                 (cuuint64_t)f.plane * sizeof(float)};
+  const cuuint32_t box[3] = {(cuuint32_t)kBoxW, (cuuint32_t)(TYm + 2), (cuuint32_t)nc};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(f.ens), dims, strides, box,
+          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  static bool attr_set[128] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) {
+    cudaGetLastError();
+    return false;
+  }
+  if (!attr_set[dev]) {
+    if (cudaFuncSetAttribute(tile_kernel_tma<MODEL, SADDLE>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    attr_set[dev] = true;
+  }
+  Field g = f;
+  g.tma_nc = nc;
+  const size_t smem = (size_t)nc * per_member + tile_b;
+  tile_kernel_tma<MODEL, SADDLE><<<tiles, NTHREADS, smem, s>>>(g, tiles_x, map);
+  *err = cudaGetLastError();
+  return true;
+}
+
 template <int MODEL, bool FM, bool SADDLE>
 static cudaError_t launch_tile(const Field &f, cudaStream_t s) {
   constexpr int TYm = TileH<MODEL>::value;
@@ -167,6 +253,10 @@ static cudaError_t launch_tile(const Field &f, cudaStream_t s) {
   if (tiles_y <= 0) return cudaSuccess;
   const long long tiles = (long long)tiles_x * tiles_y;
   if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  if constexpr (FM) {
+    cudaError_t te = cudaSuccess;
+    if (launch_tile_tma<MODEL, SADDLE>(g, tiles_x, (int)tiles, s, &te)) return te;
+  }
   tile_kernel<MODEL, FM, SADDLE><<<(int)tiles, NTHREADS, smem, s>>>(g, tiles_x);
   return cudaGetLastError();
 }

@@ -33,7 +33,8 @@ enum : uint8_t {
   V_NONFINITE = 2,
   V_BAD = 4,
   V_JITTER = 8,
-  V_CHOLFAIL = 16
+  V_CHOLFAIL = 16,
+  V_TIMEOUT = 32
 };
 
 // Neighbour directions e, n, w, s (same order as the MVN variable slots 1..4).

@@ -22,6 +22,7 @@ struct Field {
   float epan_scale;
   unsigned cptypes;     // bit 1 min, bit 2 max, bit 4 saddle
   bool vec4;            // members may be read as aligned float4 (W % 4 == 0, 16B base)
+  int tma_nc;           // members per tensor-memory-accelerator box (TMA staging)
   int samples;          // Monte Carlo / semianalytical samples per vertex
   uint32_t seed_lo, seed_hi, field_id;
 };

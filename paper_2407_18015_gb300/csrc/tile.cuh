@@ -4,6 +4,8 @@
 // single-field kernel (closed.cu) and the persistent batch kernel (batch.cu).
 #pragma once
 
+#include <cuda.h>
+
 #include "device.cuh"
 #include "launch.h"
 
@@ -287,6 +289,212 @@ __device__ __forceinline__ void stage_vertex(const Field &f, float *sm, int l, l
   }
 }
 
+// ---------------------------------------------------------------------------
+// Member staging with the tensor memory accelerator: one bulk tensor copy
+// brings a box of nc members x (TYv + 2) rows x 40 columns (x from tx0 - 4, a
+// 16-byte boundary; y from ty0 - 1; out-of-range elements read as 0) into
+// shared memory, completing on an mbarrier.  Every thread then reduces the
+// members of the halo vertices it owns (l = tid, tid + 256, ...).  Larger
+// ensembles take several boxes in turn.
+
+constexpr int kBoxW = 40;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void proxy_async_fence() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y,
+                                            int z, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+// wait for the completion of phase `parity`; gives up after a bounded number
+// of polls (each poll itself returns after a bounded time)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+  for (int i = 0; i < (1 << 20); ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Statistics of the members of every in-grid halo vertex into the shared
+// parameter tile, as stage_members computes them (same arithmetic in the same
+// member order).  Returns false if a wait gave up (the tile is then invalid).
+template <int MODEL, int TYv>
+__device__ __forceinline__ bool stage_members_tma(const Field &f, float *sm, float *box,
+                                                  uint64_t *bar, const CUtensorMap *tmap,
+                                                  int ty0, int tx0) {
+  constexpr int HY = TYv + 2, HX = 34, HALO = HY * HX;
+  constexpr int PER = (HALO + NTHREADS - 1) / NTHREADS;
+  constexpr int PLANE = HY * kBoxW;
+  const int N = f.N, nc = f.tma_nc;
+  const unsigned box_bytes = (unsigned)(PLANE * nc * sizeof(float));
+  const int ylim = min(f.H, f.y1 + 1);
+  int off[PER], lv[PER];
+  bool in[PER];
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int l = threadIdx.x + p * NTHREADS;
+    const int r = l / HX, c = l - r * HX;
+    const int gy = ty0 + r - 1, gx = tx0 + c - 1;
+    lv[p] = l;
+    in[p] = l < HALO && gy >= 0 && gy < ylim && gx >= 0 && gx < f.W;
+    off[p] = r * kBoxW + c + 3;
+  }
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  unsigned phase = 0;
+  bool ok = true;
+  // load members [k0, k0 + nc) into the box; uniform result
+  auto load = [&](int k0) -> bool {
+    if (threadIdx.x == 0) {
+      proxy_async_fence();
+      mbar_expect_tx(bar, box_bytes);
+      tma_load_3d(box, tmap, tx0 - 4, ty0 - 1, k0, bar);
+    }
+    const bool r = mbar_wait(bar, phase);
+    phase ^= 1u;
+    return __syncthreads_and(r) != 0;
+  };
+  constexpr bool EP = MODEL == kEpan || MODEL == kGauss;
+  float mn[PER], mx[PER], x0[PER];
+  bool nf[PER];
+  Kahan s1[PER], s2[PER];
+  for (int k0 = 0; k0 < N && ok; k0 += nc) {
+    if (!load(k0)) {
+      ok = false;
+      break;
+    }
+    const int kn = min(nc, N - k0);
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+      if (!in[p]) continue;
+      const float *col = box + off[p];
+      if (k0 == 0) {
+        x0[p] = mn[p] = mx[p] = col[0];
+        nf[p] = false;
+      }
+      for (int k = 0; k < kn; ++k) {
+        const float v = col[k * PLANE];
+        nf[p] |= !isfinite(v);
+        mn[p] = fminf(mn[p], v);
+        mx[p] = fmaxf(mx[p], v);
+        if constexpr (EP) {
+          const float d = v - x0[p];
+          s1[p].add(d);
+          s2[p].add(d * d);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (!ok) {
+    // the copy that timed out may still land: wait for it (bounded) before
+    // the shared memory is left to another CTA
+    if (threadIdx.x == 0) mbar_wait(bar, phase ^ 1u);
+    __syncthreads();
+    return false;
+  }
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    if (!in[p]) continue;
+    const int l = lv[p];
+    if constexpr (EP) {
+      float m, w;
+      if (mn[p] == mx[p]) {
+        m = mn[p];
+        w = 0.f;
+      } else {
+        const float S1 = s1[p].get(), S2 = s2[p].get();
+        const float md = S1 / (float)N;
+        m = x0[p] + md;
+        const float scale = MODEL == kGauss ? 1.f : f.epan_scale;
+        w = scale * sqrtf(fmaxf(S2 - S1 * md, 0.f) / (float)(N - 1));
+      }
+      sm[l] = nf[p] ? qnan() : m;
+      sm[HALO + l] = nf[p] ? qnan() : w;
+    } else {
+      sm[l] = nf[p] ? qnan() : mn[p];
+      sm[HALO + l] = nf[p] ? qnan() : mx[p];
+    }
+  }
+  if constexpr (hist_params(MODEL)) {
+    const int B = f.B;
+    float sc[PER];
+    bool bin[PER];
+    bool any = false;
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+      bin[p] = false;
+      sc[p] = 0.f;
+      if (!in[p]) continue;
+      float *wq = sm + 2 * HALO + lv[p];
+      for (int b = 0; b < B; ++b) wq[b * HALO] = nf[p] ? qnan() : 0.f;
+      bin[p] = !nf[p] && mn[p] != mx[p];
+      if (!nf[p] && !bin[p]) wq[0] = 1.f;
+      sc[p] = bin[p] ? __fdiv_rn((float)B, __fsub_rn(mx[p], mn[p])) : 0.f;
+      any |= bin[p];
+    }
+    // the members are still in the box when one box held them all
+    for (int k0 = 0; k0 < N; k0 += nc) {
+      if (k0 > 0 || N > nc) {
+        if (!load(k0)) {
+          if (threadIdx.x == 0) mbar_wait(bar, phase ^ 1u);
+          __syncthreads();
+          return false;
+        }
+      }
+      const int kn = min(nc, N - k0);
+      if (any) {
+#pragma unroll
+        for (int p = 0; p < PER; ++p) {
+          if (!bin[p]) continue;
+          const float *col = box + off[p];
+          float *w0 = sm + 2 * HALO + lv[p];
+          for (int k = 0; k < kn; ++k)
+            w0[hist_bin(col[k * PLANE], mn[p], sc[p], B) * HALO] += 1.f;
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int p = 0; p < PER; ++p)
+      if (bin[p])
+        for (int b = 0; b < B; ++b) {
+          float *w = sm + (2 + b) * HALO + lv[p];
+          *w = __fdiv_rn(*w, (float)N);
+        }
+  }
+  return true;
+}
+
 // validity of one participant's parameters; returns status bits and the
 // histogram total mass
 template <int MODEL, int HALO>
@@ -318,13 +526,20 @@ __device__ __forceinline__ uint8_t check_params(const float *sm, int l, int B, f
 // members or loaded -- and phase 2 integrates every vertex of the tile.
 // SADDLE selects the saddle probability (Eq. saddleProb) instead of the
 // minimum / maximum: a separate instance, so neither pays for the other.
-template <int MODEL, bool FROM_MEMBERS, int TYv, bool SADDLE = false>
-__device__ __forceinline__ void process_tile(const Field &f, int ty0, int tx0, float *sm) {
+// TMA: the members are staged through the tensor map tmap into `box`, with
+// the mbarrier `bar` (FROM_MEMBERS only).
+template <int MODEL, bool FROM_MEMBERS, int TYv, bool SADDLE = false, bool TMA = false>
+__device__ __forceinline__ void process_tile(const Field &f, int ty0, int tx0, float *sm,
+                                             const CUtensorMap *tmap = nullptr,
+                                             float *box = nullptr, uint64_t *bar = nullptr) {
   constexpr int TY = TYv, TX = 32, HY = TYv + 2, HX = TX + 2, HALO = HY * HX;
   // rows beyond y1 are neither computed nor needed (row y1 is a neighbour)
   const int ylim = min(f.H, f.y1 + 1);
 
-  if (FROM_MEMBERS) {
+  bool staged = true;
+  if constexpr (FROM_MEMBERS && TMA) {
+    staged = stage_members_tma<MODEL, TY>(f, sm, box, bar, tmap, ty0, tx0);
+  } else if (FROM_MEMBERS) {
     // work items per halo row: the two halo columns (scalar) and eight
     // groups of four interior columns (one float4 per member when aligned)
     for (int it = threadIdx.x; it < HY * 10; it += NTHREADS) {
@@ -354,6 +569,21 @@ __device__ __forceinline__ void process_tile(const Field &f, int ty0, int tx0, f
     }
   }
   __syncthreads();
+  if (!staged) {  // a bounded wait gave up (uniform over the CTA): NaN + flag
+    for (int v = threadIdx.x; v < TY * TX; v += NTHREADS) {
+      const int gy = ty0 + v / TX, gx = tx0 + v % TX;
+      if (gy >= f.y1 || gx >= f.W) continue;
+      const long long gi = (long long)gy * f.W + gx;
+      if constexpr (SADDLE) {
+        if (f.out_saddle) f.out_saddle[gi] = qnan();
+      } else {
+        if ((f.cptypes & kMin) && f.out_min) f.out_min[gi] = qnan();
+        if ((f.cptypes & kMax) && f.out_max) f.out_max[gi] = qnan();
+      }
+      if (f.status) f.status[gi] = V_TIMEOUT;
+    }
+    return;
+  }
   if constexpr (MODEL == kHist) {
     // tail tables S_0..S_{B+1} in place of the masses, total mass and
     // status of every staged vertex (rows 2..3+B, 4+B, 5+B)
