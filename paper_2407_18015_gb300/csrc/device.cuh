@@ -411,9 +411,32 @@ __device__ __forceinline__ void epan_pieces(const float *x, const float (*pay)[4
   constexpr int NG = EpanNodes<J>::value;
   const float x0 = x[J], x1 = x[J + 1];
   const float half = 0.5f * (x1 - x0), mid = 0.5f * (x0 + x1);
-  float s = 0.f;
+  // nodes in pairs, one per half of a float2 (packed FP32 instructions)
+  const float2 one2 = make_float2(1.f, 1.f);
+  float2 s2 = make_float2(0.f, 0.f);
 #pragma unroll
-  for (int q = 0; q < NG; ++q) {
+  for (int q = 0; q + 1 < NG; q += 2) {
+    const float2 xx = __ffma2_rn(make_float2(half, half),
+                                 make_float2(gl_x<NG>(q), gl_x<NG>(q + 1)), make_float2(mid, mid));
+    const float2 u1 = __fmul2_rn(xx, make_float2(iw1, iw1));
+    const float2 g = __ffma2_rn(make_float2(-u1.x, -u1.y), u1, one2);
+    float2 f = __fmul2_rn(make_float2(c1, c1), make_float2(fmaxf(g.x, 0.f), fmaxf(g.y, 0.f)));
+#pragma unroll
+    for (int i = 0; i < J; ++i) {
+      // epan_surv of both nodes
+      float2 u = __fmul2_rn(__fadd2_rn(xx, make_float2(-pay[0][i], -pay[0][i])),
+                            make_float2(pay[1][i], pay[1][i]));
+      u = make_float2(fminf(fmaxf(u.x, -1.f), 1.f), fminf(fmaxf(u.y, -1.f), 1.f));
+      const float2 qq = __fadd2_rn(one2, make_float2(-u.x, -u.y));
+      const float2 sv = __fmul2_rn(__fmul2_rn(make_float2(0.25f, 0.25f), __fmul2_rn(qq, qq)),
+                                   __fadd2_rn(make_float2(2.f, 2.f), u));
+      f = __fmul2_rn(f, sv);
+    }
+    s2 = __ffma2_rn(make_float2(gl_w<NG>(q), gl_w<NG>(q + 1)), f, s2);
+  }
+  float s = s2.x + s2.y;
+  if constexpr (NG & 1) {
+    constexpr int q = NG - 1;
     const float xx = fmaf(half, gl_x<NG>(q), mid);
     const float u1 = xx * iw1;
     float f = c1 * fmaxf(fmaf(-u1, u1, 1.f), 0.f);
