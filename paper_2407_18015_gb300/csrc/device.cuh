@@ -141,6 +141,47 @@ __device__ __forceinline__ float2 bern_mean4_x2(const float2 *L, const float2 *R
                     __ffma2_rn(__fadd2_rn(e1, e3), w1, __fmul2_rn(e2, w2)));
 }
 
+// bern_mean<K> (K <= 4) of two products at once, one per half of a float2
+template <int K>
+__device__ __forceinline__ float2 bern_mean_x2(const float2 *L, const float2 *R) {
+  if constexpr (K == 4) {
+    return bern_mean4_x2(L, R);
+  } else {
+    float2 e[K + 1];
+    e[0] = L[0];
+    e[1] = R[0];
+#pragma unroll
+    for (int i = 1; i < K; ++i) {
+      e[i + 1] = __fmul2_rn(e[i], R[i]);
+#pragma unroll
+      for (int j = i; j >= 1; --j) e[j] = __ffma2_rn(e[j - 1], R[i], __fmul2_rn(e[j], L[i]));
+      e[0] = __fmul2_rn(e[0], L[i]);
+    }
+    if constexpr (K == 1) {
+      return __fmul2_rn(make_float2(0.5f, 0.5f), __fadd2_rn(e[0], e[1]));
+    } else if constexpr (K == 2) {
+      const float2 w0 = make_float2(BernW<2, 0>::value, BernW<2, 0>::value);
+      const float2 w1 = make_float2(BernW<2, 1>::value, BernW<2, 1>::value);
+      return __ffma2_rn(__fadd2_rn(e[0], e[2]), w0, __fmul2_rn(e[1], w1));
+    } else {
+      const float2 w0 = make_float2(BernW<3, 0>::value, BernW<3, 0>::value);
+      const float2 w1 = make_float2(BernW<3, 1>::value, BernW<3, 1>::value);
+      return __ffma2_rn(__fadd2_rn(e[0], e[3]), w0, __fmul2_rn(__fadd2_rn(e[1], e[2]), w1));
+    }
+  }
+}
+
+// Kahan summation of two sums at once
+struct Kahan2 {
+  float2 s = {0.f, 0.f}, c = {0.f, 0.f};
+  __device__ __forceinline__ void add(float2 v) {
+    const float2 y = __fadd2_rn(v, make_float2(-c.x, -c.y));
+    const float2 t = __fadd2_rn(s, y);
+    c = __fadd2_rn(__fadd2_rn(t, make_float2(-s.x, -s.y)), make_float2(-y.x, -y.y));
+    s = t;
+  }
+};
+
 // Sort four (key, payload...) tuples ascending by key with a 5-exchange network.
 template <int NP>
 __device__ __forceinline__ void cswap(float *k, float (*p)[4], int a, int b) {
@@ -275,6 +316,57 @@ __device__ __forceinline__ float uniform_side(float W1, float R, float al[4], fl
   return acc.get() * frcp(W1);
 }
 
+// uniform_side for the minimum (.x) and the maximum (.y) problems at once:
+// each half sorts its own breakpoints, then the pieces of both are integrated
+// with packed FP32 instructions.  R <= 0 gives 0.
+__device__ __forceinline__ float2 uniform_side2(float W1, float2 R, const float2 *al,
+                                                const float *sl) {
+  R = make_float2(fmaxf(R.x, 0.f), fmaxf(R.y, 0.f));
+  float tx[4], ty[4], px[2][4], py[2][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    tx[i] = fminf(fmaxf(al[i].x, 0.f), R.x);
+    ty[i] = fminf(fmaxf(al[i].y, 0.f), R.y);
+    px[0][i] = al[i].x; px[1][i] = sl[i];
+    py[0][i] = al[i].y; py[1][i] = sl[i];
+  }
+  sort4<2>(tx, px);
+  sort4<2>(ty, py);
+  float2 x[6] = {make_float2(0.f, 0.f), make_float2(tx[0], ty[0]), make_float2(tx[1], ty[1]),
+                 make_float2(tx[2], ty[2]), make_float2(tx[3], ty[3]), R};
+  float2 a[4], sv[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    a[i] = make_float2(px[0][i], py[0][i]);
+    sv[i] = make_float2(-px[1][i], -py[1][i]);
+  }
+  Kahan2 acc;
+  acc.add(x[1]);  // piece 0: no factor has started
+  float2 L[4], Rv[4];
+  const float2 one2 = make_float2(1.f, 1.f);
+  auto factor = [&](float2 xe, int i) {
+    const float2 v = __ffma2_rn(__fadd2_rn(xe, make_float2(-a[i].x, -a[i].y)), sv[i], one2);
+    return make_float2(fmaxf(v.x, 0.f), fmaxf(v.y, 0.f));
+  };
+#pragma unroll
+  for (int j = 1; j <= 4; ++j) {
+    const float2 x0 = x[j], x1 = x[j + 1];
+#pragma unroll
+    for (int i = 0; i < j - 1; ++i) L[i] = Rv[i];
+    L[j - 1] = factor(x0, j - 1);
+#pragma unroll
+    for (int i = 0; i < j; ++i) Rv[i] = factor(x1, i);
+    float2 I;
+    if (j == 1) I = bern_mean_x2<1>(L, Rv);
+    else if (j == 2) I = bern_mean_x2<2>(L, Rv);
+    else if (j == 3) I = bern_mean_x2<3>(L, Rv);
+    else I = bern_mean_x2<4>(L, Rv);
+    acc.add(__fmul2_rn(__fadd2_rn(x1, make_float2(-x0.x, -x0.y)), I));
+  }
+  const float iw = frcp(W1);
+  return make_float2(acc.s.x * iw, acc.s.y * iw);
+}
+
 struct UniParams {
   float a, b;
 };
@@ -312,6 +404,24 @@ __device__ __forceinline__ void uniform_vertex(UniParams c, const UniParams *nb,
 #pragma unroll
   for (int i = 0; i < 4; ++i)
     sl[i] = (present[i] && nb[i].a != nb[i].b) ? frcp(nb[i].b - nb[i].a) : 0.f;
+  if ((want & kMin) && (want & kMax)) {
+    // both problems at once; maximum: negated variables, origin at -b1
+    float2 al[4];
+    float2 R = make_float2(W1, W1);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (present[i]) {
+        al[i] = make_float2(nb[i].a - c.a, c.b - nb[i].b);
+        R = make_float2(fminf(R.x, nb[i].b - c.a), fminf(R.y, c.b - nb[i].a));
+      } else {
+        al[i] = make_float2(kFar, kFar);
+      }
+    }
+    const float2 p = uniform_side2(W1, R, al, sl);
+    pmin = p.x;
+    pmax = p.y;
+    return;
+  }
   if (want & kMin) {
     float al[4], s2[4], R = W1;
 #pragma unroll
