@@ -1168,6 +1168,30 @@ struct HistSeg {
     return c;
   }
   __device__ __forceinline__ float G(float x) const { return fmaf(-sl, x - el, s); }
+  // From the initial state, cross every edge at or below 0 at once: the
+  // state step() would reach edge by edge (the count of such edges comes
+  // from -lam / h and is then checked against the edges themselves).
+  template <int WS>
+  __device__ __forceinline__ void seek0(const float *S0, int B) {
+    if (nx > 0.f) return;  // the first edge is above 0 (also: absent)
+    int j;                 // edges lam + i h <= 0 for i < j
+    if (h > 0.f) {
+      j = (int)fminf(fmaxf(floorf(-lam * invh), 0.f), (float)B) + 1;
+      if (j <= B && fmaf((float)j, h, lam) <= 0.f) ++j;
+      if (j >= 2 && fmaf((float)(j - 1), h, lam) > 0.f) --j;
+    } else {
+      j = B + 1;  // a point mass at or below 0: all its edges coincide
+    }
+    const int off = addr - WS;
+    const int k = j - 1;  // the bin now entered
+    s = S0[off + k * WS];
+    sn = S0[off + j * WS];
+    addr = off + (j + 1) * WS;
+    sl = (s - sn) * invh;
+    el = fmaf((float)k, h, lam);
+    kf = (float)j;
+    nx = j <= B ? fmaf((float)j, h, lam) : kFar;
+  }
 };
 
 // Both probabilities of a non-degenerate histogram centre in one walk over

@@ -289,6 +289,34 @@ __device__ __forceinline__ void stage_vertex(const Field &f, float *sm, int l, l
   }
 }
 
+// Tail table S_0..S_{B+1} in place of the masses of staged vertex l, its total
+// mass and its status (rows 2..3+B, 4+B, 5+B; see hist_rows)
+template <int HALO>
+__device__ __forceinline__ void hist_tail_table(float *sm, int l, int B) {
+  const float a = sm[l], b = sm[HALO + l];
+  uint8_t st = (!isfinite(a) || !isfinite(b)) ? V_NONFINITE
+                                             : (a > b ? V_BAD : (a == b ? V_DEGENERATE : 0));
+  float t = 0.f;
+  for (int q = 0; q < B; ++q) {
+    const float w = sm[(2 + q) * HALO + l];
+    if (!isfinite(w)) st |= V_NONFINITE;
+    else if (w < 0.f) st |= V_BAD;
+    t += w;
+  }
+  const bool point = a == b;
+  float c = 0.f;
+  for (int q = 0; q < B; ++q) {
+    float *r = sm + (2 + q) * HALO + l;
+    const float w = *r;
+    *r = point ? 0.f : t - c;
+    c += w;
+  }
+  sm[(2 + B) * HALO + l] = 0.f;
+  sm[(3 + B) * HALO + l] = 0.f;
+  sm[(4 + B) * HALO + l] = t;
+  sm[(5 + B) * HALO + l] = (float)st;
+}
+
 // ---------------------------------------------------------------------------
 // Member staging with the tensor memory accelerator: one bulk tensor copy
 // brings a box of nc members x (TYv + 2) rows x 40 columns (x from tx0 - 4, a
@@ -462,9 +490,10 @@ __device__ __forceinline__ bool stage_members_tma(const Field &f, float *sm, flo
       sc[p] = bin[p] ? __fdiv_rn((float)B, __fsub_rn(mx[p], mn[p])) : 0.f;
       any |= bin[p];
     }
-    // the members are still in the box when one box held them all
-    for (int k0 = 0; k0 < N; k0 += nc) {
-      if (k0 > 0 || N > nc) {
+    // boxes in reverse order: the last one of the first pass is still there
+    const int last = ((N - 1) / nc) * nc;
+    for (int k0 = last; k0 >= 0; k0 -= nc) {
+      if (k0 != last) {
         if (!load(k0)) {
           if (threadIdx.x == 0) mbar_wait(bar, phase ^ 1u);
           __syncthreads();
@@ -491,6 +520,12 @@ __device__ __forceinline__ bool stage_members_tma(const Field &f, float *sm, flo
           float *w = sm + (2 + b) * HALO + lv[p];
           *w = __fdiv_rn(*w, (float)N);
         }
+    if constexpr (MODEL == kHist) {
+      // the owner also builds the vertex's tail table
+#pragma unroll
+      for (int p = 0; p < PER; ++p)
+        if (in[p]) hist_tail_table<HALO>(sm, lv[p], B);
+    }
   }
   return true;
 }
@@ -584,34 +619,9 @@ __device__ __forceinline__ void process_tile(const Field &f, int ty0, int tx0, f
     }
     return;
   }
-  if constexpr (MODEL == kHist) {
-    // tail tables S_0..S_{B+1} in place of the masses, total mass and
-    // status of every staged vertex (rows 2..3+B, 4+B, 5+B)
-    const int B = f.B;
-    for (int l = threadIdx.x; l < HALO; l += NTHREADS) {
-      const float a = sm[l], b = sm[HALO + l];
-      uint8_t st = (!isfinite(a) || !isfinite(b)) ? V_NONFINITE
-                                                 : (a > b ? V_BAD : (a == b ? V_DEGENERATE : 0));
-      float t = 0.f;
-      for (int q = 0; q < B; ++q) {
-        const float w = sm[(2 + q) * HALO + l];
-        if (!isfinite(w)) st |= V_NONFINITE;
-        else if (w < 0.f) st |= V_BAD;
-        t += w;
-      }
-      const bool point = a == b;
-      float c = 0.f;
-      for (int q = 0; q < B; ++q) {
-        float *r = sm + (2 + q) * HALO + l;
-        const float w = *r;
-        *r = point ? 0.f : t - c;
-        c += w;
-      }
-      sm[(2 + B) * HALO + l] = 0.f;
-      sm[(3 + B) * HALO + l] = 0.f;
-      sm[(4 + B) * HALO + l] = t;
-      sm[(5 + B) * HALO + l] = (float)st;
-    }
+  if constexpr (MODEL == kHist && !(FROM_MEMBERS && TMA)) {
+    // tail tables of every staged vertex (the TMA staging builds them itself)
+    for (int l = threadIdx.x; l < HALO; l += NTHREADS) hist_tail_table<HALO>(sm, l, f.B);
     __syncthreads();
   }
   if constexpr (MODEL == kSemi) {
@@ -758,9 +768,7 @@ __device__ __forceinline__ void process_tile(const Field &f, int ty0, int tx0, f
           Tw[i] = T[i];
           const float lo = sm[nl[i]], hi = sm[HALO + nl[i]];
           h.init<HALO>(S0, nl[i], lo - lo1, lo == hi ? 0.f : (hi - lo) / (float)B, T[i]);
-          // move to the segment that contains x = 0
-          for (int g = 0; g <= B && h.nx <= 0.f; ++g)
-            if (!h.step<HALO>(S0, h.nx, (float)B)) break;
+          h.seek0<HALO>(S0, B);  // to the segment that contains x = 0
         }
         if constexpr (!SADDLE) {
           hist_walk<HALO>(S0, l, B, hi1 - lo1, nw, Tw, f.cptypes, pmin, pmax);
