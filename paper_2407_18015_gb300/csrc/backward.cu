@@ -20,6 +20,7 @@
 // Maxima use the negated variables (P_max(theta) = P_min(-theta)).
 #include "device.cuh"
 #include "launch.h"
+#include "tile.cuh"
 
 namespace ucp {
 
@@ -675,6 +676,230 @@ __global__ void __launch_bounds__(128) partials_kernel(Field f, int want_max,
   }
 }
 
+// ---------------------------------------------------------------------------
+// histogram adjoint, tiled (non-degenerate centres)
+//
+// The partials of P_min = int pdf_1 prod_n G_n (mixture form) are
+//   own bin j:        (1/h1) int_{bin j} prod_n G_n
+//   neighbour n, k:   int pdf_1 S_nk LOO_n,  LOO_n = prod_{m != n} G_m,
+// with S_nk = 1 below bin k of n, (e_{k+1} - x)/h_n on it, 0 above.  One
+// merge walk (the forward's walkers over shared-memory tail tables) carries,
+// per neighbour, the running integral C_n = int_0^x pdf_1 LOO_n and the
+// in-bin integral of its current bin; leaving bin k stores C_n(e_k) + in-bin.
+// On a piece every factor is linear, so the products (degree <= 4) are
+// integrated exactly by the 3-point Gauss-Legendre rule at the same three
+// nodes for all of them; the leave-one-out products come from prefix and
+// suffix products at the nodes.  No branch depends on the lane's data except
+// the end of the walk.  The maximum is the minimum of the mirrored problem
+// (-X; bins reversed), staged mirrored.
+
+constexpr int kGradTY = 16;
+
+template <int HALO>
+__device__ __forceinline__ void hist_grad_walk(const float *S0, int l, const int *nl,
+                                               const bool *present, int B, bool mirrored,
+                                               float wv, float *rows, long long plane,
+                                               long long gi) {
+  const float lo1 = S0[l - 2 * HALO], hi1 = S0[l - HALO];
+  const float W1 = hi1 - lo1;
+  auto row = [&](int slot, int q) -> float * {
+    return rows + ((long long)slot * B + (mirrored ? B - 1 - q : q)) * plane + gi;
+  };
+  if (!(W1 <= 1e38f)) {  // a support too wide for the walk's frame: no partials
+    for (int sl = 0; sl < 5; ++sl)
+      if (sl == 0 || present[sl - 1])
+        for (int q = 0; q < B; ++q) *row(sl, q) = __int_as_float(0x7fc00000);
+    return;
+  }
+  const float Bf = (float)B;
+  HistSeg nw[4];
+  float T[4];
+  int kb[4];  // bin of neighbour i after the seek
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    HistSeg &h = nw[i];
+    if (!present[i]) {
+      h.init_absent(l, Bf);
+      T[i] = 1.f;
+      kb[i] = -1;
+      continue;
+    }
+    const float lo = S0[nl[i] - 2 * HALO], hi = S0[nl[i] - HALO];
+    T[i] = S0[nl[i] + (2 + B) * HALO];
+    h.init<HALO>(S0, nl[i], lo - lo1, lo == hi ? 0.f : (hi - lo) / Bf, T[i]);
+    h.seek0<HALO>(S0, B);
+    kb[i] = (int)h.kf - 1;
+    // bins entirely below the centre's support: their survival is 0 there
+    for (int q = 0; q < min(kb[i], B); ++q) *row(1 + i, q) = 0.f;
+  }
+  const float h1 = W1 / Bf, ih1 = frcp(h1);
+  int addr_c = l + 2 * HALO;
+  float kcf = 1.f;
+  float sc = S0[l], scn = S0[l + HALO];
+  float dens = (sc - scn) * ih1;
+  float nxc = B > 1 ? h1 : W1;
+  int jc = 0;
+  float Gl[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) Gl[i] = nw[i].G(0.f);
+  float own = 0.f, C[4] = {0.f, 0.f, 0.f, 0.f}, Cs[4] = {0.f, 0.f, 0.f, 0.f};
+  float inb[4] = {0.f, 0.f, 0.f, 0.f};
+  // 3-point Gauss-Legendre on [0, 1]
+  const float t0 = 0.11270166537925831f, t2 = 0.88729833462074169f;
+  const float wE = 5.f / 18.f, wM = 8.f / 18.f;
+  float x0 = 0.f;
+  const int max_steps = 5 * (B + 2) + 4;
+  for (int step = 0; step < max_steps && x0 < W1; ++step) {
+    float x1 = fminf(fminf(nw[0].nx, nw[1].nx), fminf(nw[2].nx, nw[3].nx));
+    x1 = fmaxf(fminf(x1, nxc), x0);
+    float Gr[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) Gr[i] = nw[i].G(x1);
+    const float len = x1 - x0, a = len * dens;
+    // factor values at the nodes
+    float f[3][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float d = Gr[i] - Gl[i];
+      f[0][i] = fmaf(d, t0, Gl[i]);
+      f[1][i] = fmaf(d, 0.5f, Gl[i]);
+      f[2][i] = fmaf(d, t2, Gl[i]);
+    }
+    // in-bin weights (e_next - x) / h of each neighbour inside a bin
+    float wl[4], wr[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const bool in = nw[i].kf >= 1.f && nw[i].kf <= Bf;
+      wl[i] = in ? (nw[i].nx - x0) * nw[i].invh : 0.f;
+      wr[i] = in ? (nw[i].nx - x1) * nw[i].invh : 0.f;
+    }
+    float full = 0.f, loo[4] = {0.f, 0.f, 0.f, 0.f}, loow[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float wq = q == 1 ? wM : wE, tq = q == 0 ? t0 : (q == 1 ? 0.5f : t2);
+      const float p2 = f[q][0] * f[q][1], p3 = p2 * f[q][2];
+      const float s2 = f[q][3] * f[q][2], s3 = s2 * f[q][1];
+      const float L[4] = {s3, f[q][0] * s2, p2 * f[q][3], p3};
+      full = fmaf(wq, p3 * f[q][3], full);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        loo[i] = fmaf(wq, L[i], loo[i]);
+        loow[i] = fmaf(wq * fmaf(wr[i] - wl[i], tq, wl[i]), L[i], loow[i]);
+      }
+    }
+    own = fmaf(len, full, own);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      C[i] = fmaf(a, loo[i], C[i]);
+      inb[i] = fmaf(a, loow[i], inb[i]);
+    }
+    // crossings: a neighbour leaving bin k stores its partial
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int k = (int)nw[i].kf - 1;  // the bin being left, if it crosses
+      const bool c = nw[i].step<HALO>(S0, x1, Bf);
+      if (c && present[i] && k >= 0 && k < B) *row(1 + i, k) = wv * (Cs[i] + inb[i]);
+      Cs[i] = c ? C[i] : Cs[i];
+      inb[i] = c ? 0.f : inb[i];
+      Gl[i] = c ? nw[i].s : Gr[i];
+    }
+    {
+      const bool c = nxc <= x1;
+      if (c && jc < B) *row(0, jc) = wv * own * ih1;
+      own = c ? 0.f : own;
+      jc += c ? 1 : 0;
+      const float t = S0[addr_c];
+      sc = c ? scn : sc;
+      scn = c ? t : scn;
+      addr_c += c ? HALO : 0;
+      kcf = c ? kcf + 1.f : kcf;
+      nxc = c ? (kcf < Bf ? kcf * h1 : (kcf == Bf ? W1 : kFar)) : nxc;
+      dens = (sc - scn) * ih1;
+    }
+    x0 = x1;
+  }
+  for (int q = jc; q < B; ++q) *row(0, q) = 0.f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if (!present[i]) continue;
+    const int k = (int)nw[i].kf - 1;
+    if (k >= 0 && k < B) *row(1 + i, k) = wv * (Cs[i] + inb[i]);
+    // bins above the walk: their survival is 1 on the whole support
+    for (int q = max(k + 1, 0); q < B; ++q) *row(1 + i, q) = wv * C[i];
+  }
+}
+
+template <int TYv>
+__global__ void __launch_bounds__(NTHREADS, 2)
+    hist_partials_tile(Field f, int tiles_x, int want_max, const float *__restrict__ weight,
+                       float *__restrict__ rows) {
+  extern __shared__ float sm[];
+  constexpr int TY = TYv, TX = 32, HY = TY + 2, HX = TX + 2, HALO = HY * HX;
+  const int B = f.B;
+  const long long plane = f.plane;
+  const int ty0 = f.y0 + ((int)blockIdx.x / tiles_x) * TY, tx0 = ((int)blockIdx.x % tiles_x) * TX;
+  const int ylim = min(f.H, f.y1 + 1);
+  // stage the parameters (mirrored for the maximum: -X on [-hi, -lo], bins reversed)
+  for (int l = threadIdx.x; l < HALO; l += NTHREADS) {
+    const int r = l / HX, c = l - r * HX;
+    const int gy = ty0 + r - 1, gx = tx0 + c - 1;
+    if (gy < 0 || gy >= ylim || gx < 0 || gx >= f.W) continue;
+    const long long gi = (long long)gy * f.W + gx;
+    const float a = f.params[gi], b = f.params[plane + gi];
+    sm[l] = want_max ? -b : a;
+    sm[HALO + l] = want_max ? -a : b;
+    for (int q = 0; q < B; ++q)
+      sm[(2 + q) * HALO + l] = f.params[(long long)(2 + (want_max ? B - 1 - q : q)) * plane + gi];
+  }
+  __syncthreads();
+  for (int l = threadIdx.x; l < HALO; l += NTHREADS) hist_tail_table<HALO>(sm, l, B);
+  __syncthreads();
+  const unsigned short *order = hist_order<TY, HALO>(f, sm, ty0, tx0);
+  const float *S0 = sm + 2 * HALO;
+  for (int it = threadIdx.x; it < TY * TX; it += NTHREADS) {
+    const int j = it / NTHREADS, w = threadIdx.x >> 5, nwp = NTHREADS / 32;
+    const int v = order[(j * nwp + ((j & 1) ? nwp - 1 - w : w)) * 32 + (threadIdx.x & 31)];
+    const int r = v / TX + 1, c = v % TX + 1;
+    const int gy = ty0 + r - 1, gx = tx0 + c - 1;
+    if (gy >= f.y1 || gx >= f.W) continue;
+    const int l = r * HX + c;
+    const long long gi = (long long)gy * f.W + gx;
+    bool present[4];
+    int nl[4];
+    long long ni[4];
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int yy = gy + kDy[i], xx = gx + kDx[i];
+      present[i] = (yy >= 0 && yy < f.H && xx >= 0 && xx < f.W);
+      nl[i] = l + kDy[i] * HX + kDx[i];
+      ni[i] = present[i] ? (long long)yy * f.W + xx : gi;
+      k += present[i];
+    }
+    int st = (int)sm[(5 + B) * HALO + l];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (present[i]) st |= (int)sm[(5 + B) * HALO + nl[i]] & (V_NONFINITE | V_BAD);
+    const float wv = weight[gi];
+    if ((st & (V_NONFINITE | V_BAD)) || (f.boundary == 1 && k < 4)) {
+      const float fill = (st & (V_NONFINITE | V_BAD)) ? qnan() : 0.f;
+      for (int sl = 0; sl < 5; ++sl)
+        for (int q = 0; q < B; ++q) rows[((long long)sl * B + q) * plane + gi] = fill;
+      continue;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (!present[i])
+        for (int q = 0; q < B; ++q) rows[((long long)(1 + i) * B + q) * plane + gi] = 0.f;
+    if (sm[l] == sm[HALO + l]) {
+      // a point-mass centre: the product of tails (global-memory path)
+      hist_grad_vertex(f.params, plane, gi, ni, present, B, want_max != 0, wv, rows);
+    } else {
+      hist_grad_walk<HALO>(S0, l, nl, present, B, want_max != 0, wv, rows, plane, gi);
+    }
+  }
+}
+
 // pass 2: grad[q][u] = own row + the rows u's neighbours wrote about u
 __global__ void __launch_bounds__(256) gather_kernel(Field f, int Q, const float *__restrict__ rows,
                                                      float *__restrict__ grad) {
@@ -708,7 +933,31 @@ cudaError_t launch_backward(const Field &f, int model, int cptype, const float *
   switch (model) {
     case kUniform: partials_kernel<kUniform><<<(int)b, 128, 0, s>>>(f, want_max, weight, rows); break;
     case kEpan: partials_kernel<kEpan><<<(int)b, 128, 0, s>>>(f, want_max, weight, rows); break;
-    case kHist: partials_kernel<kHist><<<(int)b, 128, 0, s>>>(f, want_max, weight, rows); break;
+    case kHist: {
+      constexpr int TYg = kGradTY;
+      static bool attr_set[128] = {};
+      int dev = 0;
+      cudaError_t e = cudaGetDevice(&dev);
+      if (e != cudaSuccess) return e;
+      if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+      if (!attr_set[dev]) {
+        e = cudaFuncSetAttribute(hist_partials_tile<TYg>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(tile_floats(kHist, kMaxBins, TYg) * sizeof(float)));
+        if (e != cudaSuccess) {
+          cudaGetLastError();
+          return e;
+        }
+        attr_set[dev] = true;
+      }
+      const int tiles_x = (f.W + TX - 1) / TX, tiles_y = (f.y1 - f.y0 + TYg - 1) / TYg;
+      const long long tiles = (long long)tiles_x * tiles_y;
+      if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+      if (tiles > 0)
+        hist_partials_tile<TYg><<<(int)tiles, NTHREADS,
+                                  (size_t)tile_floats(kHist, f.B, TYg) * sizeof(float), s>>>(
+            f, tiles_x, want_max, weight, rows);
+      break;
+    }
     default: return cudaErrorInvalidValue;
   }
   cudaError_t e = cudaGetLastError();
