@@ -26,6 +26,7 @@ UCP_OK, UCP_ERR_ARG, UCP_ERR_SHAPE, UCP_ERR_CUDA, UCP_ERR_NOMEM, UCP_ERR_TIMEOUT
     UCP_ERR_UNSUPPORTED = range(7)
 UCP_V_DEGENERATE, UCP_V_NONFINITE, UCP_V_BAD_PARAMS, UCP_V_CHOL_JITTER, UCP_V_CHOL_FAIL = \
     1, 2, 4, 8, 16
+UCP_V_TIMEOUT = 32
 
 MODELS = {"uniform": UCP_UNIFORM, "epanechnikov": UCP_EPANECHNIKOV,
           "histogram": UCP_HISTOGRAM, "mvn": UCP_MVN_MC,
