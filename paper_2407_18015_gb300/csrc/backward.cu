@@ -590,14 +590,16 @@ __device__ void hist_grad_vertex(const float *params, long long plane, long long
 }
 
 // ---------------------------------------------------------------------------
-// pass 1: partial rows per centre
+// pass 1: partial rows per centre (uniform, Epanechnikov; histograms:
+// hist_partials_tile above)
 
 template <int MODEL>
 __global__ void __launch_bounds__(128) partials_kernel(Field f, int want_max,
                                                        const float *__restrict__ weight,
                                                        float *__restrict__ rows) {
   const long long plane = f.plane;
-  const int Q = (MODEL == kHist) ? f.B : 2;
+  static_assert(MODEL == kUniform || MODEL == kEpan, "histograms use hist_partials_tile");
+  const int Q = 2;
   for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < plane;
        v += (long long)gridDim.x * blockDim.x) {
     const int y = (int)(v / f.W), x = (int)(v % f.W);
@@ -613,18 +615,12 @@ __global__ void __launch_bounds__(128) partials_kernel(Field f, int want_max,
     }
     // validity of every participant
     bool bad = false;
-    const int P = (MODEL == kHist) ? 2 + f.B : 2;
     for (int t = 0; t < 5; ++t) {
       if (t > 0 && !present[t - 1]) continue;
       const long long u = t == 0 ? v : ni[t - 1];
       const float a = f.params[u], b = f.params[plane + u];
       if (!isfinite(a) || !isfinite(b)) bad = true;
       else if (MODEL == kEpan ? (b < 0.f) : (a > b)) bad = true;
-      if (MODEL == kHist)
-        for (int q = 2; q < P; ++q) {
-          const float w = f.params[(long long)q * plane + u];
-          if (!(isfinite(w) && w >= 0.f)) bad = true;
-        }
     }
     const float wv = weight[v];
     if (bad || (f.boundary == 1 && k < 4)) {
@@ -665,13 +661,6 @@ __global__ void __launch_bounds__(128) partials_kernel(Field f, int want_max,
         rows[((long long)(1 + i) * 2) * plane + v] = wv * g.nm[i];
         rows[((long long)(1 + i) * 2 + 1) * plane + v] = wv * g.nw[i];
       }
-    } else {
-      // absent neighbours: zero their rows (never gathered, kept defined)
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        if (!present[i])
-          for (int q = 0; q < Q; ++q) rows[((long long)(1 + i) * Q + q) * plane + v] = 0.f;
-      hist_grad_vertex(f.params, plane, v, ni, present, f.B, want_max != 0, wv, rows);
     }
   }
 }
