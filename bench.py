@@ -366,7 +366,7 @@ def run_ours(args):
                                "hist-8, min+max, fused fit+integrate",
                    "grid": [H2, W2], "members": N2, "bins": BINS2,
                    "parallelism": f"replicas x{world}",
-                   "l2": "flushed between timed steps (512 MB write)"},
+                   "l2": "flushed between timed steps (512 MB written, then another 512 MB read)"},
         "gpu_launches": len(MODELS2) * args.steps,
         "clocks": clocks,
         "roofline": rf,
