@@ -57,7 +57,8 @@ __device__ __forceinline__ void run_tile(const Field &f, long long local, int ti
   process_tile<MODEL, true, TYv>(f, ty0, tx0, sm);
 }
 
-__global__ void __launch_bounds__(NTHREADS, 2)
+// three resident CTAs per SM: 80 registers, the histogram walk's budget
+__global__ void __launch_bounds__(NTHREADS, 3)
     batch_kernel(const BatchItem *__restrict__ items, int nitems, long long total,
                  unsigned long long *__restrict__ counter) {
   extern __shared__ float sm[];
