@@ -246,6 +246,42 @@ def cpu_baseline_headline(ens_np):
             "sample": "the full 1024x1024x20 field, all three models, min and max, once"}
 
 
+def oracle_mvn_rate(ens_np, crop=48, samples=10000):
+    """The oracle's Monte Carlo (FP64, same Philox stream contract) on a crop
+    of the workload: vertices/s and samples/s on the host cores."""
+    import oracle
+    oracle.build()
+    sub = np.ascontiguousarray(ens_np[:, :crop, :crop])
+    t = time.perf_counter()
+    p, _ = oracle.fit(sub, oracle.MVN)
+    oracle.mvn_mc_at(p, np.arange(crop * crop), samples, 0x5EED)
+    dt = time.perf_counter() - t
+    return {"vertices_per_s": crop * crop / dt, "samples_per_s": crop * crop * samples / dt,
+            "cores": oracle.get_threads(), "seconds": dt,
+            "sample": f"a {crop}x{crop} crop (its own boundary), fit + {samples} samples each"}
+
+
+def oracle_fwd_bwd_rate(e4, weight, model, bins, rows=32):
+    """The oracle's fit, probability and analytic gradient on a strip of the
+    2048x2048x50 workload: forward and forward + adjoint vertices/s."""
+    import oracle
+    oracle.build()
+    strip = np.ascontiguousarray(e4[:, :rows, :].cpu().numpy())
+    wt = np.ascontiguousarray(weight[:rows, :].cpu().numpy())
+    mid = {"uniform": 0, "epanechnikov": 1, "histogram": 2}[model]
+    t = time.perf_counter()
+    p, _ = oracle.fit(strip, mid, bins=bins or 8)
+    oracle.prob(p, mid, bins=bins or 8)
+    t1 = time.perf_counter()
+    oracle.grad(p, mid, wt, cptype=1, bins=bins or 8)
+    t2 = time.perf_counter()
+    n = rows * strip.shape[2]
+    return {"fwd_vertices_per_s": n / (t1 - t), "fwd_bwd_vertices_per_s": n / (t2 - t),
+            "cores": oracle.get_threads(), "seconds": t2 - t,
+            "sample": f"{rows} rows of the 2048x2048 field (fit, P_min and P_max, gradient of "
+                      "sum W P_min)"}
+
+
 class L2Flush:
     """Write a 512 MB buffer, then read another: the L2 (126 MB) ends up
     holding clean lines of unrelated data, so the next step neither hits in L2
@@ -438,7 +474,8 @@ def other_rows(torch, ucp, ctx, dev, args, flush, peaks):
         samples = 512 * 512 * 10000
         rows["mvn_512x512x40_S10000"] = {
             "ms": ms, "vertices_per_s": 512 * 512 / (ms / 1e3),
-            "samples_per_s": samples / (ms / 1e3), "min_and_max": True}
+            "samples_per_s": samples / (ms / 1e3), "min_and_max": True,
+            "oracle": oracle_mvn_rate(e3.cpu().numpy())}
         del e3
     if "fwdbwd" in want:
         e4 = torch.from_numpy(synth.ensemble_bimodal(2048, 2048, 50, seed=4)).to(dev)
@@ -463,7 +500,8 @@ def other_rows(torch, ucp, ctx, dev, args, flush, peaks):
                 "ms_fwd_bwd": ms_fb / steps,
                 "fwd_bwd_vertices_per_s": 2048 * 2048 / (ms_fb / steps / 1e3),
                 "ms_fwd": ms_fw / steps,
-                "fwd_vertices_per_s": 2048 * 2048 / (ms_fw / steps / 1e3)}
+                "fwd_vertices_per_s": 2048 * 2048 / (ms_fw / steps / 1e3),
+                "oracle": oracle_fwd_bwd_rate(e4, Wt, m, b)}
             del params, grad
         del e4
     if "batch" in want:
