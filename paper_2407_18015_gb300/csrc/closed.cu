@@ -158,20 +158,20 @@ cudaError_t launch_fit(const Field &f, int model, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// cuTensorMapEncodeTiled, from the driver (no link-time dependency)
+// cuTensorMapEncodeTiled, from the driver (no link-time dependency); looked
+// up once (thread-safe static initialisation)
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() {
     void *p = nullptr;
     cudaDriverEntryPointQueryResult q;
+    PFN_cuTensorMapEncodeTiled_v12000 f = nullptr;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
                                          &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+      f = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
     cudaGetLastError();
-  }
+    return f;
+  }();
   return fn;
 }
 

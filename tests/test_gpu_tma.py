@@ -111,3 +111,31 @@ def test_tma_boundary_zero(ucp, ctx):
         _, _, ra, rb, _, _ = _run_both(ucp, ctx, ens_np, model, bins, boundary=1)
         for x, y in zip(ra, rb):
             np.testing.assert_array_equal(x.cpu().numpy(), y.cpu().numpy())
+
+
+def test_large_grid_64bit_offsets(ucp, ctx, orc):
+    """A 12288 x 12288 grid with 3 members (453 M member floats; member and
+    output offsets beyond 2^31): uniform and histogram-4 minimum / maximum on
+    sampled vertices against the oracle on the GPU's parameters."""
+    H = W = 12288
+    N = 3
+    g = torch.Generator(device="cuda").manual_seed(3)
+    ens = torch.randn((N, H, W), device="cuda", generator=g)
+    rng = np.random.default_rng(12)
+    idx = np.concatenate([[0, W - 1, (H - 1) * W, H * W - 1],
+                          rng.integers(0, H * W, 400)]).astype(np.int64)
+    for model, bins in (("uniform", 0), ("histogram", 4)):
+        d = ucp.make_desc(model, bins=bins or 8)
+        pmin, pmax, _ = ctx.probability(ens, d)
+        params = ctx.fit(ens, d)
+        torch.cuda.synchronize()
+        for i in idx:
+            y, x = int(i // W), int(i % W)
+            y0, y1, x0, x1 = max(y - 1, 0), min(y + 2, H), max(x - 1, 0), min(x + 2, W)
+            # the in-grid neighbourhood: its edges are the grid's edges
+            grid = params[:, y0:y1, x0:x1].double().cpu().numpy()
+            c = (y - y0) * (x1 - x0) + (x - x0)
+            a, b, _ = orc.prob_at(grid, d.model, [c], bins=d.bins)
+            assert abs(pmin[y, x].item() - a[0]) <= 1e-5
+            assert abs(pmax[y, x].item() - b[0]) <= 1e-5
+        del pmin, pmax, params
