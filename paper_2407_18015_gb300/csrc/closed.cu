@@ -11,6 +11,8 @@
 // and integrates P_min / P_max exactly (device.cuh).
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+
 #include "device.cuh"
 #include "launch.h"
 #include "tile.cuh"
@@ -89,37 +91,65 @@ struct TileOcc {
   static constexpr int value = MODEL == kUniform ? 5 : (MODEL == kEpan ? 4 : (MODEL == kHist ? 3 : 2));
 };
 
-// tile height: 16, or 8 for the estimator (whose shared tile also holds the
-// running mass sums and whose per-vertex work makes the halo negligible)
+// tile height: 8 rows for the uniform and histogram models and the
+// estimator (a 20-member box fits next to the parameter tile, and the
+// histogram's per-bin rows fit at three CTAs per SM), 16 for the Gaussian
+// and, from parameters, Epanechnikov models (a smaller halo share).  The
+// fused Epanechnikov kernel takes 8 rows when all members fit one box of 8
+// rows, else 16: with several boxes either way, the halo's share of the
+// compensated sums outweighs the extra boxes.  Histograms with more bins
+// than the per-bin rows allow take 16 rows.
 template <int MODEL>
 struct TileH {
-  static constexpr int value = MODEL == kSemi ? 8 : TY;
+  static constexpr int value = (MODEL == kGauss || MODEL == kEpan) ? TY : 8;
 };
 
-template <int MODEL, bool FROM_MEMBERS, bool SADDLE = false>
+// histograms walk per-bin rows at 8-row tiles (the launcher takes 8 rows
+// only when they fit), the segment walker at 16
+template <int MODEL, int TYm>
+struct HistRows {
+  static constexpr bool value = MODEL == kHist && TYm == 8;
+};
+
+// Shared memory: the parameter tile, then (HistRows) the per-bin rows,
+// 16-byte aligned.
+template <int MODEL, bool FROM_MEMBERS, bool SADDLE, int TYm>
 __global__ void __launch_bounds__(NTHREADS, TileOcc<MODEL>::value) tile_kernel(Field f, int tiles_x) {
-  extern __shared__ float sm[];
+  extern __shared__ __align__(16) float sm[];
   const int tile = blockIdx.x;
-  constexpr int TYm = TileH<MODEL>::value;
-  process_tile<MODEL, FROM_MEMBERS, TYm, SADDLE>(f, f.y0 + (tile / tiles_x) * TYm,
-                                                 (tile % tiles_x) * TX, sm);
+  constexpr bool ROWS = HistRows<MODEL, TYm>::value;
+  float4 *R4 = nullptr;
+  if constexpr (ROWS)
+    R4 = reinterpret_cast<float4 *>(sm + ((tile_floats(MODEL, f.B, TYm) + 3) & ~3LL));
+  process_tile<MODEL, FROM_MEMBERS, TYm, SADDLE, false, ROWS>(
+      f, f.y0 + (tile / tiles_x) * TYm, (tile % tiles_x) * TX, sm, nullptr, nullptr, nullptr, R4);
+}
+
+// rows of a histogram tile's per-bin tables (hist_r4_rows float4 per halo
+// vertex), in floats
+__host__ __device__ constexpr int r4_floats(int B, int TYv) {
+  return 4 * hist_r4_rows(B) * (TYv + 2) * (TX + 2);
 }
 
 // The same with the members staged by the tensor memory accelerator: shared
 // memory holds the member box (nc x (TYm + 2) x 40 floats, 128-byte
-// aligned), then the parameter tile, then the mbarrier.
-template <int MODEL, bool SADDLE = false>
+// aligned) -- for HistRows histograms the same room then takes the per-bin
+// rows, once the box is no longer read -- then the parameter tile, then the
+// mbarrier.
+template <int MODEL, bool SADDLE, int TYm>
 __global__ void __launch_bounds__(NTHREADS, TileOcc<MODEL>::value)
     tile_kernel_tma(Field f, int tiles_x, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(128) float smem[];
   const int tile = blockIdx.x;
-  constexpr int TYm = TileH<MODEL>::value;
   const int box_floats = f.tma_nc * (TYm + 2) * kBoxW;
-  float *sm = smem + box_floats;
+  constexpr bool ROWS = HistRows<MODEL, TYm>::value;
+  const int r4 = ROWS ? r4_floats(f.B, TYm) : 0;
+  float *sm = smem + max(box_floats, r4);
   const long long tile_f = tile_floats(MODEL, f.B, TYm);
   uint64_t *bar = reinterpret_cast<uint64_t *>(sm + ((tile_f + 1) & ~1LL));
-  process_tile<MODEL, true, TYm, SADDLE, true>(f, f.y0 + (tile / tiles_x) * TYm,
-                                               (tile % tiles_x) * TX, sm, &tmap, smem, bar);
+  process_tile<MODEL, true, TYm, SADDLE, true, ROWS>(
+      f, f.y0 + (tile / tiles_x) * TYm, (tile % tiles_x) * TX, sm, &tmap, smem, bar,
+      ROWS ? reinterpret_cast<float4 *>(smem) : nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -175,23 +205,36 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
+// Members per TMA box next to a TYm-row parameter tile at the model's
+// occupancy (0: not even one), capped at N and at the box limit of 256.
+template <int MODEL, int TYm>
+static int tma_box_members(int N, int B) {
+  const size_t tile_b = (size_t)((tile_floats(MODEL, B, TYm) + 1) & ~1LL) * sizeof(float) + 16;
+  const size_t per_member = (size_t)(TYm + 2) * kBoxW * sizeof(float);
+  const size_t budget = (size_t)227 * 1024 / TileOcc<MODEL>::value - 1024;
+  if (budget < tile_b + per_member) return 0;
+  const size_t nc = (budget - tile_b) / per_member;
+  return (int)std::min<size_t>(nc, (size_t)std::min(N, 256));
+}
+
 // Launch with TMA member staging when the members allow it (W % 4 == 0, a
 // 16-byte aligned base) and a box of at least one member fits next to the
 // parameter tile at the model's occupancy; returns false to fall back.
-template <int MODEL, bool SADDLE>
+template <int MODEL, bool SADDLE, int TYm>
 static bool launch_tile_tma(const Field &f, int tiles_x, int tiles, cudaStream_t s,
                             cudaError_t *err) {
-  constexpr int TYm = TileH<MODEL>::value;
   if (f.W % 4 != 0 || (reinterpret_cast<uintptr_t>(f.ens) & 15) != 0) return false;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
   const size_t tile_b = (size_t)((tile_floats(MODEL, f.B, TYm) + 1) & ~1LL) * sizeof(float) + 16;
   const size_t per_member = (size_t)(TYm + 2) * kBoxW * sizeof(float);
   const size_t budget = (size_t)227 * 1024 / TileOcc<MODEL>::value - 1024;
-  if (budget < tile_b + per_member) return false;
-  int nc = (int)((budget - tile_b) / per_member);
-  if (nc > f.N) nc = f.N;
-  if (nc > 256) nc = 256;
+  const int nc = tma_box_members<MODEL, TYm>(f.N, f.B);
+  if (nc < 1) return false;
+  // histogram per-bin rows, in the room of the member box
+  constexpr bool ROWS = HistRows<MODEL, TYm>::value;
+  const size_t r4_b = ROWS ? (size_t)r4_floats(f.B, TYm) * sizeof(float) : 0;
+  if (tile_b + r4_b > budget) return false;
   CUtensorMap map;
   const cuuint64_t dims[3] = {(cuuint64_t)f.W, (cuuint64_t)f.H, (cuuint64_t)f.N};
   const cuuint64_t strides[2] = {(cuuint64_t)f.W * sizeof(float),
@@ -209,7 +252,7 @@ static bool launch_tile_tma(const Field &f, int tiles_x, int tiles, cudaStream_t
     return false;
   }
   if (!attr_set[dev]) {
-    if (cudaFuncSetAttribute(tile_kernel_tma<MODEL, SADDLE>,
+    if (cudaFuncSetAttribute(tile_kernel_tma<MODEL, SADDLE, TYm>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
         cudaSuccess) {
       cudaGetLastError();
@@ -219,16 +262,19 @@ static bool launch_tile_tma(const Field &f, int tiles_x, int tiles, cudaStream_t
   }
   Field g = f;
   g.tma_nc = nc;
-  const size_t smem = (size_t)nc * per_member + tile_b;
-  tile_kernel_tma<MODEL, SADDLE><<<tiles, NTHREADS, smem, s>>>(g, tiles_x, map);
+  const size_t smem = std::max((size_t)nc * per_member, r4_b) + tile_b;
+  tile_kernel_tma<MODEL, SADDLE, TYm><<<tiles, NTHREADS, smem, s>>>(g, tiles_x, map);
   *err = cudaGetLastError();
   return true;
 }
 
-template <int MODEL, bool FM, bool SADDLE>
-static cudaError_t launch_tile(const Field &f, cudaStream_t s) {
-  constexpr int TYm = TileH<MODEL>::value;
-  const size_t smem = (size_t)tile_floats(MODEL, f.B, TYm) * sizeof(float);
+template <int MODEL, bool FM, bool SADDLE, int TYm>
+static cudaError_t launch_tile_h(const Field &f, cudaStream_t s) {
+  size_t smem = (size_t)tile_floats(MODEL, f.B, TYm) * sizeof(float);
+  // histogram per-bin rows after the tile (launch_tile checked that they fit)
+  if constexpr (HistRows<MODEL, TYm>::value)
+    smem = (size_t)((tile_floats(MODEL, f.B, TYm) + 3) & ~3LL) * sizeof(float) +
+           (size_t)r4_floats(f.B, TYm) * sizeof(float);
   static bool attr_set[128] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -237,10 +283,11 @@ static cudaError_t launch_tile(const Field &f, cudaStream_t s) {
   if (!attr_set[dev]) {
     // the largest tile of this model (64 bins; the histogram adds its tail
     // table, total, status and ordering scratch, the estimator its running
-    // mass sums): 169 KB at 18 x 34, 173 KB at 10 x 34
-    e = cudaFuncSetAttribute(tile_kernel<MODEL, FM, SADDLE>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)((size_t)tile_floats(MODEL, kMaxBins, TYm) * sizeof(float)));
+    // mass sums: 95 KB and 173 KB at 10 x 34), or the per-bin rows' bound
+    const size_t most = std::max((size_t)tile_floats(MODEL, kMaxBins, TYm) * sizeof(float),
+                                 MODEL == kHist ? (size_t)227 * 1024 / TileOcc<MODEL>::value : 0);
+    e = cudaFuncSetAttribute(tile_kernel<MODEL, FM, SADDLE, TYm>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
     if (e != cudaSuccess) {
       cudaGetLastError();  // do not leave the failed call as the last error
       return e;
@@ -255,10 +302,25 @@ static cudaError_t launch_tile(const Field &f, cudaStream_t s) {
   if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
   if constexpr (FM) {
     cudaError_t te = cudaSuccess;
-    if (launch_tile_tma<MODEL, SADDLE>(g, tiles_x, (int)tiles, s, &te)) return te;
+    if (launch_tile_tma<MODEL, SADDLE, TYm>(g, tiles_x, (int)tiles, s, &te)) return te;
   }
-  tile_kernel<MODEL, FM, SADDLE><<<(int)tiles, NTHREADS, smem, s>>>(g, tiles_x);
+  tile_kernel<MODEL, FM, SADDLE, TYm><<<(int)tiles, NTHREADS, smem, s>>>(g, tiles_x);
   return cudaGetLastError();
+}
+
+template <int MODEL, bool FM, bool SADDLE>
+static cudaError_t launch_tile(const Field &f, cudaStream_t s) {
+  if constexpr (MODEL == kEpan && FM) {
+    if (f.N <= tma_box_members<kEpan, 8>(f.N, f.B)) return launch_tile_h<MODEL, FM, SADDLE, 8>(f, s);
+  }
+  if constexpr (MODEL == kHist) {
+    // without the per-bin rows (more bins than fit) the smaller halo wins
+    const size_t rows_end = (size_t)((tile_floats(kHist, f.B, 8) + 3) & ~3LL) * sizeof(float) +
+                            (size_t)r4_floats(f.B, 8) * sizeof(float) + 16;
+    if (rows_end > (size_t)227 * 1024 / TileOcc<kHist>::value - 1024)
+      return launch_tile_h<MODEL, FM, SADDLE, TY>(f, s);
+  }
+  return launch_tile_h<MODEL, FM, SADDLE, TileH<MODEL>::value>(f, s);
 }
 
 template <bool SADDLE>

@@ -1274,6 +1274,137 @@ __device__ __forceinline__ void hist_walk(const float *S0, int coff, int B, floa
   pmax = fmaxf(acc.y, 0.f);
 }
 
+// Per-bin rows of a staged histogram vertex for the forward walk: float4
+// rows at R[k * WS + l], k = 0..B+1.  Row k < B describes bin k: (S_k,
+// T - S_k, slope_k, e_{k+1} - lo), with the tail S_k = T - (m_0 + ... +
+// m_{k-1}), slope_k = (S_k - S_{k+1}) / h (the bin's density, m_k / h, in
+// the mixture form) and e_{k+1} - lo = (k + 1) h (hi - lo for the last edge).
+// Row B is (0, T, 0, kFar), beyond the support, and row B + 1 repeats it so
+// that the walkers' unconditional reads one row past their last crossing
+// stay inside the table.  A point mass has row 0 = (0, T, 0, kFar): its one
+// edge takes the survival from T to 0.
+__host__ __device__ constexpr int hist_r4_rows(int B) { return B + 2; }
+
+// A neighbour's survival G and CDF F walked bin by bin over the per-bin rows:
+// before the support (G, F) = (T, 0); on bin k G(x) = S_k - slope_k (x - e_k)
+// and F(x) = T - S_k + slope_k (x - e_k); beyond it (0, T).  Crossing an edge
+// loads the next row, which also holds the edge after it, so a step needs no
+// edge arithmetic.  An absent neighbour is the constant (1, 1) that never
+// reaches an edge.
+struct HistRowWalker {
+  int addr;                 // float4 index of the row read at the next crossing
+  float lam;                // support start in the centre's frame
+  float el, nx, s, c, sl;   // segment start, next edge, G and F at el, slope
+  __device__ __forceinline__ void init_absent(int any_row) {
+    addr = any_row; lam = 0.f;
+    el = -kFar; nx = kFar; s = c = 1.f; sl = 0.f;
+  }
+  __device__ __forceinline__ void init(int row0, float lam_, float T) {
+    addr = row0; lam = lam_;
+    el = -kFar; nx = lam_; s = T; c = 0.f; sl = 0.f;
+  }
+  // One merge step at x1: cross the next edge if it is at or below x1.  No
+  // branch; the read always has a valid address (see hist_r4_rows).
+  template <int WS>
+  __device__ __forceinline__ bool step(const float4 *R, float x1) {
+    const bool cr = nx <= x1;
+    const float4 t = R[addr];
+    s = cr ? t.x : s;
+    c = cr ? t.y : c;
+    sl = cr ? t.z : sl;
+    nx = cr ? lam + t.w : nx;
+    el = cr ? x1 : el;
+    addr += cr ? WS : 0;
+    return cr;
+  }
+  __device__ __forceinline__ float G(float x) const { return fmaf(-sl, x - el, s); }
+  __device__ __forceinline__ float F(float x) const { return fmaf(sl, x - el, c); }
+  // From the initial state, cross every edge at or below 0 at once (the
+  // state step() would reach edge by edge; the count of such edges comes
+  // from -lam / h and is checked against the edges of the rows).
+  template <int WS>
+  __device__ __forceinline__ void seek0(const float4 *R, int B, float h) {
+    if (nx > 0.f) return;  // the first edge is above 0 (also: absent)
+    const int row0 = addr;
+    int j = 1;             // edges e_0 .. e_{j-1} are at or below 0
+    if (h > 0.f) {
+      auto edge = [&](int i) { return i == 0 ? lam : lam + R[row0 + (i - 1) * WS].w; };
+      j = (int)fminf(fmaxf(floorf(-lam * frcp(h)), 0.f), (float)B) + 1;
+      if (j <= B && edge(j) <= 0.f) ++j;
+      if (j >= 2 && edge(j - 1) > 0.f) --j;
+      el = edge(j - 1);
+    } else {
+      el = lam;            // a point mass: its one edge
+    }
+    const float4 t = R[row0 + (j - 1) * WS];
+    s = t.x;
+    c = t.y;
+    sl = t.z;
+    nx = lam + t.w;
+    addr = row0 + j * WS;
+  }
+};
+
+// hist_walk over the per-bin rows (centre rows from crow): the same merge of
+// the bin edges of the centre and the four neighbours in increasing order,
+// the same Bernstein mean per piece; the crossings load rows instead of
+// computing tails, slopes and edges.
+template <int WS, bool SADDLE = false>
+__device__ __forceinline__ void hist_walk_rows(const float4 *R, int crow, int B, float W1,
+                                               HistRowWalker *nw, float &pmin, float &pmax,
+                                               const int *sg = nullptr) {
+  if (!(W1 <= 1e38f)) {
+    pmin = pmax = __int_as_float(0x7fc00000);
+    return;
+  }
+  // the centre needs only the density and the next edge of its bin: the
+  // (z, w) half of each row
+  const float2 *R2 = reinterpret_cast<const float2 *>(R);
+  int addr_c = crow + WS;
+  float dens, nxc;
+  {
+    const float2 t = R2[2 * crow + 1];
+    dens = t.x;
+    nxc = t.y;
+  }
+  auto pair = [&](int i, float g, float f) {
+    if constexpr (SADDLE) return sg[i] > 0 ? make_float2(g, f) : make_float2(f, g);
+    else return make_float2(g, f);
+  };
+  float2 Pl[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) Pl[i] = pair(i, nw[i].G(0.f), nw[i].F(0.f));
+  float2 acc = make_float2(0.f, 0.f);
+  float x0 = 0.f;
+  const int max_steps = 5 * (B + 2) + 4;
+  for (int step = 0; step < max_steps && x0 < W1; ++step) {
+    float x1 = fminf(fminf(nw[0].nx, nw[1].nx), fminf(nw[2].nx, nw[3].nx));
+    x1 = fmaxf(fminf(x1, nxc), x0);
+    float2 Pr[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) Pr[i] = pair(i, nw[i].G(x1), nw[i].F(x1));
+    const float wgt = (x1 - x0) * dens;
+    acc = __ffma2_rn(make_float2(wgt, wgt), bern_mean4_x2(Pl, Pr), acc);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      // the left values of the next piece: the new segment's at x1 (the
+      // right values, except after a point mass)
+      const bool cr = nw[i].step<WS>(R, x1);
+      Pl[i] = cr ? pair(i, nw[i].s, nw[i].c) : Pr[i];
+    }
+    {
+      const bool cr = nxc <= x1;
+      const float2 t = R2[2 * addr_c + 1];
+      dens = cr ? t.x : dens;
+      nxc = cr ? t.y : nxc;
+      addr_c += cr ? WS : 0;
+    }
+    x0 = x1;
+  }
+  pmin = fmaxf(acc.x, 0.f);
+  pmax = fmaxf(acc.y, 0.f);
+}
+
 // survival and CDF of a histogram neighbour (tail table S, total T) at a
 // point v (degenerate centre)
 __device__ __forceinline__ void hist_tails_at(const float *S, int ws, int B, float lo, float hi,
@@ -1295,6 +1426,32 @@ __device__ __forceinline__ void hist_tails_at(const float *S, int ws, int B, flo
   const int j = min(max((int)floorf((v - lo) / h), 0), B - 1);
   const float fr = fminf(fmaxf((v - lo - (float)j * h) / h, 0.f), 1.f);
   const float sj = S[j * ws], sj1 = S[(j + 1) * ws];
+  gt = fmaxf(fmaf(-fr, sj - sj1, sj), 0.f);
+  lt = fmaxf(T - gt, 0.f);
+}
+
+// hist_tails_at with the tails read from per-bin rows (R at the vertex's
+// row 0, rows ws apart)
+__device__ __forceinline__ void hist_tails_at_rows(const float4 *R, int ws, int B, float lo,
+                                                   float hi, float T, float v, float &gt,
+                                                   float &lt) {
+  if (lo == hi) {
+    gt = lo > v ? T : 0.f;
+    lt = lo < v ? T : 0.f;
+    return;
+  }
+  if (v <= lo) {
+    gt = T; lt = 0.f;
+    return;
+  }
+  if (v >= hi) {
+    gt = 0.f; lt = T;
+    return;
+  }
+  const float h = (hi - lo) / (float)B;
+  const int j = min(max((int)floorf((v - lo) / h), 0), B - 1);
+  const float fr = fminf(fmaxf((v - lo - (float)j * h) / h, 0.f), 1.f);
+  const float sj = R[j * ws].x, sj1 = R[(j + 1) * ws].x;
   gt = fmaxf(fmaf(-fr, sj - sj1, sj), 0.f);
   lt = fmaxf(T - gt, 0.f);
 }

@@ -317,6 +317,42 @@ __device__ __forceinline__ void hist_tail_table(float *sm, int l, int B) {
   sm[(5 + B) * HALO + l] = (float)st;
 }
 
+// Per-bin rows (hist_r4_rows) of staged vertex l straight from its masses,
+// with its total and status in rows 4 + B and 5 + B as hist_tail_table
+// writes them (the row walk reads its tails from the rows, so the tail rows
+// of the parameter tile are not written; the masses stay there).  The tails
+// S_k = T - (m_0 + ... + m_{k-1}) are formed as hist_tail_table forms them.
+template <int HALO>
+__device__ __forceinline__ void hist_row_table(float *sm, float4 *R, int l, int B) {
+  const float a = sm[l], b = sm[HALO + l];
+  uint8_t st = (!isfinite(a) || !isfinite(b)) ? V_NONFINITE
+                                             : (a > b ? V_BAD : (a == b ? V_DEGENERATE : 0));
+  float t = 0.f;
+  for (int q = 0; q < B; ++q) {
+    const float w = sm[(2 + q) * HALO + l];
+    if (!isfinite(w)) st |= V_NONFINITE;
+    else if (w < 0.f) st |= V_BAD;
+    t += w;
+  }
+  sm[(4 + B) * HALO + l] = t;
+  sm[(5 + B) * HALO + l] = (float)st;
+  const float4 beyond = make_float4(0.f, t, 0.f, kFar);
+  if (a == b) {
+    for (int k = 0; k < hist_r4_rows(B); ++k) R[k * HALO + l] = beyond;
+    return;
+  }
+  const float h = (b - a) / (float)B, ih = frcp(h), w = b - a;
+  float c = 0.f, sk = t;
+  for (int k = 0; k < B; ++k) {
+    c += sm[(2 + k) * HALO + l];
+    const float sn = k + 1 < B ? t - c : 0.f;
+    R[k * HALO + l] = make_float4(sk, t - sk, (sk - sn) * ih, k + 1 < B ? (float)(k + 1) * h : w);
+    sk = sn;
+  }
+  R[B * HALO + l] = beyond;
+  R[(B + 1) * HALO + l] = beyond;
+}
+
 // ---------------------------------------------------------------------------
 // Member staging with the tensor memory accelerator: one bulk tensor copy
 // brings a box of nc members x (TYv + 2) rows x 40 columns (x from tx0 - 4, a
@@ -372,10 +408,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
 // Statistics of the members of every in-grid halo vertex into the shared
 // parameter tile, as stage_members computes them (same arithmetic in the same
 // member order).  Returns false if a wait gave up (the tile is then invalid).
-template <int MODEL, int TYv>
+// ROWS: histogram per-bin rows into R4 in place of the tail tables (R4 may
+// overlap the box: the rows are written after the barrier that ends the last
+// read of the box).
+template <int MODEL, int TYv, bool ROWS>
 __device__ __forceinline__ bool stage_members_tma(const Field &f, float *sm, float *box,
                                                   uint64_t *bar, const CUtensorMap *tmap,
-                                                  int ty0, int tx0) {
+                                                  int ty0, int tx0, float4 *R4) {
   constexpr int HY = TYv + 2, HX = 34, HALO = HY * HX;
   constexpr int PER = (HALO + NTHREADS - 1) / NTHREADS;
   constexpr int PLANE = HY * kBoxW;
@@ -521,10 +560,13 @@ __device__ __forceinline__ bool stage_members_tma(const Field &f, float *sm, flo
           *w = __fdiv_rn(*w, (float)N);
         }
     if constexpr (MODEL == kHist) {
-      // the owner also builds the vertex's tail table
+      // the owner also builds the vertex's tail table (or per-bin rows)
 #pragma unroll
       for (int p = 0; p < PER; ++p)
-        if (in[p]) hist_tail_table<HALO>(sm, lv[p], B);
+        if (in[p]) {
+          if constexpr (ROWS) hist_row_table<HALO>(sm, R4, lv[p], B);
+          else hist_tail_table<HALO>(sm, lv[p], B);
+        }
     }
   }
   return true;
@@ -556,24 +598,52 @@ __device__ __forceinline__ uint8_t check_params(const float *sm, int l, int B, f
   return st;
 }
 
+// NaN and the timeout flag for every vertex of a tile whose staging gave up
+// (a bounded wait expired)
+template <int TYv, bool SADDLE>
+__device__ __forceinline__ void mark_tile_timeout(const Field &f, int ty0, int tx0) {
+  constexpr int TX = 32;
+  for (int v = threadIdx.x; v < TYv * TX; v += NTHREADS) {
+    const int gy = ty0 + v / TX, gx = tx0 + v % TX;
+    if (gy >= f.y1 || gx >= f.W) continue;
+    const long long gi = (long long)gy * f.W + gx;
+    if constexpr (SADDLE) {
+      if (f.out_saddle) f.out_saddle[gi] = qnan();
+    } else {
+      if ((f.cptypes & kMin) && f.out_min) f.out_min[gi] = qnan();
+      if ((f.cptypes & kMax) && f.out_max) f.out_max[gi] = qnan();
+    }
+    if (f.status) f.status[gi] = V_TIMEOUT;
+  }
+}
+
+template <int MODEL, int TYv, bool SADDLE, bool TABLES_BUILT, bool ROWS>
+__device__ __forceinline__ void integrate_tile(const Field &f, int ty0, int tx0, float *sm,
+                                               float4 *R4);
+
 // One tile of TYv x 32 vertices: phase 1 stages the parameters of the tile
 // and its one-vertex halo ((TYv + 2) x 34) in shared memory -- fitted from the
-// members or loaded -- and phase 2 integrates every vertex of the tile.
-// SADDLE selects the saddle probability (Eq. saddleProb) instead of the
-// minimum / maximum: a separate instance, so neither pays for the other.
-// TMA: the members are staged through the tensor map tmap into `box`, with
-// the mbarrier `bar` (FROM_MEMBERS only).
-template <int MODEL, bool FROM_MEMBERS, int TYv, bool SADDLE = false, bool TMA = false>
+// members or loaded -- and phase 2 (integrate_tile) integrates every vertex
+// of the tile.  SADDLE selects the saddle probability (Eq. saddleProb)
+// instead of the minimum / maximum: a separate instance, so neither pays for
+// the other.  TMA: the members are staged through the tensor map tmap into
+// `box`, with the mbarrier `bar` (FROM_MEMBERS only).  ROWS (histograms):
+// the walk runs over per-bin rows in R4 (hist_r4_rows x halo float4, 16-byte
+// aligned; it may overlap `box`) instead of the segment walker's tail table;
+// each kernel instance carries one of the two walks.
+template <int MODEL, bool FROM_MEMBERS, int TYv, bool SADDLE = false, bool TMA = false,
+          bool ROWS = false>
 __device__ __forceinline__ void process_tile(const Field &f, int ty0, int tx0, float *sm,
                                              const CUtensorMap *tmap = nullptr,
-                                             float *box = nullptr, uint64_t *bar = nullptr) {
+                                             float *box = nullptr, uint64_t *bar = nullptr,
+                                             float4 *R4 = nullptr) {
   constexpr int TY = TYv, TX = 32, HY = TYv + 2, HX = TX + 2, HALO = HY * HX;
   // rows beyond y1 are neither computed nor needed (row y1 is a neighbour)
   const int ylim = min(f.H, f.y1 + 1);
 
   bool staged = true;
   if constexpr (FROM_MEMBERS && TMA) {
-    staged = stage_members_tma<MODEL, TY>(f, sm, box, bar, tmap, ty0, tx0);
+    staged = stage_members_tma<MODEL, TY, ROWS>(f, sm, box, bar, tmap, ty0, tx0, R4);
   } else if (FROM_MEMBERS) {
     // work items per halo row: the two halo columns (scalar) and eight
     // groups of four interior columns (one float4 per member when aligned)
@@ -605,23 +675,28 @@ __device__ __forceinline__ void process_tile(const Field &f, int ty0, int tx0, f
   }
   __syncthreads();
   if (!staged) {  // a bounded wait gave up (uniform over the CTA): NaN + flag
-    for (int v = threadIdx.x; v < TY * TX; v += NTHREADS) {
-      const int gy = ty0 + v / TX, gx = tx0 + v % TX;
-      if (gy >= f.y1 || gx >= f.W) continue;
-      const long long gi = (long long)gy * f.W + gx;
-      if constexpr (SADDLE) {
-        if (f.out_saddle) f.out_saddle[gi] = qnan();
-      } else {
-        if ((f.cptypes & kMin) && f.out_min) f.out_min[gi] = qnan();
-        if ((f.cptypes & kMax) && f.out_max) f.out_max[gi] = qnan();
-      }
-      if (f.status) f.status[gi] = V_TIMEOUT;
-    }
+    mark_tile_timeout<TY, SADDLE>(f, ty0, tx0);
     return;
   }
-  if constexpr (MODEL == kHist && !(FROM_MEMBERS && TMA)) {
-    // tail tables of every staged vertex (the TMA staging builds them itself)
-    for (int l = threadIdx.x; l < HALO; l += NTHREADS) hist_tail_table<HALO>(sm, l, f.B);
+  integrate_tile<MODEL, TY, SADDLE, FROM_MEMBERS && TMA, ROWS>(f, ty0, tx0, sm, R4);
+}
+
+// Phase 2 of a tile whose parameters (and, if TABLES_BUILT, histogram tail
+// tables or per-bin rows) are staged in shared memory: every vertex of the
+// tile integrated.
+template <int MODEL, int TYv, bool SADDLE, bool TABLES_BUILT, bool ROWS>
+__device__ __forceinline__ void integrate_tile(const Field &f, int ty0, int tx0, float *sm,
+                                               float4 *R4) {
+  constexpr int TY = TYv, TX = 32, HY = TYv + 2, HX = TX + 2, HALO = HY * HX;
+  (void)HY;
+  (void)R4;
+  if constexpr (MODEL == kHist && !TABLES_BUILT) {
+    // tail tables or rows of every staged vertex (the TMA staging builds
+    // them itself)
+    for (int l = threadIdx.x; l < HALO; l += NTHREADS) {
+      if constexpr (ROWS) hist_row_table<HALO>(sm, R4, l, f.B);
+      else hist_tail_table<HALO>(sm, l, f.B);
+    }
     __syncthreads();
   }
   if constexpr (MODEL == kSemi) {
@@ -635,7 +710,6 @@ __device__ __forceinline__ void process_tile(const Field &f, int ty0, int tx0, f
     }
     __syncthreads();
   }
-
   [[maybe_unused]] const unsigned short *order = nullptr;
   if constexpr (MODEL == kHist) order = hist_order<TY, HALO>(f, sm, ty0, tx0);
 
@@ -739,8 +813,12 @@ __device__ __forceinline__ void process_tile(const Field &f, int ty0, int tx0, f
         for (int i = 0; i < 4; ++i) {
           if (!present[i]) continue;
           float gt, lt;
-          hist_tails_at(sm + 2 * HALO + nl[i], HALO, B, sm[nl[i]], sm[HALO + nl[i]], T[i], lo1,
-                        gt, lt);
+          if constexpr (ROWS)
+            hist_tails_at_rows(R4 + nl[i], HALO, B, sm[nl[i]], sm[HALO + nl[i]], T[i], lo1, gt,
+                               lt);
+          else
+            hist_tails_at(sm + 2 * HALO + nl[i], HALO, B, sm[nl[i]], sm[HALO + nl[i]], T[i], lo1,
+                          gt, lt);
           gm *= gt;
           gM *= lt;
           if (sg[i] != 0) {
@@ -753,7 +831,27 @@ __device__ __forceinline__ void process_tile(const Field &f, int ty0, int tx0, f
           pmax = gM;
         }
         if (do_sad) psad = t1 + t2;
-      } else if (do_mm || do_sad) {
+      } else if ((do_mm || do_sad) && ROWS) {
+        HistRowWalker nw[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          HistRowWalker &h = nw[i];
+          if (!present[i]) {
+            h.init_absent(l);
+            continue;
+          }
+          const float lo = sm[nl[i]], hi = sm[HALO + nl[i]];
+          h.init(nl[i], lo - lo1, T[i]);
+          h.seek0<HALO>(R4, B, lo == hi ? 0.f : (hi - lo) / (float)B);
+        }
+        if constexpr (!SADDLE) {
+          hist_walk_rows<HALO>(R4, l, B, hi1 - lo1, nw, pmin, pmax);
+        } else {
+          float t1, t2;
+          hist_walk_rows<HALO, true>(R4, l, B, hi1 - lo1, nw, t1, t2, sg);
+          psad = t1 + t2;
+        }
+      } else if ((do_mm || do_sad) && !ROWS) {
         const float *S0 = sm + 2 * HALO;
         HistSeg nw[4];
         float Tw[4];

@@ -1,6 +1,9 @@
 """Batched persistent launch (ucp_batch_*): the same probabilities as the
-per-field launches (bit-identical: the same tile body per vertex), under CUDA
-graph capture and replay, after autotuning; spot checks against the oracle."""
+per-field launches, under CUDA graph capture and replay, after autotuning;
+spot checks against the oracle.  Bit-identical (the same tile body per
+vertex) except for histograms of at most 8 bins: the per-field kernels walk
+their per-bin row tables, the batch kernel the segment walker, which round
+differently (each within 1e-5 of the oracle); those agree to 1e-6."""
 import os
 
 import numpy as np
@@ -55,14 +58,21 @@ def _reference(ctx, fields):
     return refs
 
 
+def _same(desc, out, ref):
+    if desc.model == 2 and desc.bins <= 8:
+        assert (out - ref).abs().max().item() <= 1e-6
+    else:
+        assert torch.equal(out, ref)
+
+
 def _check(fields, refs):
     for (ens, desc, cp, (omin, omax)), (rmin, rmax) in zip(fields, refs):
         if cp & 1:
-            assert torch.equal(omin, rmin)
+            _same(desc, omin, rmin)
         else:
             assert (omin == -1).all()
         if cp & 2:
-            assert torch.equal(omax, rmax)
+            _same(desc, omax, rmax)
         else:
             assert (omax == -1).all()
 

@@ -226,3 +226,35 @@ def test_api_errors(ucp, ctx):
         ctx.backward(torch.zeros((20, 4, 5), device="cuda"), ucp.make_desc("mvn"), 1,
                      torch.zeros((4, 5), device="cuda"))
     assert e.value.status == ucp.UCP_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("bins", [1, 2, 3, 5, 8, 9, 16])
+def test_histogram_bin_counts(ucp, ctx, orc, bins):
+    """Histogram walks across bin counts -- the per-bin row tables (up to 8
+    bins) and the segment walker (more) -- from members, and from parameters
+    with a point-mass centre and neighbour, supports far below, far above and
+    far away from their neighbours, and identical neighbours: minimum, maximum
+    and saddle against the oracle."""
+    from paper_2407_18015_gb300 import synth
+    ens_np = synth.ensemble_bimodal(37, 70, 20, seed=900 + bins, lam_scale=0.3)
+    _run_field(ucp, ctx, orc, ens_np, "histogram", bins)
+    rng = np.random.default_rng(50 + bins)
+    p = H_.random_params(2, 19, 37, rng, bins=bins)
+    p[1, 5, 5] = p[0, 5, 5]                          # point-mass centre
+    p[1, 5, 8] = p[0, 5, 8] = p[0, 5, 9]             # point mass at a neighbour's edge
+    p[:2, 8, 8] -= 5.0                               # far below its neighbours
+    p[:2, 10, 10] += 5.0                             # far above
+    p[:2, 12, 12] += 1.0e6                           # far away
+    p[:, 14, 14] = p[:, 14, 15]                      # identical neighbours
+    p32 = p.astype(np.float32)
+    desc = ucp.make_desc("histogram", bins=bins)
+    pmin, pmax, st = ctx.probability_from_params(_dev(p32), desc)
+    sad, _ = ctx.saddle_from_params(_dev(p32), desc)
+    torch.cuda.synchronize()
+    p64 = p32.astype(np.float64)
+    rmin, rmax, rst = orc.prob(p64, 2, bins=bins)
+    rsad, _ = orc.saddle(p64, 2, bins=bins)
+    _compare(pmin, rmin, what="min")
+    _compare(pmax, rmax, what="max")
+    _compare(sad, rsad, what="saddle")
+    np.testing.assert_array_equal(st.cpu().numpy(), rst)
