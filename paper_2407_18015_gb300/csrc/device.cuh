@@ -1239,6 +1239,7 @@ __device__ __forceinline__ void hist_walk(const float *S0, int coff, int B, floa
   float2 acc = make_float2(0.f, 0.f);
   float x0 = 0.f;
   const int max_steps = 5 * (B + 2) + 4;
+#pragma unroll 2
   for (int step = 0; step < max_steps && x0 < W1; ++step) {
     float x1 = fminf(fminf(nw[0].nx, nw[1].nx), fminf(nw[2].nx, nw[3].nx));
     x1 = fmaxf(fminf(x1, nxc), x0);
@@ -1377,6 +1378,7 @@ __device__ __forceinline__ void hist_walk_rows(const float4 *R, int crow, int B,
   float2 acc = make_float2(0.f, 0.f);
   float x0 = 0.f;
   const int max_steps = 5 * (B + 2) + 4;
+#pragma unroll 2
   for (int step = 0; step < max_steps && x0 < W1; ++step) {
     float x1 = fminf(fminf(nw[0].nx, nw[1].nx), fminf(nw[2].nx, nw[3].nx));
     x1 = fmaxf(fminf(x1, nxc), x0);

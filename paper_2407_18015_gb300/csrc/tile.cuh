@@ -711,11 +711,13 @@ __device__ __forceinline__ void integrate_tile(const Field &f, int ty0, int tx0,
     __syncthreads();
   }
   [[maybe_unused]] const unsigned short *order = nullptr;
-  if constexpr (MODEL == kHist) order = hist_order<TY, HALO>(f, sm, ty0, tx0);
+  // the segment walker's lanes take walks of about equal length (an 8-row
+  // tile of per-bin row walks gains nothing from the ordering)
+  if constexpr (MODEL == kHist && !ROWS) order = hist_order<TY, HALO>(f, sm, ty0, tx0);
 
   for (int it = threadIdx.x; it < TY * TX; it += NTHREADS) {
     int v = it;
-    if constexpr (MODEL == kHist) {
+    if constexpr (MODEL == kHist && !ROWS) {
       // pass j of warp w takes the j-th group of eight 32-vertex blocks of
       // the ordered list, in reverse on odd passes, so that every warp gets
       // about the same total length
