@@ -166,9 +166,9 @@ EPAN_FLOPS_PER_VERTEX_TYPE = 5 * 8 * 35
 # DRAM bytes (read + write) per launch of each headline kernel from the ncu
 # capture summarised in profiles/; None once a kernel has changed since its
 # counters were taken
-TRAFFIC_BYTES = {"uniform": 83.927296e6 + 4.302848e6,
-                 "epanechnikov": 83.982336e6 + 3.933952e6,
-                 "histogram": 83.972864e6 + 4.717824e6}
+TRAFFIC_BYTES = {"uniform": 83.926016e6 + 5.108992e6,
+                 "epanechnikov": 83.945984e6 + 4.817920e6,
+                 "histogram": 83.961088e6 + 4.936192e6}
 
 
 def work_of(model, N, HW, params=None, bins=BINS2):
