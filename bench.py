@@ -73,6 +73,12 @@ def fp32_peak_tflops(mhz):
     return SM_COUNT * FP32_LANES * 2 * mhz * 1e6 / 1e12
 
 
+def issue_peak_tops(mhz):
+    """Instruction issue: 152 SMs x 4 schedulers x 32 lanes, one operation
+    per lane per clock."""
+    return SM_COUNT * FP32_LANES * mhz * 1e6 / 1e12
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 
@@ -161,6 +167,14 @@ def hist_piece_counts(params, bins):
 # exactly from the data (hist_piece_counts).
 HIST_FLOPS_PER_PIECE_TYPE = 3 * 25
 EPAN_FLOPS_PER_VERTEX_TYPE = 5 * 8 * 35
+# Monte Carlo: per sample two Philox4x32-10 blocks (~200 integer operations),
+# three Box-Muller transforms, 14 FMA for L z and 4 comparisons, ~250 lane
+# operations, against the issue rate (one operation per lane per clock).
+MVN_OPS_PER_SAMPLE = 250
+# Histogram adjoint of P_min: on every merged piece the centre's product
+# integral and one leave-one-out product integral per neighbour, each counted
+# as a forward piece integral.
+ADJ_HIST_FLOPS_PER_PIECE = 5 * HIST_FLOPS_PER_PIECE_TYPE
 
 
 # DRAM bytes (read + write) per launch of each headline kernel from the ncu
@@ -472,9 +486,14 @@ def other_rows(torch, ucp, ctx, dev, args, flush, peaks):
                             steps, 2, flush)
         ms /= steps
         samples = 512 * 512 * 10000
+        ach = samples * MVN_OPS_PER_SAMPLE / (ms / 1e3) / 1e12
+        pk = issue_peak_tops(peaks["sm_max_mhz"])
         rows["mvn_512x512x40_S10000"] = {
             "ms": ms, "vertices_per_s": 512 * 512 / (ms / 1e3),
             "samples_per_s": samples / (ms / 1e3), "min_and_max": True,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": pk, "unit": "Tops/s",
+                         "frac": ach / pk, "work": f"{MVN_OPS_PER_SAMPLE} lane operations per sample",
+                         "peak_source": f"152 SMs x 128 lanes x 1 op x {peaks['sm_max_mhz']:.0f} MHz"},
             "oracle": oracle_mvn_rate(e3.cpu().numpy())}
         del e3
     if "fwdbwd" in want:
@@ -494,14 +513,27 @@ def other_rows(torch, ucp, ctx, dev, args, flush, peaks):
 
             def fw(ev, d=d, pmin=pmin):
                 ucp.ucp_probability(ctx.handle, e4, d, ucp.UCP_MIN, pmin, None)
+            def bw(ev, d=d, params=params, grad=grad):
+                ucp.ucp_backward(ctx.handle, params, d, ucp.UCP_MIN, Wt, grad)
             ms_fb, _ = timed_steps(torch, fb, steps, 2, flush)
             ms_fw, _ = timed_steps(torch, fw, steps, 2, flush)
-            rows[f"fwd_bwd_2048x2048x50_{m}{b or ''}"] = {
+            ms_bw, _ = timed_steps(torch, bw, steps, 2, flush)
+            row = {
                 "ms_fwd_bwd": ms_fb / steps,
                 "fwd_bwd_vertices_per_s": 2048 * 2048 / (ms_fb / steps / 1e3),
                 "ms_fwd": ms_fw / steps,
                 "fwd_vertices_per_s": 2048 * 2048 / (ms_fw / steps / 1e3),
+                "ms_adjoint": ms_bw / steps,
                 "oracle": oracle_fwd_bwd_rate(e4, Wt, m, b)}
+            if m == "histogram":
+                pieces = float(hist_piece_counts(params, b).sum().item())
+                ach = pieces * ADJ_HIST_FLOPS_PER_PIECE / (ms_bw / steps / 1e3) / 1e12
+                pk = fp32_peak_tflops(peaks["sm_max_mhz"])
+                row["adjoint_roofline"] = {
+                    "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                    "frac": ach / pk, "work": f"{ADJ_HIST_FLOPS_PER_PIECE} flops per merged piece",
+                    "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz"}
+            rows[f"fwd_bwd_2048x2048x50_{m}{b or ''}"] = row
             del params, grad
         del e4
     if "batch" in want:
