@@ -246,6 +246,25 @@ int ucp_probability_host(ucp_ctx *ctx, const float *ens_host, int N, int H, int 
                          const ucp_model_desc *desc, unsigned cptypes, float *out_min_host,
                          float *out_max_host, uint8_t *status_host, ucp_stream stream);
 
+/* Several models of one ensemble with HOST arrays (the paper compares its
+ * models on the same ensemble, Sec. "Comparison of Parametric Vs.
+ * Nonparametric Models"): the members are copied to the device once, in row
+ * strips whose copies overlap the computation of the previous strip (every
+ * model) and the read-back of the one before; synchronises the stream before
+ * returning.  descs[0..nmodels-1], 1 <= nmodels <= UCP_MAX_HOST_MODELS, none
+ * with a larger stencil (UCP_ERR_UNSUPPORTED); cptypes applies to every
+ * model.  out_min_host[m] / out_max_host[m]: [H][W] host arrays of model m
+ * for the types in cptypes; an entry may be NULL, and that field of that
+ * model is then not copied back (the pointer arrays themselves must not be
+ * NULL).  status_host may be NULL, or an array of nmodels pointers any of
+ * which may be NULL.  Context-owned device buffers: N*H*W floats of members and
+ * 9*nmodels*H*W bytes of outputs.  Results are those of ucp_probability. */
+#define UCP_MAX_HOST_MODELS 16
+int ucp_probability_host_models(ucp_ctx *ctx, const float *ens_host, int N, int H, int W,
+                                const ucp_model_desc *descs, int nmodels, unsigned cptypes,
+                                float *const *out_min_host, float *const *out_max_host,
+                                uint8_t *const *status_host, ucp_stream stream);
+
 /* Uniform parameters [d' - eb/2, d' + eb/2] from a decompressed field
  * d'[H][W] and an absolute error bound eb >= 0 (Sec. "Real Datasets").
  * params: [2][H][W]. */

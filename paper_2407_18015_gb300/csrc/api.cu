@@ -155,8 +155,8 @@ int ucp_destroy(ucp_ctx *ctx) {
     if (ctx->host_ens) cudaFree(ctx->host_ens);
     if (ctx->host_out) cudaFree(ctx->host_out);
     if (ctx->pipe_ready) {
-      for (int i = 0; i < 3; ++i) cudaStreamDestroy(ctx->pipe[i]);
-      for (int k = 0; k < 2; ++k)
+      for (int i = 0; i < 2 + ucp_ctx::kPipeCompute; ++i) cudaStreamDestroy(ctx->pipe[i]);
+      for (int k = 0; k < 1 + ucp_ctx::kPipeCompute; ++k)
         for (int i = 0; i < 64; ++i) cudaEventDestroy(ctx->pipe_ev[k][i]);
     }
   }
@@ -361,8 +361,27 @@ int ucp_probability_host(ucp_ctx *ctx, const float *ens_host, int N, int H, int 
   if ((rc = valid_types(cptypes, out_min_host, out_max_host))) return rc;
   DeviceGuard g(ctx->device);
   if (g.err != cudaSuccess) return ucp_set_error(ctx, g.err);
-  return ucp_host_pipeline(ctx, ens_host, N, H, W, desc, cptypes, out_min_host, out_max_host,
-                           status_host, (cudaStream_t)stream);
+  return ucp_host_pipeline(ctx, ens_host, N, H, W, desc, 1, cptypes, &out_min_host,
+                           &out_max_host, &status_host, (cudaStream_t)stream);
+}
+
+int ucp_probability_host_models(ucp_ctx *ctx, const float *ens_host, int N, int H, int W,
+                                const ucp_model_desc *descs, int nmodels, unsigned cptypes,
+                                float *const *out_min_host, float *const *out_max_host,
+                                uint8_t *const *status_host, ucp_stream stream) {
+  if (!ctx || !ens_host || !descs || !out_min_host || !out_max_host) return UCP_ERR_ARG;
+  if (nmodels < 1 || nmodels > UCP_MAX_HOST_MODELS) return UCP_ERR_ARG;
+  int rc = valid_shape(N, H, W);
+  if (rc) return rc;
+  if (cptypes == 0 || (cptypes & ~3u)) return UCP_ERR_ARG;
+  for (int m = 0; m < nmodels; ++m) {
+    if ((rc = valid_desc(descs + m, true))) return rc;
+    if (uses_stencil(descs + m)) return UCP_ERR_UNSUPPORTED;
+  }
+  DeviceGuard g(ctx->device);
+  if (g.err != cudaSuccess) return ucp_set_error(ctx, g.err);
+  return ucp_host_pipeline(ctx, ens_host, N, H, W, descs, nmodels, cptypes, out_min_host,
+                           out_max_host, status_host, (cudaStream_t)stream);
 }
 
 int ucp_params_from_error_bound(ucp_ctx *ctx, const float *decompressed, float eb, int H,

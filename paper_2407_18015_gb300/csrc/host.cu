@@ -1,10 +1,13 @@
-// host.cu -- ucp_probability_host: host arrays in, host arrays out.
+// host.cu -- ucp_probability_host / ucp_probability_host_models: host arrays
+// in, host arrays out.
 //
-// The grid is cut into row strips.  Strip i's members (rows [r0, r1] -- one
-// extra row for the south neighbours of its last row) are copied on a copy
-// stream, the strip is computed on a compute stream once its copy event has
-// fired, and its output rows go back on a third stream.  Copies of strip i+1
-// overlap the compute of strip i and the read-back of strip i-1.
+// The grid is cut into row strips.  Strip i's members (the rows not copied
+// yet, up to one row past its last computed row, the south neighbours of its
+// last row) are copied on a copy stream; every model is computed on its own
+// compute stream once that copy has landed, and the strip's output rows of
+// every model go back on a read-back stream.  The copy of strip i+1 overlaps the
+// compute of strip i and the read-back of strip i-1.  Each member row is
+// copied once, whatever the number of models.
 #include <cuda_runtime.h>
 
 #include "launch.h"
@@ -15,7 +18,10 @@ using namespace ucp;
 namespace {
 
 constexpr int kMaxStrips = 64;
+// strips of at least 8 MiB of members, and at most 8 of them: a strip's
+// kernels then still cover a few waves of tiles
 constexpr size_t kStripBytes = 8u << 20;
+constexpr int kPipeStrips = 8;
 
 int ensure_buffer(ucp_ctx *ctx, void **p, size_t *have, size_t need) {
   if (need <= *have) return UCP_OK;
@@ -33,11 +39,11 @@ int ensure_buffer(ucp_ctx *ctx, void **p, size_t *have, size_t need) {
 
 int ensure_pipe(ucp_ctx *ctx) {
   if (ctx->pipe_ready) return UCP_OK;
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < 2 + ucp_ctx::kPipeCompute; ++i) {
     cudaError_t e = cudaStreamCreateWithFlags(&ctx->pipe[i], cudaStreamNonBlocking);
     if (e != cudaSuccess) return ucp_set_error(ctx, e);
   }
-  for (int k = 0; k < 2; ++k)
+  for (int k = 0; k < 1 + ucp_ctx::kPipeCompute; ++k)
     for (int i = 0; i < kMaxStrips; ++i) {
       cudaError_t e = cudaEventCreateWithFlags(&ctx->pipe_ev[k][i], cudaEventDisableTiming);
       if (e != cudaSuccess) return ucp_set_error(ctx, e);
@@ -49,20 +55,24 @@ int ensure_pipe(ucp_ctx *ctx) {
 }  // namespace
 
 int ucp_host_pipeline(ucp_ctx *ctx, const float *ens_host, int N, int H, int W,
-                      const ucp_model_desc *desc, unsigned cptypes, float *out_min_host,
-                      float *out_max_host, uint8_t *status_host, cudaStream_t stream) {
+                      const ucp_model_desc *descs, int nmodels, unsigned cptypes,
+                      float *const *out_min_host, float *const *out_max_host,
+                      uint8_t *const *status_host, cudaStream_t stream) {
   const long long plane = (long long)H * W;
   const size_t ens_bytes = (size_t)N * plane * sizeof(float);
   int rc = ensure_buffer(ctx, (void **)&ctx->host_ens, &ctx->host_ens_bytes, ens_bytes);
   if (rc) return rc;
-  const size_t out_bytes = (size_t)plane * (2 * sizeof(float) + 1);
+  // per model: P_min and P_max planes, then all status planes
+  const size_t out_bytes = (size_t)nmodels * plane * (2 * sizeof(float) + 1);
   if ((rc = ensure_buffer(ctx, &ctx->host_out, &ctx->host_out_bytes, out_bytes))) return rc;
   if ((rc = ensure_pipe(ctx))) return rc;
 
-  float *d_min = (float *)ctx->host_out;
-  float *d_max = d_min + plane;
-  uint8_t *d_st = (uint8_t *)(d_max + plane);
-  cudaStream_t s_in = ctx->pipe[0], s_cmp = ctx->pipe[1], s_out = ctx->pipe[2];
+  float *d_out = (float *)ctx->host_out;
+  uint8_t *d_st = (uint8_t *)(d_out + (size_t)2 * nmodels * plane);
+  // the models of a strip run on their own compute streams, so that their
+  // kernels share the GPU (one strip's tiles alone are about one wave)
+  cudaStream_t s_in = ctx->pipe[0], s_out = ctx->pipe[1];
+  const int ncs = nmodels < ucp_ctx::kPipeCompute ? nmodels : ucp_ctx::kPipeCompute;
 
   // start after the work already queued on the caller's stream
   cudaError_t e = cudaEventRecord(ctx->pipe_ev[0][0], stream);
@@ -71,65 +81,88 @@ int ucp_host_pipeline(ucp_ctx *ctx, const float *ens_host, int N, int H, int W,
 
   long long strips = (long long)((ens_bytes + kStripBytes - 1) / kStripBytes);
   if (strips < 1) strips = 1;
-  if (strips > kMaxStrips) strips = kMaxStrips;
+  if (strips > kPipeStrips) strips = kPipeStrips;
   if (strips > H) strips = H;
+  // strip i computes rows [start[i], start[i+1])
+  int start[kMaxStrips + 1];
+  int nst = 0;
   const int rows = (int)((H + strips - 1) / strips);
+  for (int r = 0; r < H; r += rows) start[nst++] = r;
+  start[nst] = H;
   const size_t pitch = (size_t)plane * sizeof(float);
 
-  Field f{};
-  f.ens = ctx->host_ens;
-  f.out_min = d_min;
-  f.out_max = d_max;
-  f.status = d_st;
-  f.plane = plane;
-  f.N = N; f.H = H; f.W = W; f.B = desc->bins;
-  f.boundary = desc->boundary;
-  f.epan_scale = desc->epan_width_scale > 0.f ? desc->epan_width_scale : 2.2360679774997896f;
-  f.cptypes = cptypes;
-  f.samples = desc->mc_samples;
-  f.seed_lo = (uint32_t)desc->seed;
-  f.seed_hi = (uint32_t)(desc->seed >> 32);
-  f.field_id = desc->field_id;
-
-  int i = 0;
-  for (int r0 = 0; r0 < H && e == cudaSuccess; r0 += rows, ++i) {
-    const int r1 = r0 + rows < H ? r0 + rows : H;
-    const int c1 = r1 < H ? r1 + 1 : H;  // copy one extra row: south neighbours
-    const size_t width = (size_t)(c1 - r0) * W * sizeof(float);
-    const size_t off = (size_t)r0 * W;
-    if (pitch <= 0x7fffffffu) {
-      e = cudaMemcpy2DAsync(ctx->host_ens + off, pitch, ens_host + off, pitch, width, N,
-                            cudaMemcpyHostToDevice, s_in);
-    } else {
-      for (int k = 0; k < N && e == cudaSuccess; ++k)
-        e = cudaMemcpyAsync(ctx->host_ens + off + (size_t)k * plane,
-                            ens_host + off + (size_t)k * plane, width, cudaMemcpyHostToDevice,
-                            s_in);
+  // every strip's copy first (the copy stream then runs back to back,
+  // whatever the host's launch latency), then every strip's kernels and
+  // read-backs, each waiting for its copy
+  int nstrips = 0, copied = 0;  // rows [0, copied) are on the device
+  for (; nstrips < nst && e == cudaSuccess; ++nstrips) {
+    const int r1 = start[nstrips + 1];
+    const int c1 = r1 < H ? r1 + 1 : H;  // one row past: the south neighbours
+    if (c1 > copied) {
+      const size_t width = (size_t)(c1 - copied) * W * sizeof(float);
+      const size_t off = (size_t)copied * W;
+      if (pitch <= 0x7fffffffu) {
+        e = cudaMemcpy2DAsync(ctx->host_ens + off, pitch, ens_host + off, pitch, width, N,
+                              cudaMemcpyHostToDevice, s_in);
+      } else {
+        for (int k = 0; k < N && e == cudaSuccess; ++k)
+          e = cudaMemcpyAsync(ctx->host_ens + off + (size_t)k * plane,
+                              ens_host + off + (size_t)k * plane, width,
+                              cudaMemcpyHostToDevice, s_in);
+      }
+      copied = c1;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->pipe_ev[0][nstrips], s_in);
+  }
+  for (int i = 0; i < nstrips && e == cudaSuccess; ++i) {
+    const int r0 = start[i], r1 = start[i + 1];
+    for (int c = 0; c < ncs && e == cudaSuccess; ++c)
+      e = cudaStreamWaitEvent(ctx->pipe[2 + c], ctx->pipe_ev[0][i], 0);
+    for (int m = 0; m < nmodels && e == cudaSuccess; ++m) {
+      cudaStream_t s_cmp = ctx->pipe[2 + m % ncs];
+      const ucp_model_desc *desc = descs + m;
+      Field f{};
+      f.ens = ctx->host_ens;
+      f.out_min = d_out + (size_t)(2 * m) * plane;
+      f.out_max = d_out + (size_t)(2 * m + 1) * plane;
+      f.status = d_st + (size_t)m * plane;
+      f.plane = plane;
+      f.N = N; f.H = H; f.W = W; f.B = desc->bins;
+      f.boundary = desc->boundary;
+      f.epan_scale = desc->epan_width_scale > 0.f ? desc->epan_width_scale : 2.2360679774997896f;
+      f.cptypes = cptypes;
+      f.samples = desc->mc_samples;
+      f.seed_lo = (uint32_t)desc->seed;
+      f.seed_hi = (uint32_t)(desc->seed >> 32);
+      f.field_id = desc->field_id;
+      f.y0 = r0;
+      f.y1 = r1;
+      e = desc->model == UCP_MVN_MC
+              ? launch_mvn_mc(f, true, desc->mc_samples, desc->seed, desc->field_id, s_cmp)
+              : launch_closed(f, desc->model, true, s_cmp);
+    }
+    for (int c = 0; c < ncs && e == cudaSuccess; ++c) {
+      e = cudaEventRecord(ctx->pipe_ev[1 + c][i], ctx->pipe[2 + c]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, ctx->pipe_ev[1 + c][i], 0);
     }
     if (e != cudaSuccess) break;
-    if ((e = cudaEventRecord(ctx->pipe_ev[0][i], s_in)) != cudaSuccess) break;
-    if ((e = cudaStreamWaitEvent(s_cmp, ctx->pipe_ev[0][i], 0)) != cudaSuccess) break;
-    f.y0 = r0;
-    f.y1 = r1;
-    e = desc->model == UCP_MVN_MC
-            ? launch_mvn_mc(f, true, desc->mc_samples, desc->seed, desc->field_id, s_cmp)
-            : launch_closed(f, desc->model, true, s_cmp);
-    if (e != cudaSuccess) break;
-    if ((e = cudaEventRecord(ctx->pipe_ev[1][i], s_cmp)) != cudaSuccess) break;
-    if ((e = cudaStreamWaitEvent(s_out, ctx->pipe_ev[1][i], 0)) != cudaSuccess) break;
-    const size_t nb = (size_t)(r1 - r0) * W;
-    if ((cptypes & 1u) && out_min_host)
-      e = cudaMemcpyAsync(out_min_host + off, d_min + off, nb * sizeof(float),
-                          cudaMemcpyDeviceToHost, s_out);
-    if (e == cudaSuccess && (cptypes & 2u) && out_max_host)
-      e = cudaMemcpyAsync(out_max_host + off, d_max + off, nb * sizeof(float),
-                          cudaMemcpyDeviceToHost, s_out);
-    if (e == cudaSuccess && status_host)
-      e = cudaMemcpyAsync(status_host + off, d_st + off, nb, cudaMemcpyDeviceToHost, s_out);
+    const size_t off = (size_t)r0 * W, nb = (size_t)(r1 - r0) * W;
+    for (int m = 0; m < nmodels && e == cudaSuccess; ++m) {
+      const float *dmin = d_out + (size_t)(2 * m) * plane, *dmax = dmin + plane;
+      if ((cptypes & 1u) && out_min_host[m])
+        e = cudaMemcpyAsync(out_min_host[m] + off, dmin + off, nb * sizeof(float),
+                            cudaMemcpyDeviceToHost, s_out);
+      if (e == cudaSuccess && (cptypes & 2u) && out_max_host[m])
+        e = cudaMemcpyAsync(out_max_host[m] + off, dmax + off, nb * sizeof(float),
+                            cudaMemcpyDeviceToHost, s_out);
+      if (e == cudaSuccess && status_host && status_host[m])
+        e = cudaMemcpyAsync(status_host[m] + off, d_st + (size_t)m * plane + off, nb,
+                            cudaMemcpyDeviceToHost, s_out);
+    }
   }
-  cudaError_t e2 = cudaStreamSynchronize(s_in);
-  cudaError_t e3 = cudaStreamSynchronize(s_cmp);
-  cudaError_t e4 = cudaStreamSynchronize(s_out);
-  if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : (e3 != cudaSuccess ? e3 : e4);
+  for (int k = 0; k < 2 + ncs; ++k) {
+    const cudaError_t ek = cudaStreamSynchronize(ctx->pipe[k]);
+    if (e == cudaSuccess) e = ek;
+  }
   return ucp_set_error(ctx, e);
 }

@@ -20,13 +20,19 @@ struct ucp_ctx {
   size_t host_ens_bytes = 0;
   void *host_out = nullptr;
   size_t host_out_bytes = 0;
-  cudaStream_t pipe[3] = {nullptr, nullptr, nullptr};
-  cudaEvent_t pipe_ev[2][64] = {};
+  // host-buffer pipeline: pipe[0] copies in, pipe[1] copies out,
+  // pipe[2..] compute (one per model, up to kPipeCompute); events per strip:
+  // copy landed (pipe_ev[0]), and each compute stream done (pipe_ev[1 + c])
+  static constexpr int kPipeCompute = 4;
+  cudaStream_t pipe[2 + kPipeCompute] = {};
+  cudaEvent_t pipe_ev[1 + kPipeCompute][64] = {};
   bool pipe_ready = false;
 };
 
 int ucp_set_error(ucp_ctx *ctx, cudaError_t e);
 int ucp_ensure_work(ucp_ctx *ctx, size_t bytes);
+// models of one ensemble from host arrays (ucp_probability_host[_models])
 int ucp_host_pipeline(ucp_ctx *ctx, const float *ens_host, int N, int H, int W,
-                      const ucp_model_desc *desc, unsigned cptypes, float *out_min_host,
-                      float *out_max_host, uint8_t *status_host, cudaStream_t stream);
+                      const ucp_model_desc *descs, int nmodels, unsigned cptypes,
+                      float *const *out_min_host, float *const *out_max_host,
+                      uint8_t *const *status_host, cudaStream_t stream);

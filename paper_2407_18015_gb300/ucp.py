@@ -79,6 +79,8 @@ def lib():
                 "ucp_probability": ([_P, _P, _I, _I, _I, D, ctypes.c_uint, _P, _P, _P, _P], _I),
                 "ucp_probability_host": ([_P, _P, _I, _I, _I, D, ctypes.c_uint, _P, _P, _P, _P],
                                          _I),
+                "ucp_probability_host_models": ([_P, _P, _I, _I, _I, D, _I, ctypes.c_uint, _P, _P,
+                                                 _P, _P], _I),
                 "ucp_saddle": ([_P, _P, _I, _I, _I, D, _P, _P, _P], _I),
                 "ucp_saddle_from_params": ([_P, _P, _I, _I, D, _P, _P, _P], _I),
                 "ucp_params_from_error_bound": ([_P, _P, ctypes.c_float, _I, _I, _P, _P], _I),
@@ -243,6 +245,28 @@ def ucp_probability_host(ctx, ens_host, desc, cptypes, out_min_host, out_max_hos
         _hptr(out_min_host, "out_min_host"), _hptr(out_max_host, "out_max_host"),
         _hptr(status_host, "status_host"), _stream(stream))
     _check(rc, "ucp_probability_host", ctx)
+
+
+def ucp_probability_host_models(ctx, ens_host, descs, cptypes, out_min_host, out_max_host,
+                                status_host=None, stream=None):
+    """Several models of one ensemble with host arrays: descs, out_min_host,
+    out_max_host (and status_host, if given) are sequences of the same length;
+    an output entry may be None when cptypes leaves it out."""
+    N, H, W = ens_host.shape
+    n = len(descs)
+    if len(out_min_host) != n or len(out_max_host) != n or \
+            (status_host is not None and len(status_host) != n):
+        raise ValueError("one output per model")
+    darr = (ucp_model_desc * n)(*descs)
+    pmin = (ctypes.c_void_p * n)(*[_hptr(a, "out_min_host") for a in out_min_host])
+    pmax = (ctypes.c_void_p * n)(*[_hptr(a, "out_max_host") for a in out_max_host])
+    pst = None if status_host is None else \
+        (ctypes.c_void_p * n)(*[_hptr(a, "status_host") for a in status_host])
+    addr = lambda a: None if a is None else ctypes.cast(a, ctypes.c_void_p)
+    rc = lib().ucp_probability_host_models(
+        ctx, _hptr(ens_host, "ens_host"), N, H, W, darr, n, int(cptypes), addr(pmin), addr(pmax),
+        addr(pst), _stream(stream))
+    _check(rc, "ucp_probability_host_models", ctx)
 
 
 def ucp_params_from_error_bound(ctx, decompressed, eb, params, stream=None):

@@ -65,6 +65,9 @@ def test_validation_happens_before_cuda(L):
     assert L.ucp_destroy(None) == ucp.UCP_ERR_ARG
     assert L.ucp_batch_create(None, None) == ucp.UCP_ERR_ARG
     assert L.ucp_batch_run(None, None) == ucp.UCP_ERR_ARG
+    outs = (P * 1)(P(16))
+    assert L.ucp_probability_host_models(None, P(16), 4, 4, 4, ctypes.byref(d), 1, 3, outs,
+                                         outs, None, None) == ucp.UCP_ERR_ARG
 
 
 def test_gauss_legendre_constants_match_numpy():

@@ -258,3 +258,47 @@ def test_histogram_bin_counts(ucp, ctx, orc, bins):
     _compare(pmax, rmax, what="max")
     _compare(sad, rsad, what="saddle")
     np.testing.assert_array_equal(st.cpu().numpy(), rst)
+
+
+@pytest.mark.parametrize("shape,N", [((300, 257), 9), ((700, 1024), 20), ((5, 12), 3)])
+def test_host_models_match_device(ucp, ctx, shape, N):
+    """ucp_probability_host_models: every model of one ensemble from host
+    arrays (pinned and pageable), the members copied once in row strips, gives
+    exactly the per-model device results; also with a model whose outputs are
+    not wanted (NULL) and without status arrays."""
+    from paper_2407_18015_gb300 import synth
+    H, W = shape
+    ens_np = synth.ensemble_bimodal(H, W, N, seed=31 + H, lam_scale=0.5)
+    descs = [ucp.make_desc(m, bins=b or 8) for m, b in MODELS] + \
+        [ucp.make_desc("histogram", bins=16), ucp.make_desc("mvn", mc_samples=64, seed=7)]
+    ref = [ctx.probability(_dev(ens_np), d) for d in descs]
+    torch.cuda.synchronize()
+    n = len(descs)
+    for pinned in (True, False):
+        ens_h = torch.from_numpy(ens_np).pin_memory() if pinned else ens_np
+        hmin = [np.full((H, W), -1, np.float32) for _ in range(n)]
+        hmax = [np.full((H, W), -1, np.float32) for _ in range(n)]
+        hst = [np.zeros((H, W), np.uint8) for _ in range(n)]
+        ucp.ucp_probability_host_models(ctx.handle, ens_h, descs, 3, hmin, hmax, hst)
+        for m in range(n):
+            np.testing.assert_array_equal(hmin[m], ref[m][0].cpu().numpy())
+            np.testing.assert_array_equal(hmax[m], ref[m][1].cpu().numpy())
+            np.testing.assert_array_equal(hst[m], ref[m][2].cpu().numpy())
+    # minimum only, the second model's output unwanted, no status
+    hmin = [np.full((H, W), -1, np.float32) if m != 1 else None for m in range(n)]
+    ucp.ucp_probability_host_models(ctx.handle, ens_np, descs, ucp.UCP_MIN, hmin, [None] * n)
+    for m in range(n):
+        if m != 1:
+            np.testing.assert_array_equal(hmin[m], ref[m][0].cpu().numpy())
+
+
+def test_host_models_rejects(ucp, ctx):
+    ens = np.zeros((3, 8, 8), np.float32)
+    out = [np.zeros((8, 8), np.float32)]
+    with pytest.raises(ucp.UcpError):
+        ucp.ucp_probability_host_models(ctx.handle, ens, [], 3, [], [])
+    with pytest.raises(ucp.UcpError):
+        ucp.ucp_probability_host_models(ctx.handle, ens, [ucp.make_desc("uniform")], 4, out, out)
+    d = ucp.make_desc("uniform", stencil=ucp.UCP_STENCIL_8)
+    with pytest.raises(ucp.UcpError):
+        ucp.ucp_probability_host_models(ctx.handle, ens, [d], 1, out, out)
