@@ -246,12 +246,30 @@ int ucp_probability_host(ucp_ctx *ctx, const float *ens_host, int N, int H, int 
                          const ucp_model_desc *desc, unsigned cptypes, float *out_min_host,
                          float *out_max_host, uint8_t *status_host, ucp_stream stream);
 
+#define UCP_MAX_MODELS 16
+
+/* Several models of one ensemble, device arrays: the models' kernels run
+ * concurrently on the context's compute streams, forked from `stream` and
+ * joined back into it (asynchronous; the results are those of
+ * ucp_probability for each model).  descs[0..nmodels-1], 1 <= nmodels <=
+ * UCP_MAX_MODELS, none with a larger stencil (UCP_ERR_UNSUPPORTED);
+ * cptypes applies to every model.  out_min[m] / out_max[m]: [H][W] device
+ * arrays of model m for the types in cptypes, an entry may be NULL (that
+ * field is not written); vertex_status may be NULL, or nmodels pointers any
+ * of which may be NULL.  Calls on one context must not overlap (they share
+ * its streams).  The paper evaluates its models on the same ensemble
+ * (Sec. "Comparison of Parametric Vs. Nonparametric Models"). */
+int ucp_probability_models(ucp_ctx *ctx, const float *ens, int N, int H, int W,
+                           const ucp_model_desc *descs, int nmodels, unsigned cptypes,
+                           float *const *out_min, float *const *out_max,
+                           uint8_t *const *vertex_status, ucp_stream stream);
+
 /* Several models of one ensemble with HOST arrays (the paper compares its
  * models on the same ensemble, Sec. "Comparison of Parametric Vs.
  * Nonparametric Models"): the members are copied to the device once, in row
  * strips whose copies overlap the computation of the previous strip (every
  * model) and the read-back of the one before; synchronises the stream before
- * returning.  descs[0..nmodels-1], 1 <= nmodels <= UCP_MAX_HOST_MODELS, none
+ * returning.  descs[0..nmodels-1], 1 <= nmodels <= UCP_MAX_MODELS, none
  * with a larger stencil (UCP_ERR_UNSUPPORTED); cptypes applies to every
  * model.  out_min_host[m] / out_max_host[m]: [H][W] host arrays of model m
  * for the types in cptypes; an entry may be NULL, and that field of that
@@ -259,7 +277,6 @@ int ucp_probability_host(ucp_ctx *ctx, const float *ens_host, int N, int H, int 
  * NULL).  status_host may be NULL, or an array of nmodels pointers any of
  * which may be NULL.  Context-owned device buffers: N*H*W floats of members and
  * 9*nmodels*H*W bytes of outputs.  Results are those of ucp_probability. */
-#define UCP_MAX_HOST_MODELS 16
 int ucp_probability_host_models(ucp_ctx *ctx, const float *ens_host, int N, int H, int W,
                                 const ucp_model_desc *descs, int nmodels, unsigned cptypes,
                                 float *const *out_min_host, float *const *out_max_host,

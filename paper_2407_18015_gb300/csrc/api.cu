@@ -158,6 +158,9 @@ int ucp_destroy(ucp_ctx *ctx) {
       for (int i = 0; i < 2 + ucp_ctx::kPipeCompute; ++i) cudaStreamDestroy(ctx->pipe[i]);
       for (int k = 0; k < 1 + ucp_ctx::kPipeCompute; ++k)
         for (int i = 0; i < 64; ++i) cudaEventDestroy(ctx->pipe_ev[k][i]);
+      if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+      for (int k = 0; k < ucp_ctx::kPipeCompute; ++k)
+        if (ctx->join_ev[k]) cudaEventDestroy(ctx->join_ev[k]);
     }
   }
   delete ctx;
@@ -365,12 +368,49 @@ int ucp_probability_host(ucp_ctx *ctx, const float *ens_host, int N, int H, int 
                            &out_max_host, &status_host, (cudaStream_t)stream);
 }
 
+int ucp_probability_models(ucp_ctx *ctx, const float *ens, int N, int H, int W,
+                           const ucp_model_desc *descs, int nmodels, unsigned cptypes,
+                           float *const *out_min, float *const *out_max,
+                           uint8_t *const *vertex_status, ucp_stream stream) {
+  if (!ctx || !ens || !descs || !out_min || !out_max) return UCP_ERR_ARG;
+  if (nmodels < 1 || nmodels > UCP_MAX_MODELS) return UCP_ERR_ARG;
+  int rc = valid_shape(N, H, W);
+  if (rc) return rc;
+  if (cptypes == 0 || (cptypes & ~3u)) return UCP_ERR_ARG;
+  for (int m = 0; m < nmodels; ++m) {
+    if ((rc = valid_desc(descs + m, true))) return rc;
+    if (uses_stencil(descs + m)) return UCP_ERR_UNSUPPORTED;
+  }
+  DeviceGuard g(ctx->device);
+  if (g.err != cudaSuccess) return ucp_set_error(ctx, g.err);
+  if ((rc = ucp_ensure_pipe(ctx))) return rc;
+  const int ncs = nmodels < ucp_ctx::kPipeCompute ? nmodels : ucp_ctx::kPipeCompute;
+  // fork: every compute stream starts after the work queued on `stream`
+  cudaError_t e = cudaEventRecord(ctx->fork_ev, (cudaStream_t)stream);
+  for (int c = 0; c < ncs && e == cudaSuccess; ++c)
+    e = cudaStreamWaitEvent(ctx->pipe[2 + c], ctx->fork_ev, 0);
+  if (e != cudaSuccess) return ucp_set_error(ctx, e);
+  for (int m = 0; m < nmodels && rc == UCP_OK; ++m)
+    rc = probability_impl(ctx, ens, nullptr, N, H, W, descs + m, cptypes,
+                          (cptypes & 1u) ? out_min[m] : nullptr,
+                          (cptypes & 2u) ? out_max[m] : nullptr,
+                          vertex_status ? vertex_status[m] : nullptr, ctx->pipe[2 + m % ncs]);
+  // join: `stream` continues after every model (also after a failed launch,
+  // so that nothing already queued outlives the call's ordering)
+  for (int c = 0; c < ncs && e == cudaSuccess; ++c) {
+    e = cudaEventRecord(ctx->join_ev[c], ctx->pipe[2 + c]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent((cudaStream_t)stream, ctx->join_ev[c], 0);
+  }
+  if (rc != UCP_OK) return rc;
+  return ucp_set_error(ctx, e);
+}
+
 int ucp_probability_host_models(ucp_ctx *ctx, const float *ens_host, int N, int H, int W,
                                 const ucp_model_desc *descs, int nmodels, unsigned cptypes,
                                 float *const *out_min_host, float *const *out_max_host,
                                 uint8_t *const *status_host, ucp_stream stream) {
   if (!ctx || !ens_host || !descs || !out_min_host || !out_max_host) return UCP_ERR_ARG;
-  if (nmodels < 1 || nmodels > UCP_MAX_HOST_MODELS) return UCP_ERR_ARG;
+  if (nmodels < 1 || nmodels > UCP_MAX_MODELS) return UCP_ERR_ARG;
   int rc = valid_shape(N, H, W);
   if (rc) return rc;
   if (cptypes == 0 || (cptypes & ~3u)) return UCP_ERR_ARG;

@@ -37,7 +37,9 @@ int ensure_buffer(ucp_ctx *ctx, void **p, size_t *have, size_t need) {
   return UCP_OK;
 }
 
-int ensure_pipe(ucp_ctx *ctx) {
+}  // namespace
+
+int ucp_ensure_pipe(ucp_ctx *ctx) {
   if (ctx->pipe_ready) return UCP_OK;
   for (int i = 0; i < 2 + ucp_ctx::kPipeCompute; ++i) {
     cudaError_t e = cudaStreamCreateWithFlags(&ctx->pipe[i], cudaStreamNonBlocking);
@@ -48,11 +50,14 @@ int ensure_pipe(ucp_ctx *ctx) {
       cudaError_t e = cudaEventCreateWithFlags(&ctx->pipe_ev[k][i], cudaEventDisableTiming);
       if (e != cudaSuccess) return ucp_set_error(ctx, e);
     }
+  for (int k = 0; k <= ucp_ctx::kPipeCompute; ++k) {
+    cudaEvent_t *ev = k == 0 ? &ctx->fork_ev : &ctx->join_ev[k - 1];
+    cudaError_t e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return ucp_set_error(ctx, e);
+  }
   ctx->pipe_ready = true;
   return UCP_OK;
 }
-
-}  // namespace
 
 int ucp_host_pipeline(ucp_ctx *ctx, const float *ens_host, int N, int H, int W,
                       const ucp_model_desc *descs, int nmodels, unsigned cptypes,
@@ -65,7 +70,7 @@ int ucp_host_pipeline(ucp_ctx *ctx, const float *ens_host, int N, int H, int W,
   // per model: P_min and P_max planes, then all status planes
   const size_t out_bytes = (size_t)nmodels * plane * (2 * sizeof(float) + 1);
   if ((rc = ensure_buffer(ctx, &ctx->host_out, &ctx->host_out_bytes, out_bytes))) return rc;
-  if ((rc = ensure_pipe(ctx))) return rc;
+  if ((rc = ucp_ensure_pipe(ctx))) return rc;
 
   float *d_out = (float *)ctx->host_out;
   uint8_t *d_st = (uint8_t *)(d_out + (size_t)2 * nmodels * plane);

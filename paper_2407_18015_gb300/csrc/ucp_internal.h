@@ -26,11 +26,17 @@ struct ucp_ctx {
   static constexpr int kPipeCompute = 4;
   cudaStream_t pipe[2 + kPipeCompute] = {};
   cudaEvent_t pipe_ev[1 + kPipeCompute][64] = {};
+  // fork of the caller's stream into the compute streams and the joins back
+  // (ucp_probability_models)
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[kPipeCompute] = {};
   bool pipe_ready = false;
 };
 
 int ucp_set_error(ucp_ctx *ctx, cudaError_t e);
 int ucp_ensure_work(ucp_ctx *ctx, size_t bytes);
+// the context's streams and events of the multi-model entry points (once)
+int ucp_ensure_pipe(ucp_ctx *ctx);
 // models of one ensemble from host arrays (ucp_probability_host[_models])
 int ucp_host_pipeline(ucp_ctx *ctx, const float *ens_host, int N, int H, int W,
                       const ucp_model_desc *descs, int nmodels, unsigned cptypes,

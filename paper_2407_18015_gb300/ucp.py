@@ -81,6 +81,8 @@ def lib():
                                          _I),
                 "ucp_probability_host_models": ([_P, _P, _I, _I, _I, D, _I, ctypes.c_uint, _P, _P,
                                                  _P, _P], _I),
+                "ucp_probability_models": ([_P, _P, _I, _I, _I, D, _I, ctypes.c_uint, _P, _P, _P,
+                                            _P], _I),
                 "ucp_saddle": ([_P, _P, _I, _I, _I, D, _P, _P, _P], _I),
                 "ucp_saddle_from_params": ([_P, _P, _I, _I, D, _P, _P, _P], _I),
                 "ucp_params_from_error_bound": ([_P, _P, ctypes.c_float, _I, _I, _P, _P], _I),
@@ -245,6 +247,28 @@ def ucp_probability_host(ctx, ens_host, desc, cptypes, out_min_host, out_max_hos
         _hptr(out_min_host, "out_min_host"), _hptr(out_max_host, "out_max_host"),
         _hptr(status_host, "status_host"), _stream(stream))
     _check(rc, "ucp_probability_host", ctx)
+
+
+def ucp_probability_models(ctx, ens, descs, cptypes, out_min, out_max, vertex_status=None,
+                           stream=None):
+    """Several models of one ensemble (device tensors), their kernels
+    concurrent on the context's streams, forked from and joined back into the
+    current stream.  descs, out_min, out_max (and vertex_status, if given) are
+    sequences of the same length; an output entry may be None."""
+    H, W = _grid(ens, descs[0], "ens")
+    n = len(descs)
+    if len(out_min) != n or len(out_max) != n or \
+            (vertex_status is not None and len(vertex_status) != n):
+        raise ValueError("one output per model")
+    darr = (ucp_model_desc * n)(*descs)
+    arr = lambda ts, dt, nm: ctypes.cast((ctypes.c_void_p * n)(
+        *[_ptr(t, dt, name=nm) for t in ts]), ctypes.c_void_p)
+    rc = lib().ucp_probability_models(
+        ctx, _ptr(ens, torch.float32, name="ens"), ens.shape[0], H, W, darr, n, int(cptypes),
+        arr(out_min, torch.float32, "out_min"), arr(out_max, torch.float32, "out_max"),
+        None if vertex_status is None else arr(vertex_status, torch.uint8, "vertex_status"),
+        _stream(stream, ens.device))
+    _check(rc, "ucp_probability_models", ctx)
 
 
 def ucp_probability_host_models(ctx, ens_host, descs, cptypes, out_min_host, out_max_host,

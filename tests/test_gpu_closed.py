@@ -302,3 +302,36 @@ def test_host_models_rejects(ucp, ctx):
     d = ucp.make_desc("uniform", stencil=ucp.UCP_STENCIL_8)
     with pytest.raises(ucp.UcpError):
         ucp.ucp_probability_host_models(ctx.handle, ens, [d], 1, out, out)
+
+
+def test_models_concurrent_match_single(ucp, ctx):
+    """ucp_probability_models (the models' kernels concurrent on the context's
+    streams, forked from and joined into the current stream) gives exactly
+    the per-model ucp_probability results, with unwanted outputs left
+    untouched and on a non-default stream."""
+    from paper_2407_18015_gb300 import synth
+    ens_np = synth.ensemble_bimodal(333, 260, 20, seed=77, lam_scale=0.5)
+    ens = _dev(ens_np)
+    descs = [ucp.make_desc(m, bins=b or 8) for m, b in MODELS] + \
+        [ucp.make_desc("histogram", bins=16), ucp.make_desc("mvn", mc_samples=64, seed=3),
+         ucp.make_desc("gaussian")]
+    ref = [ctx.probability(ens, d) for d in descs]
+    n = len(descs)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        omin = [torch.full((333, 260), -1.0, device="cuda") for _ in range(n)]
+        omax = [torch.full((333, 260), -1.0, device="cuda") if m != 2 else None for m in range(n)]
+        ost = [torch.zeros((333, 260), dtype=torch.uint8, device="cuda") for _ in range(n)]
+        ucp.ucp_probability_models(ctx.handle, ens, descs, 3, omin, omax, ost)
+        got = [(a.clone(), None if b is None else b.clone(), c.clone())
+               for a, b, c in zip(omin, omax, ost)]
+    torch.cuda.synchronize()
+    for m in range(n):
+        assert torch.equal(got[m][0], ref[m][0])
+        if m != 2:
+            assert torch.equal(got[m][1], ref[m][1])
+        assert torch.equal(got[m][2], ref[m][2])
+    with pytest.raises(ucp.UcpError):
+        ucp.ucp_probability_models(ctx.handle, ens, [ucp.make_desc("uniform",
+                                                                   stencil=ucp.UCP_STENCIL_6)],
+                                   1, omin[:1], omax[:1])
