@@ -88,7 +88,8 @@ __global__ void __launch_bounds__(256) fit_kernel(Field f) {
 // resident CTAs per SM each model's register budget is tuned for
 template <int MODEL>
 struct TileOcc {
-  static constexpr int value = MODEL == kUniform ? 5 : (MODEL == kEpan ? 5 : (MODEL == kHist ? 3 : 2));
+  static constexpr int value =
+      MODEL == kUniform ? 5 : (MODEL == kEpan ? 5 : (MODEL == kHist ? 3 : (MODEL == kSemi ? 4 : 2)));
 };
 
 // tile height: 8 rows for the uniform and histogram models and the

@@ -1017,32 +1017,24 @@ struct SemiNb {
   int kind;          // 0 absent, 1 bins, 2 point mass
 };
 
-// F_n(x) and G_n(x) = T_n - F_n(x) of a neighbour at the local position x
+// F_n(x) and G_n(x) = T_n - F_n(x) of a neighbour at the local position x.
+// Branch-free, so that the lanes of a warp stay converged: the in-support
+// value is formed for every kind (its reads stay inside the neighbour's
+// rows: the bin index is clamped to [0, B-1]; an absent or point-mass
+// neighbour has ih = 0) and the result selected by position and kind.
 template <int WS>
 __device__ __forceinline__ void semi_tails(const float *w, const float *C, const SemiNb &n, int B,
                                            float x, float &G, float &F) {
-  if (n.kind == 0) {
-    G = F = 1.f;
-    return;
-  }
-  if (n.kind == 2) {
-    G = x < n.lam ? n.T : 0.f;
-    F = x > n.lam ? n.T : 0.f;
-    return;
-  }
   const float v = (x - n.lam) * n.ih;
   const float fk = floorf(v);
-  if (fk < 0.f) {
-    G = n.T;
-    F = 0.f;
-  } else if (fk >= (float)B) {
-    G = 0.f;
-    F = n.T;
-  } else {
-    const int k = (int)fk;
-    const float Ck = k > 0 ? C[(k - 1) * WS + n.off] : 0.f;
-    F = fmaf(w[k * WS + n.off], v - fk, Ck);
-    G = n.T - F;
+  const int k = (int)fminf(fmaxf(fk, 0.f), (float)(B - 1));
+  const float Ck = C[max(k - 1, 0) * WS + n.off];
+  const float Fin = fmaf(w[k * WS + n.off], v - fk, k > 0 ? Ck : 0.f);
+  F = fk < 0.f ? 0.f : (fk >= (float)B ? n.T : Fin);
+  G = fk < 0.f ? n.T : (fk >= (float)B ? 0.f : n.T - Fin);
+  if (n.kind != 1) {
+    G = n.kind == 2 ? (x < n.lam ? n.T : 0.f) : 1.f;
+    F = n.kind == 2 ? (x > n.lam ? n.T : 0.f) : 1.f;
   }
 }
 
