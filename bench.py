@@ -27,6 +27,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -377,9 +378,12 @@ def run_ours(args):
                 e1.record()
                 ev.append((m, e0, e1))
 
-    # the timed region: barrier + synchronize on both sides
-    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-    sampler = ClockSampler(local, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv"))
+    # the timed region: barrier + synchronize on both sides.  The raw clock
+    # samples go to a CSV (UCP_CLOCKS_DIR, else the temporary directory); the
+    # JSON line carries their summary.
+    clocks_dir = os.environ.get("UCP_CLOCKS_DIR") or tempfile.gettempdir()
+    os.makedirs(clocks_dir, exist_ok=True)
+    sampler = ClockSampler(local, os.path.join(clocks_dir, f"ucp_clocks_rank{rank}.csv"))
     time.sleep(1.0)                      # let the sampler start before timing
     replicas.barrier()
     torch.cuda.synchronize()

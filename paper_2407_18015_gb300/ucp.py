@@ -63,7 +63,7 @@ def lib():
         if _lib is None:
             if not os.path.exists(LIB_PATH):
                 raise ImportError(f"libucp.so not built ({LIB_PATH}); run "
-                                  "`python -c 'import __graft_entry__ as g; g.build()'`")
+                                  "`python -m paper_2407_18015_gb300.build`")
             L = ctypes.CDLL(LIB_PATH)
             D = ctypes.POINTER(ucp_model_desc)
             sig = {
