@@ -546,8 +546,27 @@ __device__ __forceinline__ bool stage_members_tma(const Field &f, float *sm, flo
           if (!bin[p]) continue;
           const float *col = box + off[p];
           float *w0 = sm + 2 * HALO + lv[p];
-          for (int k = 0; k < kn; ++k)
-            w0[hist_bin(col[k * PLANE], mn[p], sc[p], B) * HALO] += 1.f;
+          bool counted = false;
+          if constexpr (ROWS) {
+            // up to 8 bins (always so with per-bin rows) and 255 members:
+            // 8-bit counters packed in two registers, no shared-memory
+            // read-modify-write chain from member to member
+            if (N <= 255) {
+              uint32_t c0 = 0u, c1 = 0u;
+              for (int k = 0; k < kn; ++k) {
+                const int j = hist_bin(col[k * PLANE], mn[p], sc[p], B);
+                const uint32_t inc = 1u << ((j & 3) << 3);
+                c0 += j < 4 ? inc : 0u;
+                c1 += j < 4 ? 0u : inc;
+              }
+              for (int b = 0; b < B; ++b)
+                w0[b * HALO] += (float)(((b < 4 ? c0 : c1) >> ((b & 3) << 3)) & 255u);
+              counted = true;
+            }
+          }
+          if (!counted)
+            for (int k = 0; k < kn; ++k)
+              w0[hist_bin(col[k * PLANE], mn[p], sc[p], B) * HALO] += 1.f;
         }
       }
       __syncthreads();
