@@ -68,6 +68,22 @@ def test_validation_happens_before_cuda(L):
     outs = (P * 1)(P(16))
     assert L.ucp_probability_host_models(None, P(16), 4, 4, 4, ctypes.byref(d), 1, 3, outs,
                                          outs, None, None) == ucp.UCP_ERR_ARG
+    assert L.ucp_probability_models(None, P(16), 4, 4, 4, ctypes.byref(d), 1, 3, outs, outs,
+                                    None, None) == ucp.UCP_ERR_ARG
+    # a context-sized zeroed buffer stands in for the context: these calls
+    # fail validation (no models, bad types, larger stencil) before any CUDA
+    fake = ctypes.create_string_buffer(1 << 16)
+    ctx = ctypes.cast(fake, ctypes.c_void_p)
+    for fn in (L.ucp_probability_models, L.ucp_probability_host_models):
+        assert fn(ctx, P(16), 4, 4, 4, ctypes.byref(d), 0, 3, outs, outs, None,
+                  None) == ucp.UCP_ERR_ARG
+        assert fn(ctx, P(16), 4, 4, 4, ctypes.byref(d), 17, 3, outs, outs, None,
+                  None) == ucp.UCP_ERR_ARG
+        assert fn(ctx, P(16), 4, 4, 4, ctypes.byref(d), 1, 4, outs, outs, None,
+                  None) == ucp.UCP_ERR_ARG
+        d6 = ucp.make_desc("uniform", stencil=ucp.UCP_STENCIL_6)
+        assert fn(ctx, P(16), 4, 4, 4, ctypes.byref(d6), 1, 3, outs, outs, None,
+                  None) == ucp.UCP_ERR_UNSUPPORTED
 
 
 def test_gauss_legendre_constants_match_numpy():
