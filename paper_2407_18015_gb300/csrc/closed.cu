@@ -1,14 +1,15 @@
 // closed.cu -- closed-form critical-point probability kernels (uniform,
 // Epanechnikov, histogram) and the statistics pass.
 //
-// Tile kernel: one CTA per 16 x 32 tile of vertices.  Phase 1 stages the
-// parameters of the tile and its one-vertex halo (18 x 34) in shared memory,
-// either fitted from the members (the statistics pass fused into the same
-// launch, so parameters never reach HBM) or loaded from a parameter array.
-// Phase 2 gives each thread two vertices; a vertex reads its own and its
-// four neighbours' parameters from shared memory (the neighbourhood access
-// of the paper's VTK-m worklet, Sec. "Integration with VTK-m and ParaView")
-// and integrates P_min / P_max exactly (device.cuh).
+// Tile kernel: one CTA per TY x 32 tile of vertices (TY = 8 or 16, see
+// TileH).  Phase 1 stages the parameters of the tile and its one-vertex halo
+// ((TY + 2) x 34) in shared memory, either fitted from the members (the
+// statistics pass fused into the same launch, so parameters never reach HBM)
+// or loaded from a parameter array.  Phase 2 gives each of the 256 threads
+// TY / 8 vertices; a vertex reads its own and its four neighbours'
+// parameters from shared memory (the neighbourhood access of the paper's
+// VTK-m worklet, Sec. "Integration with VTK-m and ParaView") and integrates
+// P_min / P_max exactly (device.cuh).
 #include <cudaTypedefs.h>
 
 #include <algorithm>
