@@ -183,9 +183,9 @@ ADJ_HIST_FLOPS_PER_PIECE = 5 * HIST_FLOPS_PER_PIECE_TYPE
 # DRAM bytes (read + write) per launch of each headline kernel from the ncu
 # capture summarised in profiles/; None once a kernel has changed since its
 # counters were taken
-TRAFFIC_BYTES = {"uniform": 83.920128e6 + 4.726016e6,
-                 "epanechnikov": 83.941632e6 + 4.446976e6,
-                 "histogram": 83.966720e6 + 4.915968e6}
+TRAFFIC_BYTES = {"uniform": 83.921408e6 + 4.750592e6,
+                 "epanechnikov": 83.937536e6 + 4.673024e6,
+                 "histogram": 83.967488e6 + 5.478144e6}
 
 
 def work_of(model, N, HW, params=None, bins=BINS2):

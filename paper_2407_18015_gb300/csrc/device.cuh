@@ -554,10 +554,13 @@ __device__ __forceinline__ void epan_pieces(const float *x, const float (*pay)[4
     float2 f = __fmul2_rn(make_float2(c1, c1), make_float2(fmaxf(g.x, 0.f), fmaxf(g.y, 0.f)));
 #pragma unroll
     for (int i = 0; i < J; ++i) {
-      // epan_surv of both nodes
-      float2 u = __fmul2_rn(__fadd2_rn(xx, make_float2(-pay[0][i], -pay[0][i])),
-                            make_float2(pay[1][i], pay[1][i]));
-      u = make_float2(fminf(fmaxf(u.x, -1.f), 1.f), fminf(fmaxf(u.y, -1.f), 1.f));
+      // epan_surv of both nodes, unclamped: on the piece where J factors
+      // have started, each started factor's u lies in [-1, 1] (the piece
+      // begins after the factor's start, and R is at most every present
+      // neighbour's end); absent and point-mass factors start at R and so
+      // only enter pieces of zero width
+      const float2 u = __fmul2_rn(__fadd2_rn(xx, make_float2(-pay[0][i], -pay[0][i])),
+                                  make_float2(pay[1][i], pay[1][i]));
       const float2 qq = __fadd2_rn(one2, make_float2(-u.x, -u.y));
       const float2 sv = __fmul2_rn(__fmul2_rn(make_float2(0.25f, 0.25f), __fmul2_rn(qq, qq)),
                                    __fadd2_rn(make_float2(2.f, 2.f), u));
