@@ -18,6 +18,8 @@
 //     Epanechnikov differentiates the density (it vanishes at the ends);
 //     histogram: dP/dw_j = (1/h) int_{bin j} prod G.
 // Maxima use the negated variables (P_max(theta) = P_min(-theta)).
+#include <atomic>
+
 #include "device.cuh"
 #include "launch.h"
 #include "tile.cuh"
@@ -924,19 +926,21 @@ cudaError_t launch_backward(const Field &f, int model, int cptype, const float *
     case kEpan: partials_kernel<kEpan><<<(int)b, 128, 0, s>>>(f, want_max, weight, rows); break;
     case kHist: {
       constexpr int TYg = kGradTY;
-      static bool attr_set[128] = {};
+      // per device: the attribute is set once (host threads may race to set
+      // it; setting it twice is harmless, the flag itself is atomic)
+      static std::atomic<bool> attr_set[128] = {};
       int dev = 0;
       cudaError_t e = cudaGetDevice(&dev);
       if (e != cudaSuccess) return e;
       if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
-      if (!attr_set[dev]) {
+      if (!attr_set[dev].load(std::memory_order_acquire)) {
         e = cudaFuncSetAttribute(hist_partials_tile<TYg>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(tile_floats(kHist, kMaxBins, TYg) * sizeof(float)));
         if (e != cudaSuccess) {
           cudaGetLastError();
           return e;
         }
-        attr_set[dev] = true;
+        attr_set[dev].store(true, std::memory_order_release);
       }
       const int tiles_x = (f.W + TX - 1) / TX, tiles_y = (f.y1 - f.y0 + TYg - 1) / TYg;
       const long long tiles = (long long)tiles_x * tiles_y;

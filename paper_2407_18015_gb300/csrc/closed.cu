@@ -10,6 +10,7 @@
 // parameters from shared memory (the neighbourhood access of the paper's
 // VTK-m worklet, Sec. "Integration with VTK-m and ParaView") and integrates
 // P_min / P_max exactly (device.cuh).
+#include <atomic>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -247,20 +248,22 @@ static bool launch_tile_tma(const Field &f, int tiles_x, int tiles, cudaStream_t
           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return false;
-  static bool attr_set[128] = {};
+  // per device: the attribute is set once (several host threads may race to
+  // set it; setting it twice is harmless, the flag itself is atomic)
+  static std::atomic<bool> attr_set[128] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) {
     cudaGetLastError();
     return false;
   }
-  if (!attr_set[dev]) {
+  if (!attr_set[dev].load(std::memory_order_acquire)) {
     if (cudaFuncSetAttribute(tile_kernel_tma<MODEL, SADDLE, TYm>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
         cudaSuccess) {
       cudaGetLastError();
       return false;
     }
-    attr_set[dev] = true;
+    attr_set[dev].store(true, std::memory_order_release);
   }
   Field g = f;
   g.tma_nc = nc;
@@ -277,12 +280,14 @@ static cudaError_t launch_tile_h(const Field &f, cudaStream_t s) {
   if constexpr (HistRows<MODEL, TYm>::value)
     smem = (size_t)((tile_floats(MODEL, f.B, TYm) + 3) & ~3LL) * sizeof(float) +
            (size_t)r4_floats(f.B, TYm) * sizeof(float);
-  static bool attr_set[128] = {};
+  // per device: the attribute is set once (several host threads may race to
+  // set it; setting it twice is harmless, the flag itself is atomic)
+  static std::atomic<bool> attr_set[128] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
-  if (!attr_set[dev]) {
+  if (!attr_set[dev].load(std::memory_order_acquire)) {
     // the largest tile of this model (64 bins; the histogram adds its tail
     // table, total, status and ordering scratch, the estimator its running
     // mass sums: 95 KB and 173 KB at 10 x 34), or the per-bin rows' bound
@@ -294,7 +299,7 @@ static cudaError_t launch_tile_h(const Field &f, cudaStream_t s) {
       cudaGetLastError();  // do not leave the failed call as the last error
       return e;
     }
-    attr_set[dev] = true;
+    attr_set[dev].store(true, std::memory_order_release);
   }
   Field g = f;
   g.vec4 = (f.ens != nullptr) && (f.W % 4 == 0) && ((reinterpret_cast<uintptr_t>(f.ens) & 15) == 0);
