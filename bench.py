@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-rows", action="store_true", help="headline workload only")
     ap.add_argument("--rows", default="mvn,fwdbwd,batch,saddle,gmm,stencil")
+    ap.add_argument("--batch-fields", type=int, default=64, help="fields of the batch row")
+    ap.add_argument("--batch-max", type=int, default=2048, help="largest field side of the batch row")
     return ap.parse_args()
 
 
@@ -547,7 +549,8 @@ def other_rows(torch, ucp, ctx, dev, args, flush, peaks):
             del params, grad
         del e4
     if "batch" in want:
-        rows["batch_64_fields"] = batch_row(torch, ucp, ctx, dev, steps, flush)
+        rows[f"batch_{args.batch_fields}_fields"] = batch_row(torch, ucp, ctx, dev, steps, flush,
+                                                              args.batch_fields, args.batch_max)
     if "saddle" in want:
         e2 = torch.from_numpy(synth.ensemble_bimodal(H2, W2, N2, seed=SEED2)).to(dev)
         out = torch.empty((H2, W2), device=dev)
@@ -635,12 +638,12 @@ def gmm_row(torch, ucp, ctx, dev, steps, flush):
     return out
 
 
-def batch_row(torch, ucp, ctx, dev, steps, flush):
-    """64 fields of uneven sizes (128^2..2048^2), N in {10,20,50,100}, mixed
-    models and types: 64 per-field launches vs one autotuned persistent launch
-    replayed from a CUDA graph."""
+def batch_row(torch, ucp, ctx, dev, steps, flush, nfields=64, largest=2048):
+    """nfields (64) fields of uneven sizes (128^2..largest^2, largest 2048),
+    N in {10,20,50,100}, mixed models and types: per-field launches vs one
+    autotuned persistent launch replayed from a CUDA graph."""
     from paper_2407_18015_gb300 import synth
-    specs = synth.batch_specs()
+    specs = synth.batch_specs(fields=nfields, hi=largest)
     fields = []
     verts = 0
     for sp in specs:
