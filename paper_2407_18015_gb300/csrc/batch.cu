@@ -339,7 +339,8 @@ int ucp_batch_tune(ucp_batch *batch, ucp_stream stream) {
     int best_th = batch->th[model];
     for (int th = 0; th < 3 && rc == UCP_OK; ++th) {
       int ths[3] = {th, th, th};
-      if ((rc = finalize(batch, sub, ths))) break;
+      rc = finalize(batch, sub, ths);
+      if (rc != UCP_OK) break;
       float t_min = 1e30f;
       for (int rep = 0; rep < 4 && rc == UCP_OK; ++rep) {  // first run warms up
         cudaEventRecord(e0, s);
