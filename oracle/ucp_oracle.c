@@ -412,7 +412,7 @@ static void vertex_min_max(const double *params, int H, int W, int model, int B,
   gather_params(params, plane, np, (int64_t)y * W + x, pv);
   st = dist_make(model, pv, B, &v);
   for (n = 0; n < k; ++n) {
-    double pn[2 + MAXB];
+    double pn[2 + MAXB] = {0};
     gather_params(params, plane, np, nidx[n], pn);
     st |= dist_make(model, pn, B, &nb[n]) & (ST_NONFINITE | ST_BAD_PARAMS);
   }
@@ -456,7 +456,7 @@ static double vertex_saddle(const double *params, int H, int W, int model, int B
   gather_params(params, plane, np, (int64_t)y * W + x, pv);
   st = dist_make(model, pv, B, &v);
   for (n = 0; n < k; ++n) {
-    double pn[2 + MAXB];
+    double pn[2 + MAXB] = {0};
     gather_params(params, plane, np, nidx[n], pn);
     st |= dist_make(model, pn, B, &nb[n]) & (ST_NONFINITE | ST_BAD_PARAMS);
   }
@@ -581,7 +581,7 @@ static void vertex_min_max_stencil(const double *params, int D, int H, int W, in
   int off[MAXK][3], kfull = stencil_offsets(stencil, off), k = 0, n, st;
   int z = (int)(i / ((int64_t)H * W)), y = (int)((i / W) % H), x = (int)(i % W);
   int np = nparams(model, B);
-  double pv[2 + MAXB];
+  double pv[2 + MAXB] = {0};
   dist_t v, nb[MAXK];
   for (n = 0; n < kfull; ++n) {
     int zz = z + off[n][0], yy = y + off[n][1], xx = x + off[n][2];
@@ -591,7 +591,7 @@ static void vertex_min_max_stencil(const double *params, int D, int H, int W, in
   gather_params(params, plane, np, i, pv);
   st = dist_make(model, pv, B, &v);
   for (n = 0; n < k; ++n) {
-    double pn[2 + MAXB];
+    double pn[2 + MAXB] = {0};
     gather_params(params, plane, np, nidx[n], pn);
     st |= dist_make(model, pn, B, &nb[n]) & (ST_NONFINITE | ST_BAD_PARAMS);
   }
