@@ -238,10 +238,12 @@ int ucp_saddle_from_params(ucp_ctx *ctx, const float *params, int H, int W,
                            uint8_t *vertex_status, ucp_stream stream);
 
 /* Same as ucp_probability with HOST arrays: copies ens_host to a
- * context-owned device buffer, computes, copies the fields back and
- * synchronises the stream before returning.  Pinned host memory gives the
- * full copy bandwidth; pageable memory works too.  out_min_host /
- * out_max_host follow cptypes; status_host may be NULL. */
+ * context-owned device buffer in row strips overlapped with the computation,
+ * copies the fields back and returns once the context's streams are
+ * synchronised (the work starts after what is queued on `stream`).  Pinned
+ * host memory gives the full copy bandwidth; pageable memory works too.
+ * out_min_host / out_max_host follow cptypes; status_host may be NULL.  The
+ * one-model case of ucp_probability_host_models. */
 int ucp_probability_host(ucp_ctx *ctx, const float *ens_host, int N, int H, int W,
                          const ucp_model_desc *desc, unsigned cptypes, float *out_min_host,
                          float *out_max_host, uint8_t *status_host, ucp_stream stream);
