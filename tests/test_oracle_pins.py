@@ -449,6 +449,117 @@ def test_gradient_matches_central_differences(orc, model, cptype):
     assert worst < 2e-6
 
 
+def _fd_check(orc, p, model, W, cptype, bins, boundary, skip=(), h=1e-6):
+    """Central differences of the loss against orc.grad at every parameter
+    (q, y, x) not in `skip`; returns the worst relative difference and the
+    gradient."""
+    g = orc.grad(p, model, W, cptype=cptype, bins=bins, boundary=boundary)
+    off = 2 if model == 2 else 0
+    worst = 0.0
+
+    def loss(pp):
+        pmin, pmax, _ = orc.prob(pp, model, bins=bins, boundary=boundary)
+        return float(((pmin if cptype == 1 else pmax) * W).sum())
+    for q in range(g.shape[0]):
+        for y in range(p.shape[1]):
+            for x in range(p.shape[2]):
+                if (q, y, x) in skip:
+                    continue
+                pp = p.copy()
+                pm = p.copy()
+                pp[off + q, y, x] += h
+                pm[off + q, y, x] -= h
+                fd = (loss(pp) - loss(pm)) / (2 * h)
+                worst = max(worst, abs(fd - g[q, y, x]) / (1 + abs(fd)))
+    return worst, g
+
+
+@pytest.mark.parametrize("model", [0, 1, 2])
+@pytest.mark.parametrize("cptype", [1, 2])
+def test_gradient_boundary_zero_mode_matches_central_differences(orc, model, cptype):
+    """Boundary mode 1 writes P = 0 at every vertex with fewer than four
+    neighbours, so those vertices drop out of the loss; a vertex on the
+    boundary still has gradient through its interior neighbours.  A skip
+    keyed on the wrong vertex (u's neighbour count instead of v's) changes
+    the gradient of every boundary vertex and fails here."""
+    rng = np.random.default_rng(140 + 3 * model + cptype)
+    bins = 4
+    p = H_.random_params(model, 5, 6, rng, bins=bins)
+    W = rng.uniform(0.5, 1, (5, 6))
+    worst, g = _fd_check(orc, p, model, W, cptype, bins, boundary=1)
+    assert worst < 2e-6
+    # the corner has no interior neighbour on a 5 x 6 grid: zero gradient
+    assert np.all(g[:, 0, 0] == 0.0) and np.all(g[:, -1, -1] == 0.0)
+    # edge vertices next to interior ones do have gradients
+    edge = np.concatenate([g[:, 0, 1:-1], g[:, -1, 1:-1], g[:, 1:-1, 0], g[:, 1:-1, -1]], 1)
+    assert np.abs(edge).max() > 1e-3
+    # and they differ from mode 0 (the edge vertices' own P is dropped)
+    g0 = orc.grad(p, model, W, cptype=cptype, bins=bins, boundary=0)
+    assert np.abs(g0[:, 0, :] - g[:, 0, :]).max() > 1e-3
+
+
+def _point_mass_grid(model, rng, bins):
+    """A 6 x 7 grid with point masses at an interior vertex, an edge
+    vertex, a corner and two adjacent interior vertices (so that a point
+    mass is both a centre and a neighbour of a point mass)."""
+    p = H_.random_params(model, 6, 7, rng, bins=bins)
+    sites = ((2, 3), (0, 4), (0, 0), (4, 1), (4, 2))
+    for (y, x) in sites:
+        if model == 1:
+            p[1, y, x] = 0.0
+        else:
+            p[1, y, x] = p[0, y, x]
+    return p, sites
+
+
+@pytest.mark.parametrize("model", [0, 1, 2])
+@pytest.mark.parametrize("cptype", [1, 2])
+def test_gradient_point_masses_match_central_differences(orc, model, cptype):
+    """Point masses (all members equal) as centres and as neighbours.
+    Histogram: P is linear in every vertex's masses, point masses
+    included, so central differences are exact to rounding for every mass
+    (a wrong sign in the point-mass neighbour factor [x < c] / [x > c]
+    fails here).  Uniform / Epanechnikov: every parameter of the other
+    vertices is checked by central differences; the point mass's own
+    support parameters are not differentiable there (a > b and w < 0 are
+    invalid, so only one side exists) and the reading is that their
+    derivative is 0, which is asserted exactly."""
+    rng = np.random.default_rng(150 + 3 * model + cptype)
+    bins = 4
+    p, sites = _point_mass_grid(model, rng, bins)
+    W = rng.uniform(0.5, 1, (6, 7))
+    nq = bins if model == 2 else 2
+    skip = () if model == 2 else {(q, y, x) for (y, x) in sites for q in range(nq)}
+    worst, g = _fd_check(orc, p, model, W, cptype, bins, boundary=0, skip=skip)
+    assert worst < 2e-6
+    if model != 2:
+        for (y, x) in sites:
+            assert np.all(g[:, y, x] == 0.0)
+    else:
+        # a point-mass centre's mass derivative is the product of the
+        # neighbours' strict tails at its position; it is not zero here
+        assert np.abs(g[:, 2, 3]).max() > 1e-3
+
+
+def test_gradient_point_mass_histogram_closed_form(orc):
+    """Hand-built 1 x 3 histogram line: a point mass c = 0.5 of total mass
+    T between two one-bin histograms U[0, 1] (mass s) and U[0.25, 1.25]
+    (mass r).  P_min(centre) = T * s * (1 - 0.5) * r * (1.25 - 0.5) / 1, so
+    dP/dT = 0.375 s r, dP/ds = 0.375 T r, dP/dr = 0.375 T s; with weight 1 on
+    the centre only."""
+    T, s, r = 0.7, 1.3, 0.9
+    p = np.array([[[0.0, 0.5, 0.25]], [[1.0, 0.5, 1.25]], [[s, T, r]]])
+    W = np.array([[0.0, 1.0, 0.0]])
+    g = orc.grad(p, 2, W, cptype=1, bins=1)
+    assert abs(orc.prob(p, 2, bins=1)[0][0, 1] - 0.375 * T * s * r) < 1e-15
+    np.testing.assert_allclose(g[0, 0], [0.375 * T * r, 0.375 * s * r, 0.375 * T * s],
+                               rtol=0, atol=1e-15)
+    # maximum: Pr[X_l < c] = 0.5 s, Pr[X_r < c] = 0.25 r
+    g = orc.grad(p, 2, W, cptype=2, bins=1)
+    np.testing.assert_allclose(g[0, 0], [0.125 * T * r, 0.125 * s * r, 0.125 * T * s],
+                               rtol=0, atol=1e-15)
+
+
 def test_gradient_identities(orc):
     """Translation and scale invariance of each P_v (all five participants
     shifted/scaled together) and Euler's identity for histogram masses."""
