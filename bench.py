@@ -180,6 +180,10 @@ MVN_OPS_PER_SAMPLE = 250
 # integral and one leave-one-out product integral per neighbour, each counted
 # as a forward piece integral.
 ADJ_HIST_FLOPS_PER_PIECE = 5 * HIST_FLOPS_PER_PIECE_TYPE
+# Epanechnikov adjoint of P_min: per vertex the derivative integrals with
+# respect to (m, w) of the centre and of each of the four neighbours, ten
+# integrals, each counted as one forward vertex integral of one type.
+ADJ_EPAN_FLOPS_PER_VERTEX = 10 * EPAN_FLOPS_PER_VERTEX_TYPE
 
 
 # DRAM bytes (read + write) per launch of each headline kernel from the ncu
@@ -265,9 +269,10 @@ def cpu_baseline_headline(ens_np):
             "sample": "the full 1024x1024x20 field, all three models, min and max, once"}
 
 
-def oracle_mvn_rate(ens_np, crop=48, samples=10000):
-    """The oracle's Monte Carlo (FP64, same Philox stream contract) on a crop
-    of the workload: vertices/s and samples/s on the host cores."""
+def oracle_mvn_rate(ens_np, crop=128, samples=10000):
+    """The oracle's Monte Carlo (FP64, same Philox stream contract) on a
+    crop of the workload: vertices/s and samples/s on the host cores, and
+    the full field's time extrapolated from them (labelled as such)."""
     import oracle
     oracle.build()
     sub = np.ascontiguousarray(ens_np[:, :crop, :crop])
@@ -275,16 +280,22 @@ def oracle_mvn_rate(ens_np, crop=48, samples=10000):
     p, _ = oracle.fit(sub, oracle.MVN)
     oracle.mvn_mc_at(p, np.arange(crop * crop), samples, 0x5EED)
     dt = time.perf_counter() - t
+    full = ens_np.shape[1] * ens_np.shape[2]
     return {"vertices_per_s": crop * crop / dt, "samples_per_s": crop * crop * samples / dt,
             "cores": oracle.get_threads(), "seconds": dt,
-            "sample": f"a {crop}x{crop} crop (its own boundary), fit + {samples} samples each"}
+            "full_field_seconds_extrapolated": full / (crop * crop / dt),
+            "sample": f"a {crop}x{crop} crop (its own boundary), fit + {samples} samples each; "
+                      "the full-field time is extrapolated by vertex count"}
 
 
-def oracle_fwd_bwd_rate(e4, weight, model, bins, rows=32):
-    """The oracle's fit, probability and analytic gradient on a strip of the
-    2048x2048x50 workload: forward and forward + adjoint vertices/s."""
+def oracle_fwd_bwd_rate(e4, weight, model, bins, rows=None):
+    """The oracle's fit, probability and analytic gradient on the 2048x2048x50
+    workload: the full field (rows=None) or a strip of `rows` rows, whose
+    rates are extrapolated to the full field by vertex count (labelled)."""
     import oracle
     oracle.build()
+    Hh, Ww = weight.shape
+    rows = Hh if rows is None else rows
     strip = np.ascontiguousarray(e4[:, :rows, :].cpu().numpy())
     wt = np.ascontiguousarray(weight[:rows, :].cpu().numpy())
     mid = {"uniform": 0, "epanechnikov": 1, "histogram": 2}[model]
@@ -294,11 +305,17 @@ def oracle_fwd_bwd_rate(e4, weight, model, bins, rows=32):
     t1 = time.perf_counter()
     oracle.grad(p, mid, wt, cptype=1, bins=bins or 8)
     t2 = time.perf_counter()
-    n = rows * strip.shape[2]
-    return {"fwd_vertices_per_s": n / (t1 - t), "fwd_bwd_vertices_per_s": n / (t2 - t),
-            "cores": oracle.get_threads(), "seconds": t2 - t,
-            "sample": f"{rows} rows of the 2048x2048 field (fit, P_min and P_max, gradient of "
-                      "sum W P_min)"}
+    n = rows * Ww
+    out = {"fwd_vertices_per_s": n / (t1 - t), "fwd_bwd_vertices_per_s": n / (t2 - t),
+           "cores": oracle.get_threads(), "seconds": t2 - t}
+    if rows == Hh:
+        out["sample"] = ("the full 2048x2048 field (fit, P_min and P_max, gradient of "
+                         "sum W P_min)")
+    else:
+        out["full_field_seconds_extrapolated"] = (t2 - t) * Hh / rows
+        out["sample"] = (f"{rows} of the 2048 rows (fit, P_min and P_max, gradient of sum W "
+                         "P_min); full-field rates extrapolated by vertex count")
+    return out
 
 
 class L2Flush:
@@ -447,11 +464,45 @@ def run_ours(args):
         line["cpu_baseline"] = cpu_baseline_headline(ens_np) if world == 1 else None
         if not args.no_rows:
             line["rows"] = other_rows(torch, ucp, ctx, dev, args, flush, peaks)
+        line["summary"] = summarise(line)
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def _g(x):
+    return None if x is None else float(f"{x:.3g}")
+
+
+def summarise(line):
+    """A compact digest of the line (ms, vertices/s and roofline fraction per
+    kernel and row), placed last so that it survives a truncated tail."""
+    out = {"headline": {"ms": _g(line["ms_per_step"]), "vps": _g(line["value"]),
+                        "frac": _g(line["roofline"]["frac"]),
+                        "e2e_vps": _g(line.get("e2e", {}).get("value"))}}
+    for m, r in line.get("per_model", {}).items():
+        out[m] = {"ms": _g(r["ms"]), "vps": _g(r["vertices_per_s"]),
+                  "frac": _g(r["roofline"]["frac"]), "bound": r["roofline"]["bound"]}
+    for name, r in (line.get("rows") or {}).items():
+        d = {}
+        for k in ("ms", "ms_fwd", "ms_adjoint", "ms_fwd_bwd", "ms_batched_graph",
+                  "ms_per_field_launches", "speedup", "vertices_per_s", "fwd_vertices_per_s",
+                  "fwd_bwd_vertices_per_s", "batched_vertices_per_s"):
+            if isinstance(r.get(k), (int, float)):
+                d[k] = _g(r[k])
+        for k in ("roofline", "fwd_roofline_hbm", "fwd_roofline_fp32", "adjoint_roofline"):
+            if isinstance(r.get(k), dict):
+                d[k + "_frac"] = _g(r[k]["frac"])
+        if isinstance(r.get("oracle"), dict):
+            o = r["oracle"]
+            d["oracle_vps"] = _g(o.get("fwd_bwd_vertices_per_s", o.get("vertices_per_s")))
+        if d:
+            out[name] = d
+    if isinstance(line.get("cpu_baseline"), dict):
+        out["cpu_baseline_vps"] = _g(line["cpu_baseline"]["value"])
+    return out
 
 
 def e2e_headline(torch, ucp, ctx, ens_np, args):
@@ -511,7 +562,10 @@ def other_rows(torch, ucp, ctx, dev, args, flush, peaks):
     if "fwdbwd" in want:
         e4 = torch.from_numpy(synth.ensemble_bimodal(2048, 2048, 50, seed=4)).to(dev)
         Wt = torch.from_numpy(synth.weight_field(2048, 2048, seed=44)).to(dev)
-        for m, b in (("histogram", 16), ("epanechnikov", 0)):
+        HW4, N4 = 2048 * 2048, 50
+        fp32 = fp32_peak_tflops(peaks["sm_max_mhz"])
+        fp32_src = f"152 SMs x 128 FP32 lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz (derived)"
+        for m, b in (("histogram", 16), ("epanechnikov", 0), ("uniform", 0)):
             d = ucp.make_desc(m, bins=b or 8)
             params = ctx.fit(e4, d)
             pmin = torch.empty((2048, 2048), device=dev)
@@ -525,32 +579,64 @@ def other_rows(torch, ucp, ctx, dev, args, flush, peaks):
 
             def fw(ev, d=d, pmin=pmin):
                 ucp.ucp_probability(ctx.handle, e4, d, ucp.UCP_MIN, pmin, None)
+
             def bw(ev, d=d, params=params, grad=grad):
                 ucp.ucp_backward(ctx.handle, params, d, ucp.UCP_MIN, Wt, grad)
             ms_fb, _ = timed_steps(torch, fb, steps, 2, flush)
             ms_fw, _ = timed_steps(torch, fw, steps, 2, flush)
             ms_bw, _ = timed_steps(torch, bw, steps, 2, flush)
+            ms_fb, ms_fw, ms_bw = ms_fb / steps, ms_fw / steps, ms_bw / steps
+            # forward (fused fit + P_min): members read once, one field written
+            fwd_bytes = (4.0 * N4 + 4.0) * HW4
+            hbm = fwd_bytes / (ms_fw / 1e3) / 1e9
             row = {
-                "ms_fwd_bwd": ms_fb / steps,
-                "fwd_bwd_vertices_per_s": 2048 * 2048 / (ms_fb / steps / 1e3),
-                "ms_fwd": ms_fw / steps,
-                "fwd_vertices_per_s": 2048 * 2048 / (ms_fw / steps / 1e3),
-                "ms_adjoint": ms_bw / steps,
-                "oracle": oracle_fwd_bwd_rate(e4, Wt, m, b)}
+                "ms_fwd_bwd": ms_fb, "fwd_bwd_vertices_per_s": HW4 / (ms_fb / 1e3),
+                "ms_fwd": ms_fw, "fwd_vertices_per_s": HW4 / (ms_fw / 1e3),
+                "ms_adjoint": ms_bw,
+                "fwd_roofline_hbm": {"bound": "hbm", "achieved": hbm, "peak": peaks["hbm_gbs"],
+                                     "unit": "GB/s", "frac": hbm / peaks["hbm_gbs"],
+                                     "work": f"{4 * N4 + 4} bytes per vertex (members + P_min)",
+                                     "peak_source": "MEASURED_PEAKS.json hbm_gbs"}}
             if m == "histogram":
                 pieces = float(hist_piece_counts(params, b).sum().item())
-                ach = pieces * ADJ_HIST_FLOPS_PER_PIECE / (ms_bw / steps / 1e3) / 1e12
-                pk = fp32_peak_tflops(peaks["sm_max_mhz"])
+                fl = pieces * HIST_FLOPS_PER_PIECE_TYPE / (ms_fw / 1e3) / 1e12
+                row["fwd_roofline_fp32"] = {
+                    "bound": "alu", "achieved": fl, "peak": fp32, "unit": "TFLOP/s",
+                    "frac": fl / fp32, "work": f"{HIST_FLOPS_PER_PIECE_TYPE} flops per merged "
+                    "piece (one type)", "peak_source": fp32_src}
+                ach = pieces * ADJ_HIST_FLOPS_PER_PIECE / (ms_bw / 1e3) / 1e12
                 row["adjoint_roofline"] = {
-                    "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
-                    "frac": ach / pk, "work": f"{ADJ_HIST_FLOPS_PER_PIECE} flops per merged piece",
-                    "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz"}
+                    "bound": "alu", "achieved": ach, "peak": fp32, "unit": "TFLOP/s",
+                    "frac": ach / fp32, "work": f"{ADJ_HIST_FLOPS_PER_PIECE} flops per merged piece",
+                    "peak_source": fp32_src}
+                row["oracle"] = oracle_fwd_bwd_rate(e4, Wt, m, b, rows=128)
+            elif m == "epanechnikov":
+                fl = HW4 * EPAN_FLOPS_PER_VERTEX_TYPE / (ms_fw / 1e3) / 1e12
+                row["fwd_roofline_fp32"] = {
+                    "bound": "alu", "achieved": fl, "peak": fp32, "unit": "TFLOP/s",
+                    "frac": fl / fp32, "work": f"{EPAN_FLOPS_PER_VERTEX_TYPE} flops per vertex "
+                    "(one type)", "peak_source": fp32_src}
+                ach = HW4 * ADJ_EPAN_FLOPS_PER_VERTEX / (ms_bw / 1e3) / 1e12
+                row["adjoint_roofline"] = {
+                    "bound": "alu", "achieved": ach, "peak": fp32, "unit": "TFLOP/s",
+                    "frac": ach / fp32, "work": f"{ADJ_EPAN_FLOPS_PER_VERTEX} flops per vertex "
+                    "(ten derivative integrals)", "peak_source": fp32_src}
+                row["oracle"] = oracle_fwd_bwd_rate(e4, Wt, m, b)
+            else:
+                # adjoint: params (2 planes) and W read, 2 gradient planes written
+                bw_bytes = 4.0 * (2 + 1 + 2) * HW4
+                a = bw_bytes / (ms_bw / 1e3) / 1e9
+                row["adjoint_roofline"] = {
+                    "bound": "hbm", "achieved": a, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": a / peaks["hbm_gbs"], "work": "20 bytes per vertex",
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
             rows[f"fwd_bwd_2048x2048x50_{m}{b or ''}"] = row
             del params, grad
         del e4
     if "batch" in want:
         rows[f"batch_{args.batch_fields}_fields"] = batch_row(torch, ucp, ctx, dev, steps, flush,
-                                                              args.batch_fields, args.batch_max)
+                                                              args.batch_fields, args.batch_max,
+                                                              peaks)
     if "saddle" in want:
         e2 = torch.from_numpy(synth.ensemble_bimodal(H2, W2, N2, seed=SEED2)).to(dev)
         out = torch.empty((H2, W2), device=dev)
@@ -638,7 +724,30 @@ def gmm_row(torch, ucp, ctx, dev, steps, flush):
     return out
 
 
-def batch_row(torch, ucp, ctx, dev, steps, flush, nfields=64, largest=2048):
+def batch_ideal_seconds(torch, ucp, ctx, fields, peaks):
+    """The batch's roofline time: per field the larger of its HBM time
+    (members read once, one probability field written) and its FP32 time
+    (the per-unit flop figures of the tile kernels: Epanechnikov per vertex,
+    histogram per merged piece; uniform has none), summed over the fields."""
+    fp32 = fp32_peak_tflops(peaks["sm_max_mhz"]) * 1e12
+    hbm = peaks["hbm_gbs"] * 1e9
+    total = 0.0
+    for ens, desc, cp, o in fields:
+        N, Hh, Ww = ens.shape
+        byt = (4.0 * N + 4.0) * Hh * Ww
+        if desc.model == ucp.UCP_EPANECHNIKOV:
+            fl = EPAN_FLOPS_PER_VERTEX_TYPE * Hh * Ww
+        elif desc.model == ucp.UCP_HISTOGRAM:
+            params = ctx.fit(ens, desc)
+            fl = HIST_FLOPS_PER_PIECE_TYPE * float(hist_piece_counts(params, desc.bins).sum().item())
+            del params
+        else:
+            fl = 0.0
+        total += max(byt / hbm, fl / fp32)
+    return total
+
+
+def batch_row(torch, ucp, ctx, dev, steps, flush, nfields=64, largest=2048, peaks=None):
     """nfields (64) fields of uneven sizes (128^2..largest^2, largest 2048),
     N in {10,20,50,100}, mixed models and types: per-field launches vs one
     autotuned persistent launch replayed from a CUDA graph."""
@@ -673,10 +782,19 @@ def batch_row(torch, ucp, ctx, dev, steps, flush, nfields=64, largest=2048):
     b.close()
     ms_pf /= steps
     ms_b /= steps
-    return {"fields": len(fields), "vertices": verts, "ms_per_field_launches": ms_pf,
-            "ms_batched_graph": ms_b, "speedup": ms_pf / ms_b,
-            "batched_vertices_per_s": verts / (ms_b / 1e3),
-            "per_field_vertices_per_s": verts / (ms_pf / 1e3)}
+    out = {"fields": len(fields), "vertices": verts, "ms_per_field_launches": ms_pf,
+           "ms_batched_graph": ms_b, "speedup": ms_pf / ms_b,
+           "batched_vertices_per_s": verts / (ms_b / 1e3),
+           "per_field_vertices_per_s": verts / (ms_pf / 1e3)}
+    if peaks is not None:
+        ideal = batch_ideal_seconds(torch, ucp, ctx, fields, peaks)
+        out["roofline"] = {
+            "bound": "mixed", "achieved_ms": ms_b, "roofline_ms": ideal * 1e3,
+            "frac": ideal * 1e3 / ms_b,
+            "work": "per field max(HBM time of (4N+4) bytes per vertex, FP32 time of the tile "
+                    "kernels' flop figures), summed",
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs; FP32 152 x 128 x 2 x max SM clock"}
+    return out
 
 
 def main():

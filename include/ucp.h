@@ -318,7 +318,12 @@ int ucp_backward(ucp_ctx *ctx, const float *params, int H, int W, const ucp_mode
  * array's device address (once, with that device current); make that first
  * call before any stream capture.  All calls on a device share the array:
  * calls that can overlap on the GPU (unordered streams) race on it.  It keeps
- * the last call's contents; no part of it needs to start at zero. */
+ * the last call's contents; no part of it needs to start at zero.  The
+ * looked-up address is kept for the life of the process: do not call this
+ * entry point on a device after cudaDeviceReset (or any other reset of its
+ * primary context) in the same process, since the array then lives at a new
+ * address.  Argument checks (and their status codes) are those of
+ * ucp_backward. */
 size_t ucp_backward_static_capacity(void);
 int ucp_backward_static(const float *params, int H, int W, const ucp_model_desc *desc,
                         int cptype, const float *weight, float *grad_params, ucp_stream stream);

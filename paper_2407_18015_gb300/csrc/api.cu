@@ -41,7 +41,25 @@ struct DeviceGuard {
   }
 };
 
-int valid_desc(const ucp_model_desc *d, bool allow_sampled) {
+// the larger-stencil path (stencil.cu) instead of the four-neighbour one
+bool uses_stencil(const ucp_model_desc *d) { return d->stencil != UCP_STENCIL_4; }
+
+int slices(const ucp_model_desc *d) { return d->depth > 1 ? d->depth : 1; }
+
+int valid_types(unsigned cptypes, const float *out_min, const float *out_max) {
+  if (cptypes == 0 || (cptypes & ~3u)) return UCP_ERR_ARG;
+  if ((cptypes & 1u) && !out_min) return UCP_ERR_ARG;
+  if ((cptypes & 2u) && !out_max) return UCP_ERR_ARG;
+  return UCP_OK;
+}
+
+float epan_scale(const ucp_model_desc *d) {
+  return d->epan_width_scale > 0.f ? d->epan_width_scale : 2.2360679774997896f;
+}
+
+}  // namespace
+
+int ucp_valid_desc(const ucp_model_desc *d, bool allow_sampled) {
   if (!d) return UCP_ERR_ARG;
   if (d->model < UCP_UNIFORM || d->model > UCP_GAUSSIAN) return UCP_ERR_ARG;
   const bool sampled = d->model == UCP_MVN_MC || d->model == UCP_HISTOGRAM_SEMI;
@@ -58,12 +76,7 @@ int valid_desc(const ucp_model_desc *d, bool allow_sampled) {
   return UCP_OK;
 }
 
-// the larger-stencil path (stencil.cu) instead of the four-neighbour one
-bool uses_stencil(const ucp_model_desc *d) { return d->stencil != UCP_STENCIL_4; }
-
-int slices(const ucp_model_desc *d) { return d->depth > 1 ? d->depth : 1; }
-
-int valid_shape(long long N, long long H, long long W) {
+int ucp_valid_shape(long long N, long long H, long long W) {
   if (N < 1 || H < 1 || W < 1) return UCP_ERR_SHAPE;
   // vertex indices are 32-bit (Philox counter word 1); members 64-bit
   if (H * W > 0xFFFFFFFFLL) return UCP_ERR_SHAPE;
@@ -71,18 +84,15 @@ int valid_shape(long long N, long long H, long long W) {
   return UCP_OK;
 }
 
-int valid_types(unsigned cptypes, const float *out_min, const float *out_max) {
-  if (cptypes == 0 || (cptypes & ~3u)) return UCP_ERR_ARG;
-  if ((cptypes & 1u) && !out_min) return UCP_ERR_ARG;
-  if ((cptypes & 2u) && !out_max) return UCP_ERR_ARG;
-  return UCP_OK;
+// the checks ucp_backward and ucp_backward_static share, before any CUDA call
+int ucp_valid_backward(const ucp_model_desc *desc, int cptype, int H, int W) {
+  int rc = ucp_valid_desc(desc, false);
+  if (rc) return rc;
+  if (desc->model == UCP_GAUSSIAN) return UCP_ERR_UNSUPPORTED;
+  if (desc->stencil != UCP_STENCIL_4) return UCP_ERR_UNSUPPORTED;
+  if (cptype != UCP_MIN && cptype != UCP_MAX) return UCP_ERR_ARG;
+  return ucp_valid_shape(1, H, W);
 }
-
-float epan_scale(const ucp_model_desc *d) {
-  return d->epan_width_scale > 0.f ? d->epan_width_scale : 2.2360679774997896f;
-}
-
-}  // namespace
 
 int ucp_set_error(ucp_ctx *ctx, cudaError_t e) {
   if (e == cudaSuccess) return UCP_OK;
@@ -116,7 +126,7 @@ const char *ucp_status_string(int status) {
 const char *ucp_version(void) { return "ucp 1.0"; }
 
 int ucp_param_count(const ucp_model_desc *desc) {
-  if (valid_desc(desc, true) != UCP_OK) return 0;
+  if (ucp_valid_desc(desc, true) != UCP_OK) return 0;
   return param_planes(desc->model, desc->bins);
 }
 
@@ -172,9 +182,9 @@ const char *ucp_last_error(const ucp_ctx *ctx) { return ctx ? ctx->last_error : 
 int ucp_fit(ucp_ctx *ctx, const float *ens, int N, int H, int W, const ucp_model_desc *desc,
             float *params, uint8_t *vertex_status, ucp_stream stream) {
   if (!ctx || !ens || !params) return UCP_ERR_ARG;
-  int rc = valid_desc(desc, true);
+  int rc = ucp_valid_desc(desc, true);
   if (rc) return rc;
-  if ((rc = valid_shape(N, (long long)slices(desc) * H, W))) return rc;
+  if ((rc = ucp_valid_shape(N, (long long)slices(desc) * H, W))) return rc;
   H *= slices(desc);  // the fit is per vertex: D slices are D * H rows
   DeviceGuard g(ctx->device);
   if (g.err != cudaSuccess) return ucp_set_error(ctx, g.err);
@@ -270,9 +280,9 @@ int ucp_probability_from_params(ucp_ctx *ctx, const float *params, int H, int W,
                                 const ucp_model_desc *desc, unsigned cptypes, float *out_min,
                                 float *out_max, uint8_t *vertex_status, ucp_stream stream) {
   if (!ctx || !params) return UCP_ERR_ARG;
-  int rc = valid_desc(desc, true);
+  int rc = ucp_valid_desc(desc, true);
   if (rc) return rc;
-  if ((rc = valid_shape(1, (long long)slices(desc) * H, W))) return rc;
+  if ((rc = ucp_valid_shape(1, (long long)slices(desc) * H, W))) return rc;
   if ((rc = valid_types(cptypes, out_min, out_max))) return rc;
   DeviceGuard g(ctx->device);
   if (g.err != cudaSuccess) return ucp_set_error(ctx, g.err);
@@ -287,9 +297,9 @@ int ucp_probability(ucp_ctx *ctx, const float *ens, int N, int H, int W,
                     const ucp_model_desc *desc, unsigned cptypes, float *out_min, float *out_max,
                     uint8_t *vertex_status, ucp_stream stream) {
   if (!ctx || !ens) return UCP_ERR_ARG;
-  int rc = valid_desc(desc, true);
+  int rc = ucp_valid_desc(desc, true);
   if (rc) return rc;
-  if ((rc = valid_shape(N, (long long)slices(desc) * H, W))) return rc;
+  if ((rc = ucp_valid_shape(N, (long long)slices(desc) * H, W))) return rc;
   if ((rc = valid_types(cptypes, out_min, out_max))) return rc;
   DeviceGuard g(ctx->device);
   if (g.err != cudaSuccess) return ucp_set_error(ctx, g.err);
@@ -329,10 +339,10 @@ static int saddle_impl(ucp_ctx *ctx, const float *ens, const float *params, int 
 int ucp_saddle(ucp_ctx *ctx, const float *ens, int N, int H, int W, const ucp_model_desc *desc,
                float *out_saddle, uint8_t *vertex_status, ucp_stream stream) {
   if (!ctx || !ens || !out_saddle) return UCP_ERR_ARG;
-  int rc = valid_desc(desc, true);
+  int rc = ucp_valid_desc(desc, true);
   if (rc) return rc;
   if (uses_stencil(desc)) return UCP_ERR_UNSUPPORTED;
-  if ((rc = valid_shape(N, H, W))) return rc;
+  if ((rc = ucp_valid_shape(N, H, W))) return rc;
   DeviceGuard g(ctx->device);
   if (g.err != cudaSuccess) return ucp_set_error(ctx, g.err);
   return saddle_impl(ctx, ens, nullptr, N, H, W, desc, out_saddle, vertex_status,
@@ -343,10 +353,10 @@ int ucp_saddle_from_params(ucp_ctx *ctx, const float *params, int H, int W,
                            const ucp_model_desc *desc, float *out_saddle,
                            uint8_t *vertex_status, ucp_stream stream) {
   if (!ctx || !params || !out_saddle) return UCP_ERR_ARG;
-  int rc = valid_desc(desc, true);
+  int rc = ucp_valid_desc(desc, true);
   if (rc) return rc;
   if (uses_stencil(desc)) return UCP_ERR_UNSUPPORTED;
-  if ((rc = valid_shape(1, H, W))) return rc;
+  if ((rc = ucp_valid_shape(1, H, W))) return rc;
   DeviceGuard g(ctx->device);
   if (g.err != cudaSuccess) return ucp_set_error(ctx, g.err);
   return saddle_impl(ctx, nullptr, params, 1, H, W, desc, out_saddle, vertex_status,
@@ -357,10 +367,10 @@ int ucp_probability_host(ucp_ctx *ctx, const float *ens_host, int N, int H, int 
                          const ucp_model_desc *desc, unsigned cptypes, float *out_min_host,
                          float *out_max_host, uint8_t *status_host, ucp_stream stream) {
   if (!ctx || !ens_host) return UCP_ERR_ARG;
-  int rc = valid_desc(desc, true);
+  int rc = ucp_valid_desc(desc, true);
   if (rc) return rc;
   if (uses_stencil(desc)) return UCP_ERR_UNSUPPORTED;
-  if ((rc = valid_shape(N, H, W))) return rc;
+  if ((rc = ucp_valid_shape(N, H, W))) return rc;
   if ((rc = valid_types(cptypes, out_min_host, out_max_host))) return rc;
   DeviceGuard g(ctx->device);
   if (g.err != cudaSuccess) return ucp_set_error(ctx, g.err);
@@ -374,11 +384,11 @@ int ucp_probability_models(ucp_ctx *ctx, const float *ens, int N, int H, int W,
                            uint8_t *const *vertex_status, ucp_stream stream) {
   if (!ctx || !ens || !descs || !out_min || !out_max) return UCP_ERR_ARG;
   if (nmodels < 1 || nmodels > UCP_MAX_MODELS) return UCP_ERR_ARG;
-  int rc = valid_shape(N, H, W);
+  int rc = ucp_valid_shape(N, H, W);
   if (rc) return rc;
   if (cptypes == 0 || (cptypes & ~3u)) return UCP_ERR_ARG;
   for (int m = 0; m < nmodels; ++m) {
-    if ((rc = valid_desc(descs + m, true))) return rc;
+    if ((rc = ucp_valid_desc(descs + m, true))) return rc;
     if (uses_stencil(descs + m)) return UCP_ERR_UNSUPPORTED;
   }
   DeviceGuard g(ctx->device);
@@ -411,11 +421,11 @@ int ucp_probability_host_models(ucp_ctx *ctx, const float *ens_host, int N, int 
                                 uint8_t *const *status_host, ucp_stream stream) {
   if (!ctx || !ens_host || !descs || !out_min_host || !out_max_host) return UCP_ERR_ARG;
   if (nmodels < 1 || nmodels > UCP_MAX_MODELS) return UCP_ERR_ARG;
-  int rc = valid_shape(N, H, W);
+  int rc = ucp_valid_shape(N, H, W);
   if (rc) return rc;
   if (cptypes == 0 || (cptypes & ~3u)) return UCP_ERR_ARG;
   for (int m = 0; m < nmodels; ++m) {
-    if ((rc = valid_desc(descs + m, true))) return rc;
+    if ((rc = ucp_valid_desc(descs + m, true))) return rc;
     if (uses_stencil(descs + m)) return UCP_ERR_UNSUPPORTED;
   }
   DeviceGuard g(ctx->device);
@@ -428,7 +438,7 @@ int ucp_params_from_error_bound(ucp_ctx *ctx, const float *decompressed, float e
                                 int W, float *params, ucp_stream stream) {
   if (!ctx || !decompressed || !params) return UCP_ERR_ARG;
   if (!(eb >= 0.f) || !isfinite(eb)) return UCP_ERR_ARG;
-  int rc = valid_shape(1, H, W);
+  int rc = ucp_valid_shape(1, H, W);
   if (rc) return rc;
   DeviceGuard g(ctx->device);
   if (g.err != cudaSuccess) return ucp_set_error(ctx, g.err);
@@ -439,12 +449,8 @@ int ucp_params_from_error_bound(ucp_ctx *ctx, const float *decompressed, float e
 int ucp_backward(ucp_ctx *ctx, const float *params, int H, int W, const ucp_model_desc *desc,
                  int cptype, const float *weight, float *grad_params, ucp_stream stream) {
   if (!ctx || !params || !weight || !grad_params) return UCP_ERR_ARG;
-  int rc = valid_desc(desc, false);
+  int rc = ucp_valid_backward(desc, cptype, H, W);
   if (rc) return rc;
-  if (desc->model == UCP_GAUSSIAN) return UCP_ERR_UNSUPPORTED;
-  if (uses_stencil(desc)) return UCP_ERR_UNSUPPORTED;
-  if (cptype != UCP_MIN && cptype != UCP_MAX) return UCP_ERR_ARG;
-  if ((rc = valid_shape(1, H, W))) return rc;
   DeviceGuard g(ctx->device);
   if (g.err != cudaSuccess) return ucp_set_error(ctx, g.err);
   const int Q = desc->model == UCP_HISTOGRAM ? desc->bins : 2;

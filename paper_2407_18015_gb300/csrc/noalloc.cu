@@ -11,7 +11,10 @@
 // stand-in), so the device address is looked up once per device with
 // cudaGetSymbolAddress, with that device current, on the first call made on
 // that device; that first call should therefore come before any stream
-// capture.  Every call on a device shares the one array: calls whose work
+// capture.  The address is cached for the life of the process, so the entry
+// point must not be used on a device after a reset of its primary context
+// (cudaDeviceReset), which reloads the module.  Every call on a device shares
+// the one array: calls whose work
 // overlaps on the GPU (different streams, no ordering between them) race on
 // it.  The array keeps the last call's contents; nothing in it needs to start
 // at zero, because the partials pass writes every entry the gather pass reads.
@@ -60,20 +63,10 @@ extern "C" size_t ucp_backward_static_capacity(void) { return kStaticRowsFloats;
 extern "C" int ucp_backward_static(const float *params, int H, int W,
                                    const ucp_model_desc *desc, int cptype, const float *weight,
                                    float *grad_params, ucp_stream stream) {
-  if (!params || !weight || !grad_params || !desc) return UCP_ERR_ARG;
-  if (desc->model != UCP_UNIFORM && desc->model != UCP_EPANECHNIKOV &&
-      desc->model != UCP_HISTOGRAM)
-    return (desc->model == UCP_MVN_MC || desc->model == UCP_HISTOGRAM_SEMI ||
-            desc->model == UCP_GAUSSIAN)
-               ? UCP_ERR_UNSUPPORTED
-               : UCP_ERR_ARG;
-  if (desc->model == UCP_HISTOGRAM && (desc->bins < 1 || desc->bins > kMaxBinsHost))
-    return UCP_ERR_ARG;
-  if (desc->boundary != UCP_BOUNDARY_INGRID && desc->boundary != UCP_BOUNDARY_ZERO)
-    return UCP_ERR_ARG;
-  if (desc->stencil != UCP_STENCIL_4 || desc->depth > 1) return UCP_ERR_UNSUPPORTED;
-  if (cptype != UCP_MIN && cptype != UCP_MAX) return UCP_ERR_ARG;
-  if (H < 1 || W < 1) return UCP_ERR_SHAPE;
+  if (!params || !weight || !grad_params) return UCP_ERR_ARG;
+  // the same checks, in the same order, as ucp_backward
+  const int vrc = ucp_valid_backward(desc, cptype, H, W);
+  if (vrc) return vrc;
   const size_t Q = desc->model == UCP_HISTOGRAM ? (size_t)desc->bins : 2;
   if ((size_t)H * (size_t)W > kStaticRowsFloats / (5 * Q)) return UCP_ERR_SHAPE;
   int dev = 0;

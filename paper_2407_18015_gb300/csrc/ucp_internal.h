@@ -34,6 +34,12 @@ struct ucp_ctx {
 };
 
 int ucp_set_error(ucp_ctx *ctx, cudaError_t e);
+// argument checks of the C ABI (status codes of include/ucp.h), made before
+// anything is enqueued: a model description (sampled models allowed or
+// not), a grid shape, and the whole argument set of the adjoint
+int ucp_valid_desc(const ucp_model_desc *d, bool allow_sampled);
+int ucp_valid_shape(long long N, long long H, long long W);
+int ucp_valid_backward(const ucp_model_desc *desc, int cptype, int H, int W);
 int ucp_ensure_work(ucp_ctx *ctx, size_t bytes);
 // the context's streams and events of the multi-model entry points (once)
 int ucp_ensure_pipe(ucp_ctx *ctx);

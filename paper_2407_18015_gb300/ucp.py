@@ -301,25 +301,62 @@ def ucp_params_from_error_bound(ctx, decompressed, eb, params, stream=None):
     _check(rc, "ucp_params_from_error_bound", ctx)
 
 
+def _backward_args(params, desc, weight, grad_params):
+    """Shape, dtype and device checks of the adjoint's tensors, made before
+    any launch: params [P][H][W] (P the model's parameter planes), weight
+    [H][W], grad_params [Q][H][W] (Q = 2, or bins for histograms), float32,
+    contiguous, all on one CUDA device.  A short output or weight would
+    otherwise be written or read out of bounds on the device."""
+    for name, t in (("params", params), ("weight", weight), ("grad_params", grad_params)):
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a torch.Tensor")
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.dtype != torch.float32:
+            raise TypeError(f"{name} must be torch.float32, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if params.dim() != 3:
+        raise ValueError(f"params must be [P][H][W], got {tuple(params.shape)}")
+    P, H, W = params.shape
+    if desc.model not in (UCP_UNIFORM, UCP_EPANECHNIKOV, UCP_HISTOGRAM) or \
+            desc.stencil != UCP_STENCIL_4:
+        # the C entry point rejects these models and stencils with its own
+        # status before anything is launched
+        return H, W
+    planes = lib().ucp_param_count(ctypes.byref(desc))
+    if planes <= 0:
+        raise UcpError(UCP_ERR_ARG, "ucp_backward", "invalid model description")
+    Q = desc.bins if desc.model == UCP_HISTOGRAM else 2
+    if P != planes:
+        raise ValueError(f"params has {P} planes, the model has {planes}")
+    if tuple(weight.shape) != (H, W):
+        raise ValueError(f"weight must be [{H}][{W}], got {tuple(weight.shape)}")
+    if tuple(grad_params.shape) != (Q, H, W):
+        raise ValueError(f"grad_params must be [{Q}][{H}][{W}], got {tuple(grad_params.shape)}")
+    if weight.device != params.device or grad_params.device != params.device:
+        raise ValueError("params, weight and grad_params must be on one device")
+    return H, W
+
+
 def ucp_backward(ctx, params, desc, cptype, weight, grad_params, stream=None):
-    _, H, W = params.shape
-    rc = lib().ucp_backward(ctx, _ptr(params, torch.float32, name="params"), H, W,
-                            ctypes.byref(desc), int(cptype),
-                            _ptr(weight, torch.float32, name="weight"),
-                            _ptr(grad_params, torch.float32, name="grad_params"),
+    H, W = _backward_args(params, desc, weight, grad_params)
+    rc = lib().ucp_backward(ctx, params.data_ptr(), H, W, ctypes.byref(desc), int(cptype),
+                            weight.data_ptr(), grad_params.data_ptr(),
                             _stream(stream, params.device))
     _check(rc, "ucp_backward", ctx)
 
 
 def ucp_backward_static(params, desc, cptype, weight, grad_params, stream=None):
     """The adjoint without device allocation (no context; scratch is a fixed
-    device array inside the library; see include/ucp.h)."""
-    _, H, W = params.shape
-    rc = lib().ucp_backward_static(_ptr(params, torch.float32, name="params"), H, W,
-                                   ctypes.byref(desc), int(cptype),
-                                   _ptr(weight, torch.float32, name="weight"),
-                                   _ptr(grad_params, torch.float32, name="grad_params"),
-                                   _stream(stream, params.device))
+    device array inside the library; see include/ucp.h).  The C entry point
+    works on the current device, so the call is made with params' device
+    current."""
+    H, W = _backward_args(params, desc, weight, grad_params)
+    with torch.cuda.device(params.device):
+        rc = lib().ucp_backward_static(params.data_ptr(), H, W, ctypes.byref(desc), int(cptype),
+                                       weight.data_ptr(), grad_params.data_ptr(),
+                                       _stream(stream, params.device))
     _check(rc, "ucp_backward_static")
 
 

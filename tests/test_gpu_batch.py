@@ -147,3 +147,45 @@ def test_batch_errors(ucp, ctx):
     assert e.value.status == ucp.UCP_ERR_ARG
     b.run()          # an empty batch is a no-op
     b.close()
+
+
+def test_batch_at_64_field_workload_scale(ucp, ctx, tmp_path, monkeypatch):
+    """The 64-field batched workload (uneven shapes, N in {10, 20, 50, 100},
+    uniform / Epanechnikov / histogram-16, minimum or maximum), every side
+    halved to bound the test's memory and time: the autotuned launch,
+    captured in a CUDA graph and replayed, equals the per-field launches
+    field by field."""
+    from paper_2407_18015_gb300 import synth
+    monkeypatch.setenv("UCP_TUNE_CACHE", str(tmp_path / "tune.json"))
+    specs = synth.batch_specs(fields=64)
+    assert {s["N"] for s in specs} == {10, 20, 50, 100}
+    assert {s["model"] for s in specs} == {"uniform", "epanechnikov", "histogram"}
+    fields = []
+    for sp in specs:
+        ens = torch.from_numpy(synth.batch_field(sp, scale=0.5)).cuda()
+        desc = ucp.make_desc(sp["model"], bins=sp["bins"])
+        cp = ucp.UCP_MIN if sp["cptype"] == "min" else ucp.UCP_MAX
+        Hh, Ww = ens.shape[1:]
+        out = (torch.full((Hh, Ww), -1.0, device="cuda"), torch.full((Hh, Ww), -1.0, device="cuda"))
+        fields.append((ens, desc, cp, out))
+    refs = _reference(ctx, fields)
+    b = ucp.Batch(ctx)
+    for ens, desc, cp, (omin, omax) in fields:
+        b.add(ens, desc, cp, omin, omax)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b.tune()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        b.run()
+    for _, _, _, (omin, omax) in fields:
+        omin.fill_(-1.0)
+        omax.fill_(-1.0)
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+    _check(fields, refs)
+    b.close()
+    del fields, refs
+    torch.cuda.empty_cache()

@@ -58,3 +58,42 @@ def test_static_adjoint_rejects_oversize(ucp):
     with pytest.raises(ucp.UcpError) as e:
         ucp.ucp_backward_static(p, desc, ucp.UCP_MIN, W, g)
     assert e.value.status == ucp.UCP_ERR_SHAPE
+
+
+def test_static_adjoint_checks_shapes_before_launch(ucp):
+    """A short gradient, weight or parameter array is rejected by the
+    binding before anything is launched (it would be written or read out
+    of bounds on the device)."""
+    desc = ucp.make_desc("histogram", bins=8)
+    p = torch.zeros((10, 12, 13), device="cuda")
+    W = torch.zeros((12, 13), device="cuda")
+    g = torch.zeros((8, 12, 13), device="cuda")
+    ctx = ucp.Context(0)
+    for args in ((p, W, g[:4]), (p, W[:6], g), (p[:9], W, g), (p, W.double(), g)):
+        with pytest.raises((ValueError, TypeError)):
+            ucp.ucp_backward_static(args[0], desc, ucp.UCP_MIN, args[1], args[2])
+        with pytest.raises((ValueError, TypeError)):
+            ucp.ucp_backward(ctx.handle, args[0], desc, ucp.UCP_MIN, args[1], args[2])
+    ctx.close()
+    torch.cuda.synchronize()
+    assert bool((g == 0).all())
+
+
+def test_static_adjoint_status_matches_context_adjoint(ucp):
+    """The same invalid descriptions give the same status through both
+    adjoint entry points (shared argument checks)."""
+    ctx = ucp.Context(0)
+    p = torch.zeros((2, 4, 5), device="cuda")
+    W = torch.zeros((4, 5), device="cuda")
+    for kw in (dict(model="uniform", depth=-1), dict(model="uniform", stencil=7),
+               dict(model="uniform", stencil=1), dict(model="gaussian"),
+               dict(model="mvn"), dict(model="uniform", boundary=5)):
+        desc = ucp.make_desc(**kw)
+        st = []
+        for call in (lambda: ucp.ucp_backward_static(p, desc, 1, W, p),
+                     lambda: ucp.ucp_backward(ctx.handle, p, desc, 1, W, p)):
+            with pytest.raises(ucp.UcpError) as e:
+                call()
+            st.append(e.value.status)
+        assert st[0] == st[1], (kw, st)
+    ctx.close()
