@@ -87,11 +87,16 @@ __global__ void __launch_bounds__(256) fit_kernel(Field f) {
 // ---------------------------------------------------------------------------
 // tile kernel
 
-// resident CTAs per SM each model's register budget is tuned for
-template <int MODEL>
+// resident CTAs per SM each model's register budget is tuned for (ROWS:
+// histogram tiles that walk per-bin rows, four CTAs per SM when their
+// members are staged by the tensor memory accelerator)
+template <int MODEL, bool ROWS = false>
 struct TileOcc {
   static constexpr int value =
-      MODEL == kUniform ? 5 : (MODEL == kEpan ? 5 : (MODEL == kHist ? 3 : (MODEL == kSemi ? 4 : 2)));
+      MODEL == kUniform ? 5
+                        : (MODEL == kEpan ? 5
+                                          : (MODEL == kHist ? (ROWS ? 3 : 3)
+                                                            : (MODEL == kSemi ? 4 : 2)));
 };
 
 // tile height: 8 rows for the uniform and histogram models and the
@@ -114,6 +119,20 @@ struct HistRows {
   static constexpr bool value = MODEL == kHist && TYm == 8;
 };
 
+// floats of the parameter tile: the model's tile, or for per-bin-row
+// histogram tiles the smaller one of hist_rows_tile_floats (masses held in
+// it only when they are not counted in registers)
+template <int MODEL, int TYm, bool ROWS>
+__host__ __device__ constexpr long long param_tile_floats(int B, bool masses) {
+  return ROWS ? hist_rows_tile_floats(B, TYm, masses) : tile_floats(MODEL, B, TYm);
+}
+
+// rows of a histogram tile's per-bin tables (hist_r4_rows float4 per halo
+// vertex, rows hist_r4_stride apart), in floats
+__host__ __device__ constexpr int r4_floats(int B, int TYv) {
+  return 4 * hist_r4_rows(B) * hist_r4_stride((TYv + 2) * (TX + 2));
+}
+
 // Shared memory: the parameter tile, then (HistRows) the per-bin rows,
 // 16-byte aligned.
 template <int MODEL, bool FROM_MEMBERS, bool SADDLE, int TYm>
@@ -123,15 +142,10 @@ __global__ void __launch_bounds__(NTHREADS, TileOcc<MODEL>::value) tile_kernel(F
   constexpr bool ROWS = HistRows<MODEL, TYm>::value;
   float4 *R4 = nullptr;
   if constexpr (ROWS)
-    R4 = reinterpret_cast<float4 *>(sm + ((tile_floats(MODEL, f.B, TYm) + 3) & ~3LL));
+    R4 = reinterpret_cast<float4 *>(
+        sm + ((param_tile_floats<MODEL, TYm, ROWS>(f.B, true) + 3) & ~3LL));
   process_tile<MODEL, FROM_MEMBERS, TYm, SADDLE, false, ROWS>(
       f, f.y0 + (tile / tiles_x) * TYm, (tile % tiles_x) * TX, sm, nullptr, nullptr, nullptr, R4);
-}
-
-// rows of a histogram tile's per-bin tables (hist_r4_rows float4 per halo
-// vertex), in floats
-__host__ __device__ constexpr int r4_floats(int B, int TYv) {
-  return 4 * hist_r4_rows(B) * (TYv + 2) * (TX + 2);
 }
 
 // The same with the members staged by the tensor memory accelerator: shared
@@ -140,7 +154,7 @@ __host__ __device__ constexpr int r4_floats(int B, int TYv) {
 // rows, once the box is no longer read -- then the parameter tile, then the
 // mbarrier.
 template <int MODEL, bool SADDLE, int TYm>
-__global__ void __launch_bounds__(NTHREADS, TileOcc<MODEL>::value)
+__global__ void __launch_bounds__(NTHREADS, (TileOcc<MODEL, HistRows<MODEL, TYm>::value>::value))
     tile_kernel_tma(Field f, int tiles_x, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(128) float smem[];
   const int tile = blockIdx.x;
@@ -148,7 +162,7 @@ __global__ void __launch_bounds__(NTHREADS, TileOcc<MODEL>::value)
   constexpr bool ROWS = HistRows<MODEL, TYm>::value;
   const int r4 = ROWS ? r4_floats(f.B, TYm) : 0;
   float *sm = smem + max(box_floats, r4);
-  const long long tile_f = tile_floats(MODEL, f.B, TYm);
+  const long long tile_f = param_tile_floats<MODEL, TYm, ROWS>(f.B, false);
   uint64_t *bar = reinterpret_cast<uint64_t *>(sm + ((tile_f + 1) & ~1LL));
   process_tile<MODEL, true, TYm, SADDLE, true, ROWS>(
       f, f.y0 + (tile / tiles_x) * TYm, (tile % tiles_x) * TX, sm, &tmap, smem, bar,
@@ -212,9 +226,11 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // occupancy (0: not even one), capped at N and at the box limit of 256.
 template <int MODEL, int TYm>
 static int tma_box_members(int N, int B) {
-  const size_t tile_b = (size_t)((tile_floats(MODEL, B, TYm) + 1) & ~1LL) * sizeof(float) + 16;
+  constexpr bool ROWS = HistRows<MODEL, TYm>::value;
+  const size_t tile_b =
+      (size_t)((param_tile_floats<MODEL, TYm, ROWS>(B, false) + 1) & ~1LL) * sizeof(float) + 16;
   const size_t per_member = (size_t)(TYm + 2) * kBoxW * sizeof(float);
-  const size_t budget = (size_t)227 * 1024 / TileOcc<MODEL>::value - 1024;
+  const size_t budget = (size_t)227 * 1024 / TileOcc<MODEL, ROWS>::value - 1024;
   if (budget < tile_b + per_member) return 0;
   const size_t nc = (budget - tile_b) / per_member;
   return (int)std::min<size_t>(nc, (size_t)std::min(N, 256));
@@ -229,13 +245,14 @@ static bool launch_tile_tma(const Field &f, int tiles_x, int tiles, cudaStream_t
   if (f.W % 4 != 0 || (reinterpret_cast<uintptr_t>(f.ens) & 15) != 0) return false;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
-  const size_t tile_b = (size_t)((tile_floats(MODEL, f.B, TYm) + 1) & ~1LL) * sizeof(float) + 16;
-  const size_t per_member = (size_t)(TYm + 2) * kBoxW * sizeof(float);
-  const size_t budget = (size_t)227 * 1024 / TileOcc<MODEL>::value - 1024;
-  const int nc = tma_box_members<MODEL, TYm>(f.N, f.B);
-  if (nc < 1) return false;
   // histogram per-bin rows, in the room of the member box
   constexpr bool ROWS = HistRows<MODEL, TYm>::value;
+  const size_t tile_b =
+      (size_t)((param_tile_floats<MODEL, TYm, ROWS>(f.B, false) + 1) & ~1LL) * sizeof(float) + 16;
+  const size_t per_member = (size_t)(TYm + 2) * kBoxW * sizeof(float);
+  const size_t budget = (size_t)227 * 1024 / TileOcc<MODEL, ROWS>::value - 1024;
+  const int nc = tma_box_members<MODEL, TYm>(f.N, f.B);
+  if (nc < 1) return false;
   const size_t r4_b = ROWS ? (size_t)r4_floats(f.B, TYm) * sizeof(float) : 0;
   if (tile_b + r4_b > budget) return false;
   CUtensorMap map;
@@ -278,7 +295,7 @@ static cudaError_t launch_tile_h(const Field &f, cudaStream_t s) {
   size_t smem = (size_t)tile_floats(MODEL, f.B, TYm) * sizeof(float);
   // histogram per-bin rows after the tile (launch_tile checked that they fit)
   if constexpr (HistRows<MODEL, TYm>::value)
-    smem = (size_t)((tile_floats(MODEL, f.B, TYm) + 3) & ~3LL) * sizeof(float) +
+    smem = (size_t)((param_tile_floats<MODEL, TYm, true>(f.B, true) + 3) & ~3LL) * sizeof(float) +
            (size_t)r4_floats(f.B, TYm) * sizeof(float);
   // per device: the attribute is set once (several host threads may race to
   // set it; setting it twice is harmless, the flag itself is atomic)
@@ -321,10 +338,17 @@ static cudaError_t launch_tile(const Field &f, cudaStream_t s) {
     if (f.N <= tma_box_members<kEpan, 8>(f.N, f.B)) return launch_tile_h<MODEL, FM, SADDLE, 8>(f, s);
   }
   if constexpr (MODEL == kHist) {
-    // without the per-bin rows (more bins than fit) the smaller halo wins
-    const size_t rows_end = (size_t)((tile_floats(kHist, f.B, 8) + 3) & ~3LL) * sizeof(float) +
+    // Per-bin rows on 8-row tiles when they fit at four CTAs per SM next to
+    // the small parameter tile (counts in registers: at most 8 bins and
+    // 65535 members); otherwise the segment walker on 16-row tiles, where
+    // the smaller halo wins.  The per-thread staging (members not TMA
+    // aligned) and the from-parameters path hold the masses in the tile
+    // and run the same rows at three CTAs per SM.
+    const size_t rows_end = (size_t)((hist_rows_tile_floats(f.B, 8, false) + 3) & ~3LL) *
+                                sizeof(float) +
                             (size_t)r4_floats(f.B, 8) * sizeof(float) + 16;
-    if (rows_end > (size_t)227 * 1024 / TileOcc<kHist>::value - 1024)
+    if (f.B > 8 || (FM && f.N > 65535) ||
+        rows_end > (size_t)227 * 1024 / TileOcc<kHist, true>::value - 1024)
       return launch_tile_h<MODEL, FM, SADDLE, TY>(f, s);
   }
   return launch_tile_h<MODEL, FM, SADDLE, TileH<MODEL>::value>(f, s);

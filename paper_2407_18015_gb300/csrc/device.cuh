@@ -1291,61 +1291,98 @@ __device__ __forceinline__ void hist_walk(const float *S0, int coff, int B, floa
   pmax = fmaxf(acc.y, 0.f);
 }
 
+// Shared-memory reads that happen only where p holds (one predicated
+// instruction, no branch); where p is false the result is unspecified and
+// must not be used.  addr: a shared-state-space address.
+__device__ __forceinline__ float4 lds128_if(bool p, uint32_t addr) {
+  float4 r;
+  asm(
+      "{\n .reg .pred q;\n setp.ne.b32 q, %5, 0;\n"
+      " @q ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n}"
+      : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+      : "r"(addr), "r"((int)p));
+  return r;
+}
+__device__ __forceinline__ float2 lds64_if(bool p, uint32_t addr) {
+  float2 r;
+  asm(
+      "{\n .reg .pred q;\n setp.ne.b32 q, %3, 0;\n @q ld.shared.v2.f32 {%0, %1}, [%2];\n}"
+      : "=f"(r.x), "=f"(r.y)
+      : "r"(addr), "r"((int)p));
+  return r;
+}
+
 // Per-bin rows of a staged histogram vertex for the forward walk: float4
-// rows at R[k * WS + l], k = 0..B+1.  Row k < B describes bin k: (S_k,
+// rows at R[k * RS + l], k = 0..B.  Row k < B describes bin k: (S_k,
 // T - S_k, slope_k, e_{k+1} - lo), with the tail S_k = T - (m_0 + ... +
 // m_{k-1}), slope_k = (S_k - S_{k+1}) / h (the bin's density, m_k / h, in
 // the mixture form) and e_{k+1} - lo = (k + 1) h (hi - lo for the last edge).
-// Row B is (0, T, 0, kFar), beyond the support, and row B + 1 repeats it so
-// that the walkers' unconditional reads one row past their last crossing
-// stay inside the table.  A point mass has row 0 = (0, T, 0, kFar): its one
-// edge takes the survival from T to 0.
-__host__ __device__ constexpr int hist_r4_rows(int B) { return B + 2; }
+// Row B is (0, T, 0, kFar), beyond the support.  A point mass has every row
+// (0, T, 0, kFar): its one edge takes the survival from T to 0.  A walker
+// reads a row only when it crosses an edge, at most B + 1 times, so no row
+// past B is ever read.
+__host__ __device__ constexpr int hist_r4_rows(int B) { return B + 1; }
 
-// A neighbour's survival G and CDF F walked bin by bin over the per-bin rows:
-// before the support (G, F) = (T, 0); on bin k G(x) = S_k - slope_k (x - e_k)
-// and F(x) = T - S_k + slope_k (x - e_k); beyond it (0, T).  Crossing an edge
-// loads the next row, which also holds the edge after it, so a step needs no
-// edge arithmetic.  An absent neighbour is the constant (1, 1) that never
-// reaches an edge.
+// Row stride of the per-bin rows of a halo of `halo` vertices, in float4:
+// a multiple of 8 (128 bytes).  The 32 lanes of a warp walk 32 consecutive
+// vertices and read the rows of the same neighbour direction, so lane i
+// reads R[k_i * RS + l0 + i]; with RS a multiple of 128 bytes the bank of
+// that 16-byte read depends on i alone, whatever row k_i each lane is on,
+// and the eight lanes of a quarter warp never share a bank.
+__host__ __device__ constexpr int hist_r4_stride(int halo) { return (halo + 7) & ~7; }
+
+// A neighbour's survival G and CDF F walked bin by bin over the per-bin
+// rows: before the support (G, F) = (T, 0); on bin k G falls and F rises by
+// slope_k per unit of x; beyond it (0, T).  The walker holds (G, F) at the
+// walk's current position and advances them by the step length; crossing an
+// edge (one predicated 16-byte read) restarts them from the row's exact
+// values (S_k, T - S_k), which also carries the jump of a point mass.  An
+// absent neighbour is the constant (1, 1) that never reaches an edge.
 struct HistRowWalker {
-  int addr;                 // float4 index of the row read at the next crossing
-  float lam;                // support start in the centre's frame
-  float el, nx, s, c, sl;   // segment start, next edge, G and F at el, slope
-  __device__ __forceinline__ void init_absent(int any_row) {
-    addr = any_row; lam = 0.f;
-    el = -kFar; nx = kFar; s = c = 1.f; sl = 0.f;
+  uint32_t addr;  // shared-memory address of the row read at the next crossing
+  float lam;      // support start in the centre's frame
+  float nx;       // next edge in the centre's frame (kFar: none left)
+  float2 sv;      // (-slope, slope): the change of (G, F) per unit of x
+  float2 gf;      // (G, F) at the walk's current position
+  __device__ __forceinline__ void init_absent() {
+    addr = 0u; lam = 0.f; nx = kFar;
+    sv = make_float2(0.f, 0.f); gf = make_float2(1.f, 1.f);
   }
-  __device__ __forceinline__ void init(int row0, float lam_, float T) {
-    addr = row0; lam = lam_;
-    el = -kFar; nx = lam_; s = T; c = 0.f; sl = 0.f;
+  __device__ __forceinline__ void init(const float4 *row0, float lam_, float T) {
+    addr = static_cast<uint32_t>(__cvta_generic_to_shared(row0)); lam = lam_; nx = lam_;
+    sv = make_float2(0.f, 0.f); gf = make_float2(T, 0.f);
   }
-  // One merge step at x1: cross the next edge if it is at or below x1.  No
-  // branch; the read always has a valid address (see hist_r4_rows).
-  template <int WS>
-  __device__ __forceinline__ bool step(const float4 *R, float x1) {
+  // (G, F) a distance d further on the current segment
+  __device__ __forceinline__ float2 at(float d) const {
+    return __ffma2_rn(sv, make_float2(d, d), gf);
+  }
+  // Move to x1 (where the current segment gives `pr`): cross the next edge
+  // if it is at or below x1 -- it is then exactly at x1, the walk's next
+  // breakpoint being the smallest next edge -- and start the new segment
+  // from its row.  Branch free: the row read is predicated, the state
+  // updates are selects.
+  template <int RS>
+  __device__ __forceinline__ void step(float x1, float2 pr) {
     const bool cr = nx <= x1;
-    const float4 t = R[addr];
-    s = cr ? t.x : s;
-    c = cr ? t.y : c;
-    sl = cr ? t.z : sl;
+    const float4 t = lds128_if(cr, addr);
+    gf.x = cr ? t.x : pr.x;
+    gf.y = cr ? t.y : pr.y;
+    sv.x = cr ? -t.z : sv.x;
+    sv.y = cr ? t.z : sv.y;
     nx = cr ? lam + t.w : nx;
-    el = cr ? x1 : el;
-    addr += cr ? WS : 0;
-    return cr;
+    addr += cr ? (uint32_t)(RS * 16) : 0u;
   }
-  __device__ __forceinline__ float G(float x) const { return fmaf(-sl, x - el, s); }
-  __device__ __forceinline__ float F(float x) const { return fmaf(sl, x - el, c); }
   // From the initial state, cross every edge at or below 0 at once (the
   // state step() would reach edge by edge; the count of such edges comes
-  // from -lam / h and is checked against the edges of the rows).
-  template <int WS>
-  __device__ __forceinline__ void seek0(const float4 *R, int B, float h) {
+  // from -lam / h and is checked against the edges of the rows), and set
+  // (G, F) to their values at 0.
+  template <int RS>
+  __device__ __forceinline__ void seek0(const float4 *row0, int B, float h) {
     if (nx > 0.f) return;  // the first edge is above 0 (also: absent)
-    const int row0 = addr;
     int j = 1;             // edges e_0 .. e_{j-1} are at or below 0
+    float el;
     if (h > 0.f) {
-      auto edge = [&](int i) { return i == 0 ? lam : lam + R[row0 + (i - 1) * WS].w; };
+      auto edge = [&](int i) { return i == 0 ? lam : lam + row0[(i - 1) * RS].w; };
       j = (int)fminf(fmaxf(floorf(-lam * frcp(h)), 0.f), (float)B) + 1;
       if (j <= B && edge(j) <= 0.f) ++j;
       if (j >= 2 && edge(j - 1) > 0.f) --j;
@@ -1353,21 +1390,30 @@ struct HistRowWalker {
     } else {
       el = lam;            // a point mass: its one edge
     }
-    const float4 t = R[row0 + (j - 1) * WS];
-    s = t.x;
-    c = t.y;
-    sl = t.z;
+    const float4 t = row0[(j - 1) * RS];
+    // on the segment that starts at el <= 0: G(x) = S - slope (x - el) and
+    // F(x) = T - S + slope (x - el), taken at x = 0
+    gf = make_float2(fmaf(t.z, el, t.x), fmaf(-t.z, el, t.y));
+    sv = make_float2(-t.z, t.z);
     nx = lam + t.w;
-    addr = row0 + j * WS;
+    addr = static_cast<uint32_t>(__cvta_generic_to_shared(row0 + j * RS));
   }
 };
 
-// hist_walk over the per-bin rows (centre rows from crow): the same merge of
-// the bin edges of the centre and the four neighbours in increasing order,
-// the same Bernstein mean per piece; the crossings load rows instead of
-// computing tails, slopes and edges.
-template <int WS, bool SADDLE = false>
-__device__ __forceinline__ void hist_walk_rows(const float4 *R, int crow, int B, float W1,
+// Both probabilities of a non-degenerate histogram centre in one walk over
+// [0, W1] (local frame at lo1; the centre's rows from crow): all bin edges of
+// the centre and of the four neighbours are merged in increasing order; on
+// each piece the centre pdf is the constant m_j / h1 and each factor is
+// linear, so the piece integral is the Bernstein mean of the factor end
+// values (bern_mean4_pairs_x2).  Beyond a neighbour's support its survival is
+// 0, before it its CDF is 0, so both integrals run over the centre's whole
+// support.  Every lane executes the same instructions on every step; only the
+// row reads of the crossings are predicated.
+// SADDLE = false: (pmin, pmax) = (int pdf prod G, int pdf prod F).
+// SADDLE = true:  (pmin, pmax) = (t1, t2) with factor i = G_i if sg[i] > 0
+// else F_i for t1, and the other one for t2 (absent neighbours are 1 in both).
+template <int RS, bool SADDLE = false>
+__device__ __forceinline__ void hist_walk_rows(const float4 *crow, int B, float W1,
                                                HistRowWalker *nw, float &pmin, float &pmax,
                                                const int *sg = nullptr) {
   if (!(W1 <= 1e38f)) {
@@ -1376,46 +1422,41 @@ __device__ __forceinline__ void hist_walk_rows(const float4 *R, int crow, int B,
   }
   // the centre needs only the density and the next edge of its bin: the
   // (z, w) half of each row
-  const float2 *R2 = reinterpret_cast<const float2 *>(R);
-  int addr_c = crow + WS;
+  uint32_t addr_c = static_cast<uint32_t>(__cvta_generic_to_shared(crow + RS)) + 8u;
   float dens, nxc;
   {
-    const float2 t = R2[2 * crow + 1];
-    dens = t.x;
-    nxc = t.y;
+    const float4 t = crow[0];
+    dens = t.z;
+    nxc = t.w;
   }
-  auto pair = [&](int i, float g, float f) {
-    if constexpr (SADDLE) return sg[i] > 0 ? make_float2(g, f) : make_float2(f, g);
-    else return make_float2(g, f);
+  auto pair = [&](int i, float2 v) {
+    if constexpr (SADDLE) return sg[i] > 0 ? v : make_float2(v.y, v.x);
+    else return v;
   };
-  float2 Pl[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) Pl[i] = pair(i, nw[i].G(0.f), nw[i].F(0.f));
   float2 acc = make_float2(0.f, 0.f);
   float x0 = 0.f;
-  const int max_steps = 5 * (B + 2) + 4;
-#pragma unroll 2
+  const int max_steps = 5 * (B + 1) + 4;
+#pragma unroll 1
   for (int step = 0; step < max_steps && x0 < W1; ++step) {
-    float x1 = fminf(fminf(nw[0].nx, nw[1].nx), fminf(nw[2].nx, nw[3].nx));
-    x1 = fmaxf(fminf(x1, nxc), x0);
-    float2 Pr[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) Pr[i] = pair(i, nw[i].G(x1), nw[i].F(x1));
-    const float wgt = (x1 - x0) * dens;
-    acc = __ffma2_rn(make_float2(wgt, wgt), bern_mean4_pairs_x2(Pl, Pr), acc);
+    const float x1 = fminf(fminf(fminf(nw[0].nx, nw[1].nx), fminf(nw[2].nx, nw[3].nx)), nxc);
+    const float d = x1 - x0;
+    float2 pr[4], L[4], Rv[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      // the left values of the next piece: the new segment's at x1 (the
-      // right values, except after a point mass)
-      const bool cr = nw[i].step<WS>(R, x1);
-      Pl[i] = cr ? pair(i, nw[i].s, nw[i].c) : Pr[i];
+      pr[i] = nw[i].at(d);
+      L[i] = pair(i, nw[i].gf);
+      Rv[i] = pair(i, pr[i]);
     }
+    const float wgt = d * dens;
+    acc = __ffma2_rn(make_float2(wgt, wgt), bern_mean4_pairs_x2(L, Rv), acc);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) nw[i].step<RS>(x1, pr[i]);
     {
       const bool cr = nxc <= x1;
-      const float2 t = R2[2 * addr_c + 1];
+      const float2 t = lds64_if(cr, addr_c);
       dens = cr ? t.x : dens;
       nxc = cr ? t.y : nxc;
-      addr_c += cr ? WS : 0;
+      addr_c += cr ? (uint32_t)(RS * 16) : 0u;
     }
     x0 = x1;
   }

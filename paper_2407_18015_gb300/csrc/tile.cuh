@@ -23,6 +23,18 @@ __host__ __device__ constexpr long long tile_floats(int model, int B, int TYv) {
                           : 2 * halo;
 }
 
+// Shared-memory floats of the parameter tile of a histogram tile that walks
+// per-bin rows: lo, hi, then the total mass T and the status (rows 2 and 3,
+// written once the rows are built); while the rows are built from masses
+// held in the tile (rows 2 .. 1 + B), those take their place, else (masses
+// from bin counts in registers) a table of the values count / N follows.
+// The rows themselves (hist_r4_rows x hist_r4_stride float4) come on top.
+constexpr int ROWS_MASS_TABLE = 256;
+__host__ __device__ constexpr long long hist_rows_tile_floats(int B, int TYv, bool masses) {
+  const long long halo = (long long)(TYv + 2) * 34;
+  return masses ? (2 + B > 4 ? 2 + B : 4) * halo : 4 * halo + ROWS_MASS_TABLE;
+}
+
 // Number of pieces of the histogram walk of a tile vertex (0 for a vertex
 // that does not walk): the centre's B bins plus every neighbour edge inside
 // the centre's support.
@@ -317,12 +329,34 @@ __device__ __forceinline__ void hist_tail_table(float *sm, int l, int B) {
   sm[(5 + B) * HALO + l] = (float)st;
 }
 
-// Per-bin rows (hist_r4_rows) of staged vertex l straight from its masses,
-// with its total and status in rows 4 + B and 5 + B as hist_tail_table
-// writes them (the row walk reads its tails from the rows, so the tail rows
-// of the parameter tile are not written; the masses stay there).  The tails
-// S_k = T - (m_0 + ... + m_{k-1}) are formed as hist_tail_table forms them.
-template <int HALO>
+// Per-bin rows of one vertex (see hist_r4_rows) from its lo, hi and masses
+// m_0..m_{B-1} (all FP32): R[k * RS] for k = 0..B.  T = m_0 + ... + m_{B-1}
+// in bin order; the tails S_k = T - (m_0 + ... + m_{k-1}).
+template <int RS, typename Mass>
+__device__ __forceinline__ void hist_rows_build(float4 *R, float a, float b, float t, int B,
+                                                Mass mass) {
+  const float4 beyond = make_float4(0.f, t, 0.f, kFar);
+  if (a == b) {
+    for (int k = 0; k < hist_r4_rows(B); ++k) R[k * RS] = beyond;
+    return;
+  }
+  // for a power of two B the product with 1/B is the quotient exactly
+  const float w = b - a;
+  const float h = (B & (B - 1)) == 0 ? w * (1.f / (float)B) : w / (float)B, ih = frcp(h);
+  float c = 0.f, sk = t;
+  for (int k = 0; k < B; ++k) {
+    c += mass(k);
+    const float sn = k + 1 < B ? t - c : 0.f;
+    R[k * RS] = make_float4(sk, t - sk, (sk - sn) * ih, k + 1 < B ? (float)(k + 1) * h : w);
+    sk = sn;
+  }
+  R[B * RS] = beyond;
+}
+
+// Per-bin rows of staged vertex l from the masses in its parameter tile
+// (rows 2 .. 1 + B); afterwards the tile holds lo, hi, the total mass (row 2)
+// and the status bits (row 3), as check_params<kHist, HALO, true> reads them.
+template <int HALO, int RS>
 __device__ __forceinline__ void hist_row_table(float *sm, float4 *R, int l, int B) {
   const float a = sm[l], b = sm[HALO + l];
   uint8_t st = (!isfinite(a) || !isfinite(b)) ? V_NONFINITE
@@ -334,23 +368,56 @@ __device__ __forceinline__ void hist_row_table(float *sm, float4 *R, int l, int 
     else if (w < 0.f) st |= V_BAD;
     t += w;
   }
-  sm[(4 + B) * HALO + l] = t;
-  sm[(5 + B) * HALO + l] = (float)st;
+  hist_rows_build<RS>(R + l, a, b, t, B, [&](int k) { return sm[(2 + k) * HALO + l]; });
+  sm[2 * HALO + l] = t;
+  sm[3 * HALO + l] = (float)st;
+}
+
+// The same from bin counts kept in registers (fitted mass count / N of bin k
+// from cnt_mass(k)), for a vertex fitted from its members: lo = mn, hi = mx;
+// nf marks non-finite members (all parameters NaN), mn == mx a point mass
+// (mass 1 in bin 0).  The same masses, total, rows and status as the
+// parameter tile and hist_row_table give.
+template <int HALO, int RS, typename Mass>
+__device__ __forceinline__ void hist_row_table_counts(float *sm, float4 *R, int l, int B, bool nf,
+                                                      float mn, float mx, Mass cnt_mass) {
+  // at most 8 bins: every loop unrolled to 8 with the bins past B idle
+  float m[8];
+  float t = 0.f;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    m[q] = 0.f;
+    if (q < B) {
+      m[q] = nf ? qnan() : (mn == mx ? (q == 0 ? 1.f : 0.f) : cnt_mass(q));
+      t += m[q];
+    }
+  }
+  const uint8_t st = nf ? V_NONFINITE : (mn == mx ? V_DEGENERATE : 0);
+  R += l;
+  const float a = nf ? qnan() : mn, b = nf ? qnan() : mx;
   const float4 beyond = make_float4(0.f, t, 0.f, kFar);
   if (a == b) {
-    for (int k = 0; k < hist_r4_rows(B); ++k) R[k * HALO + l] = beyond;
-    return;
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+      if (k <= B) R[k * RS] = beyond;
+  } else {
+    // as hist_rows_build
+    const float w = b - a;
+    const float h = (B & (B - 1)) == 0 ? w * (1.f / (float)B) : w / (float)B, ih = frcp(h);
+    float c = 0.f, sk = t;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (k < B) {
+        c += m[k];
+        const float sn = k + 1 < B ? t - c : 0.f;
+        R[k * RS] = make_float4(sk, t - sk, (sk - sn) * ih, k + 1 < B ? (float)(k + 1) * h : w);
+        sk = sn;
+      }
+    }
+    R[B * RS] = beyond;
   }
-  const float h = (b - a) / (float)B, ih = frcp(h), w = b - a;
-  float c = 0.f, sk = t;
-  for (int k = 0; k < B; ++k) {
-    c += sm[(2 + k) * HALO + l];
-    const float sn = k + 1 < B ? t - c : 0.f;
-    R[k * HALO + l] = make_float4(sk, t - sk, (sk - sn) * ih, k + 1 < B ? (float)(k + 1) * h : w);
-    sk = sn;
-  }
-  R[B * HALO + l] = beyond;
-  R[(B + 1) * HALO + l] = beyond;
+  sm[2 * HALO + l] = t;
+  sm[3 * HALO + l] = (float)st;
 }
 
 // ---------------------------------------------------------------------------
@@ -436,19 +503,33 @@ __device__ __forceinline__ bool stage_members_tma(const Field &f, float *sm, flo
     mbar_init(bar, 1);
     mbar_init_fence();
   }
+  if constexpr (MODEL == kHist && ROWS) {
+    // the masses count / N of up to 255 members (see the per-bin rows below)
+    if (N <= 255)
+      for (int c = threadIdx.x; c <= N; c += NTHREADS)
+        sm[4 * HALO + c] = __fdiv_rn((float)c, (float)N);
+  }
   __syncthreads();
   unsigned phase = 0;
   bool ok = true;
   // load members [k0, k0 + nc) into the box; uniform result
+  // One warp polls the mbarrier while the copy is in flight; the others
+  // wait at the CTA barrier, which takes no issue slots from the warps of
+  // other CTAs.  Once the phase is complete every thread tests it once
+  // more (it returns at once), so each thread acquires the copied data
+  // itself.
   auto load = [&](int k0) -> bool {
     if (threadIdx.x == 0) {
       proxy_async_fence();
       mbar_expect_tx(bar, box_bytes);
       tma_load_3d(box, tmap, tx0 - 4, ty0 - 1, k0, bar);
     }
-    const bool r = mbar_wait(bar, phase);
+    bool r = true;
+    if (threadIdx.x < 32) r = mbar_wait(bar, phase);
+    r = __syncthreads_and(r) != 0;
+    if (r) (void)mbar_wait(bar, phase);
     phase ^= 1u;
-    return __syncthreads_and(r) != 0;
+    return r;
   };
   constexpr bool EP = MODEL == kEpan || MODEL == kGauss;
   float mn[PER], mx[PER], x0[PER];
@@ -512,6 +593,79 @@ __device__ __forceinline__ bool stage_members_tma(const Field &f, float *sm, flo
       sm[HALO + l] = nf[p] ? qnan() : mx[p];
     }
   }
+  if constexpr (MODEL == kHist && ROWS) {
+    // per-bin rows (at most 8 bins): the bin counts of every owned vertex
+    // stay in registers across the boxes, packed 8-bit counters for up to
+    // 255 members, 16-bit ones for more; the rows are built from them once
+    // the last box has been read (they take the box's room).  Masses count /
+    // N come from a table of the N + 1 possible values (ROWS_MASS_TABLE
+    // floats after the parameter tile, filled at the start of the staging)
+    // for up to 255 members.
+    constexpr int RS = hist_r4_stride(HALO);
+    const int B = f.B;
+    const bool wide = N > 255;
+    const float *mtab = sm + 4 * HALO;
+    float sc[PER];
+    bool bin[PER];
+    bool any = false;
+    // 8-bit counters of bins 0..7 in one 64-bit word (up to 255 members);
+    // 16-bit counters of bins 2q, 2q+1 in cA..cD (more members)
+    unsigned long long c8[PER];
+    uint32_t cA[PER], cB[PER], cC[PER], cD[PER];
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+      c8[p] = 0ull;
+      cA[p] = cB[p] = cC[p] = cD[p] = 0u;
+      bin[p] = in[p] && !nf[p] && mn[p] != mx[p];
+      sc[p] = bin[p] ? __fdiv_rn((float)B, __fsub_rn(mx[p], mn[p])) : 0.f;
+      any |= bin[p];
+    }
+    const int last = ((N - 1) / nc) * nc;
+    for (int k0 = last; k0 >= 0; k0 -= nc) {
+      if (k0 != last) {
+        if (!load(k0)) {
+          if (threadIdx.x == 0) mbar_wait(bar, phase ^ 1u);
+          __syncthreads();
+          return false;
+        }
+      }
+      const int kn = min(nc, N - k0);
+      if (any) {
+#pragma unroll
+        for (int p = 0; p < PER; ++p) {
+          if (!bin[p]) continue;
+          const float *col = box + off[p];
+          if (!wide) {
+#pragma unroll 4
+            for (int k = 0; k < kn; ++k)
+              c8[p] += 1ull << (hist_bin(col[k * PLANE], mn[p], sc[p], B) << 3);
+          } else {
+            for (int k = 0; k < kn; ++k) {
+              const int j = hist_bin(col[k * PLANE], mn[p], sc[p], B);
+              const uint32_t inc = 1u << ((j & 1) << 4);
+              const int q = j >> 1;
+              cA[p] += q == 0 ? inc : 0u;
+              cB[p] += q == 1 ? inc : 0u;
+              cC[p] += q == 2 ? inc : 0u;
+              cD[p] += q == 3 ? inc : 0u;
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+      if (!in[p]) continue;
+      hist_row_table_counts<HALO, RS>(
+          sm, R4, lv[p], B, nf[p], mn[p], mx[p], [&](int k) -> float {
+            if (!wide) return mtab[(unsigned)(c8[p] >> (k << 3)) & 255u];
+            const uint32_t w = k < 2 ? cA[p] : (k < 4 ? cB[p] : (k < 6 ? cC[p] : cD[p]));
+            return __fdiv_rn((float)((w >> ((k & 1) << 4)) & 0xFFFFu), (float)N);
+          });
+    }
+    return true;
+  }
   if constexpr (hist_params(MODEL)) {
     const int B = f.B;
     float sc[PER];
@@ -546,27 +700,8 @@ __device__ __forceinline__ bool stage_members_tma(const Field &f, float *sm, flo
           if (!bin[p]) continue;
           const float *col = box + off[p];
           float *w0 = sm + 2 * HALO + lv[p];
-          bool counted = false;
-          if constexpr (ROWS) {
-            // up to 8 bins (always so with per-bin rows) and 255 members:
-            // 8-bit counters packed in two registers, no shared-memory
-            // read-modify-write chain from member to member
-            if (N <= 255) {
-              uint32_t c0 = 0u, c1 = 0u;
-              for (int k = 0; k < kn; ++k) {
-                const int j = hist_bin(col[k * PLANE], mn[p], sc[p], B);
-                const uint32_t inc = 1u << ((j & 3) << 3);
-                c0 += j < 4 ? inc : 0u;
-                c1 += j < 4 ? 0u : inc;
-              }
-              for (int b = 0; b < B; ++b)
-                w0[b * HALO] += (float)(((b < 4 ? c0 : c1) >> ((b & 3) << 3)) & 255u);
-              counted = true;
-            }
-          }
-          if (!counted)
-            for (int k = 0; k < kn; ++k)
-              w0[hist_bin(col[k * PLANE], mn[p], sc[p], B) * HALO] += 1.f;
+          for (int k = 0; k < kn; ++k)
+            w0[hist_bin(col[k * PLANE], mn[p], sc[p], B) * HALO] += 1.f;
         }
       }
       __syncthreads();
@@ -579,13 +714,10 @@ __device__ __forceinline__ bool stage_members_tma(const Field &f, float *sm, flo
           *w = __fdiv_rn(*w, (float)N);
         }
     if constexpr (MODEL == kHist) {
-      // the owner also builds the vertex's tail table (or per-bin rows)
+      // the owner also builds the vertex's tail table
 #pragma unroll
       for (int p = 0; p < PER; ++p)
-        if (in[p]) {
-          if constexpr (ROWS) hist_row_table<HALO>(sm, R4, lv[p], B);
-          else hist_tail_table<HALO>(sm, lv[p], B);
-        }
+        if (in[p]) hist_tail_table<HALO>(sm, lv[p], B);
     }
   }
   return true;
@@ -593,8 +725,13 @@ __device__ __forceinline__ bool stage_members_tma(const Field &f, float *sm, flo
 
 // validity of one participant's parameters; returns status bits and the
 // histogram total mass
-template <int MODEL, int HALO>
+template <int MODEL, int HALO, bool ROWS = false>
 __device__ __forceinline__ uint8_t check_params(const float *sm, int l, int B, float &T) {
+  if constexpr (MODEL == kHist && ROWS) {
+    // precomputed with the per-bin rows
+    T = sm[2 * HALO + l];
+    return (uint8_t)sm[3 * HALO + l];
+  }
   if constexpr (MODEL == kHist) {
     // precomputed by the tail-table pass
     T = sm[(4 + B) * HALO + l];
@@ -707,13 +844,14 @@ template <int MODEL, int TYv, bool SADDLE, bool TABLES_BUILT, bool ROWS>
 __device__ __forceinline__ void integrate_tile(const Field &f, int ty0, int tx0, float *sm,
                                                float4 *R4) {
   constexpr int TY = TYv, TX = 32, HY = TYv + 2, HX = TX + 2, HALO = HY * HX;
+  constexpr int RS = hist_r4_stride(HALO);
   (void)HY;
   (void)R4;
   if constexpr (MODEL == kHist && !TABLES_BUILT) {
     // tail tables or rows of every staged vertex (the TMA staging builds
     // them itself)
     for (int l = threadIdx.x; l < HALO; l += NTHREADS) {
-      if constexpr (ROWS) hist_row_table<HALO>(sm, R4, l, f.B);
+      if constexpr (ROWS) hist_row_table<HALO, RS>(sm, R4, l, f.B);
       else hist_tail_table<HALO>(sm, l, f.B);
     }
     __syncthreads();
@@ -759,11 +897,12 @@ __device__ __forceinline__ void integrate_tile(const Field &f, int ty0, int tx0,
       k += present[i];
     }
     float T[4], Tc;
-    uint8_t st = check_params<MODEL, HALO>(sm, l, f.B, Tc);
+    uint8_t st = check_params<MODEL, HALO, ROWS>(sm, l, f.B, Tc);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       T[i] = 1.f;
-      if (present[i]) st |= check_params<MODEL, HALO>(sm, nl[i], f.B, T[i]) & (V_NONFINITE | V_BAD);
+      if (present[i])
+        st |= check_params<MODEL, HALO, ROWS>(sm, nl[i], f.B, T[i]) & (V_NONFINITE | V_BAD);
     }
     float pmin = 0.f, pmax = 0.f, psad = 0.f;
     int sg[4], sg2[4];
@@ -835,8 +974,7 @@ __device__ __forceinline__ void integrate_tile(const Field &f, int ty0, int tx0,
           if (!present[i]) continue;
           float gt, lt;
           if constexpr (ROWS)
-            hist_tails_at_rows(R4 + nl[i], HALO, B, sm[nl[i]], sm[HALO + nl[i]], T[i], lo1, gt,
-                               lt);
+            hist_tails_at_rows(R4 + nl[i], RS, B, sm[nl[i]], sm[HALO + nl[i]], T[i], lo1, gt, lt);
           else
             hist_tails_at(sm + 2 * HALO + nl[i], HALO, B, sm[nl[i]], sm[HALO + nl[i]], T[i], lo1,
                           gt, lt);
@@ -858,18 +996,18 @@ __device__ __forceinline__ void integrate_tile(const Field &f, int ty0, int tx0,
         for (int i = 0; i < 4; ++i) {
           HistRowWalker &h = nw[i];
           if (!present[i]) {
-            h.init_absent(l);
+            h.init_absent();
             continue;
           }
           const float lo = sm[nl[i]], hi = sm[HALO + nl[i]];
-          h.init(nl[i], lo - lo1, T[i]);
-          h.seek0<HALO>(R4, B, lo == hi ? 0.f : (hi - lo) / (float)B);
+          h.init(R4 + nl[i], lo - lo1, T[i]);
+          h.seek0<RS>(R4 + nl[i], B, lo == hi ? 0.f : (hi - lo) / (float)B);
         }
         if constexpr (!SADDLE) {
-          hist_walk_rows<HALO>(R4, l, B, hi1 - lo1, nw, pmin, pmax);
+          hist_walk_rows<RS>(R4 + l, B, hi1 - lo1, nw, pmin, pmax);
         } else {
           float t1, t2;
-          hist_walk_rows<HALO, true>(R4, l, B, hi1 - lo1, nw, t1, t2, sg);
+          hist_walk_rows<RS, true>(R4 + l, B, hi1 - lo1, nw, t1, t2, sg);
           psad = t1 + t2;
         }
       } else if ((do_mm || do_sad) && !ROWS) {
