@@ -95,7 +95,7 @@ struct TileOcc {
   static constexpr int value =
       MODEL == kUniform ? 5
                         : (MODEL == kEpan ? 5
-                                          : (MODEL == kHist ? (ROWS ? 3 : 3)
+                                          : (MODEL == kHist ? (ROWS ? 4 : 3)
                                                             : (MODEL == kSemi ? 4 : 2)));
 };
 

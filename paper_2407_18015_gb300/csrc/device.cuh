@@ -292,6 +292,12 @@ __device__ __forceinline__ int hist_bin(float x, float lo, float s, int B) {
   int i = (int)floorf(__fmul_rn(__fsub_rn(x, lo), s));
   return min(max(i, 0), B - 1);
 }
+// hist_bin for a finite member x >= lo (lo the members' minimum, s > 0):
+// (x - lo) * s is then >= 0, so truncation is the floor and the lower clamp
+// never acts -- the same bin as hist_bin
+__device__ __forceinline__ int hist_bin_nonneg(float x, float lo, float s, int B) {
+  return min(__float2int_rz(__fmul_rn(__fsub_rn(x, lo), s)), B - 1);
+}
 
 // ---------------------------------------------------------------------------
 // closed-form integration, uniform model
@@ -1291,36 +1297,36 @@ __device__ __forceinline__ void hist_walk(const float *S0, int coff, int B, floa
   pmax = fmaxf(acc.y, 0.f);
 }
 
-// Shared-memory reads that happen only where p holds (one predicated
-// instruction, no branch); where p is false the result is unspecified and
-// must not be used.  addr: a shared-state-space address.
-__device__ __forceinline__ float4 lds128_if(bool p, uint32_t addr) {
-  float4 r;
-  asm(
-      "{\n .reg .pred q;\n setp.ne.b32 q, %5, 0;\n"
-      " @q ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n}"
-      : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
-      : "r"(addr), "r"((int)p));
-  return r;
+// Crossing step of a walker over shared-memory rows: if nx <= x1, read the
+// 16-byte row at addr into v and advance addr by `stride` bytes; else leave
+// both.  One comparison, one predicated read and one predicated add, no
+// branch.  addr: a shared-state-space address.
+template <unsigned stride>
+__device__ __forceinline__ void lds128_cross(float nx, float x1, uint32_t &addr, float4 &v) {
+  asm("{\n .reg .pred q;\n setp.le.f32 q, %5, %6;\n"
+      " @q ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n"
+      " @q add.u32 %4, %4, %7;\n}"
+      : "+f"(v.x), "+f"(v.y), "+f"(v.z), "+f"(v.w), "+r"(addr)
+      : "f"(nx), "f"(x1), "n"(stride));
 }
-__device__ __forceinline__ float2 lds64_if(bool p, uint32_t addr) {
-  float2 r;
-  asm(
-      "{\n .reg .pred q;\n setp.ne.b32 q, %3, 0;\n @q ld.shared.v2.f32 {%0, %1}, [%2];\n}"
-      : "=f"(r.x), "=f"(r.y)
-      : "r"(addr), "r"((int)p));
-  return r;
+template <unsigned stride>
+__device__ __forceinline__ void lds64_cross(float nx, float x1, uint32_t &addr, float2 &v) {
+  asm("{\n .reg .pred q;\n setp.le.f32 q, %3, %4;\n"
+      " @q ld.shared.v2.f32 {%0, %1}, [%2];\n"
+      " @q add.u32 %2, %2, %5;\n}"
+      : "+f"(v.x), "+f"(v.y), "+r"(addr)
+      : "f"(nx), "f"(x1), "n"(stride));
 }
 
 // Per-bin rows of a staged histogram vertex for the forward walk: float4
 // rows at R[k * RS + l], k = 0..B.  Row k < B describes bin k: (S_k,
 // T - S_k, slope_k, e_{k+1} - lo), with the tail S_k = T - (m_0 + ... +
 // m_{k-1}), slope_k = (S_k - S_{k+1}) / h (the bin's density, m_k / h, in
-// the mixture form) and e_{k+1} - lo = (k + 1) h (hi - lo for the last edge).
-// Row B is (0, T, 0, kFar), beyond the support.  A point mass has every row
-// (0, T, 0, kFar): its one edge takes the survival from T to 0.  A walker
-// reads a row only when it crosses an edge, at most B + 1 times, so no row
-// past B is ever read.
+// the mixture form) and e_{k+1} - lo = (k + 1) h (hi - lo for the last
+// edge).  Row B is (0, T, 0, kFar), beyond the support.  A point mass has
+// every row (0, T, 0, kFar): its one edge takes the survival from T to 0.
+// A walker reads a row only when it crosses an edge, at most B + 1 times,
+// so no row past B is ever read.
 __host__ __device__ constexpr int hist_r4_rows(int B) { return B + 1; }
 
 // Row stride of the per-bin rows of a halo of `halo` vertices, in float4:
@@ -1333,53 +1339,44 @@ __host__ __device__ constexpr int hist_r4_stride(int halo) { return (halo + 7) &
 
 // A neighbour's survival G and CDF F walked bin by bin over the per-bin
 // rows: before the support (G, F) = (T, 0); on bin k G falls and F rises by
-// slope_k per unit of x; beyond it (0, T).  The walker holds (G, F) at the
-// walk's current position and advances them by the step length; crossing an
-// edge (one predicated 16-byte read) restarts them from the row's exact
-// values (S_k, T - S_k), which also carries the jump of a point mass.  An
-// absent neighbour is the constant (1, 1) that never reaches an edge.
+// slope_k per unit of x; beyond it (0, T).  The walker holds the row of its
+// current segment, (G, F, slope, next edge - lo) with G and F taken at the
+// walk's current position, advances G and F by the step length and,
+// crossing an edge, lets one predicated 16-byte read replace the whole state
+// with the next row, whose (S_k, T - S_k) are the exact values at that edge
+// (which also carries the jump of a point mass).  An absent neighbour is the
+// constant G = F = 1 that never reaches an edge.
 struct HistRowWalker {
-  uint32_t addr;  // shared-memory address of the row read at the next crossing
+  float4 r;       // (G, F at the current position, slope, next edge - lo)
   float lam;      // support start in the centre's frame
-  float nx;       // next edge in the centre's frame (kFar: none left)
-  float2 sv;      // (-slope, slope): the change of (G, F) per unit of x
-  float2 gf;      // (G, F) at the walk's current position
+  uint32_t addr;  // shared-memory address of the row read at the next crossing
+  __device__ __forceinline__ float nx() const { return lam + r.w; }
   __device__ __forceinline__ void init_absent() {
-    addr = 0u; lam = 0.f; nx = kFar;
-    sv = make_float2(0.f, 0.f); gf = make_float2(1.f, 1.f);
+    r = make_float4(1.f, 1.f, 0.f, kFar); lam = 0.f; addr = 0u;
   }
+  // before the support: (G, F) = (T, 0), the first edge is the support start
   __device__ __forceinline__ void init(const float4 *row0, float lam_, float T) {
-    addr = static_cast<uint32_t>(__cvta_generic_to_shared(row0)); lam = lam_; nx = lam_;
-    sv = make_float2(0.f, 0.f); gf = make_float2(T, 0.f);
+    r = make_float4(T, 0.f, 0.f, 0.f); lam = lam_;
+    addr = static_cast<uint32_t>(__cvta_generic_to_shared(row0));
   }
-  // (G, F) a distance d further on the current segment
-  __device__ __forceinline__ float2 at(float d) const {
-    return __ffma2_rn(sv, make_float2(d, d), gf);
-  }
-  // Move to x1 (where the current segment gives `pr`): cross the next edge
-  // if it is at or below x1 -- it is then exactly at x1, the walk's next
-  // breakpoint being the smallest next edge -- and start the new segment
-  // from its row.  Branch free: the row read is predicated, the state
-  // updates are selects.
+  // Move to x1 (G and F there given): cross the next edge if it is at or
+  // below x1 -- it is then exactly at x1, the walk's next breakpoint being
+  // the smallest next edge -- and take the new segment's row.
   template <int RS>
-  __device__ __forceinline__ void step(float x1, float2 pr) {
-    const bool cr = nx <= x1;
-    const float4 t = lds128_if(cr, addr);
-    gf.x = cr ? t.x : pr.x;
-    gf.y = cr ? t.y : pr.y;
-    sv.x = cr ? -t.z : sv.x;
-    sv.y = cr ? t.z : sv.y;
-    nx = cr ? lam + t.w : nx;
-    addr += cr ? (uint32_t)(RS * 16) : 0u;
+  __device__ __forceinline__ void step(float x1, float g1, float f1) {
+    const float n = nx();
+    r.x = g1;
+    r.y = f1;
+    lds128_cross<(unsigned)(RS * 16)>(n, x1, addr, r);
   }
   // From the initial state, cross every edge at or below 0 at once (the
   // state step() would reach edge by edge; the count of such edges comes
-  // from -lam / h and is checked against the edges of the rows), and set
-  // (G, F) to their values at 0.
+  // from -lam / h and is checked against the edges of the rows), and set G
+  // and F to their values at 0.
   template <int RS>
   __device__ __forceinline__ void seek0(const float4 *row0, int B, float h) {
-    if (nx > 0.f) return;  // the first edge is above 0 (also: absent)
-    int j = 1;             // edges e_0 .. e_{j-1} are at or below 0
+    if (nx() > 0.f) return;  // the first edge is above 0 (also: absent)
+    int j = 1;               // edges e_0 .. e_{j-1} are at or below 0
     float el;
     if (h > 0.f) {
       auto edge = [&](int i) { return i == 0 ? lam : lam + row0[(i - 1) * RS].w; };
@@ -1388,14 +1385,13 @@ struct HistRowWalker {
       if (j >= 2 && edge(j - 1) > 0.f) --j;
       el = edge(j - 1);
     } else {
-      el = lam;            // a point mass: its one edge
+      el = lam;              // a point mass: its one edge
     }
-    const float4 t = row0[(j - 1) * RS];
+    r = row0[(j - 1) * RS];
     // on the segment that starts at el <= 0: G(x) = S - slope (x - el) and
     // F(x) = T - S + slope (x - el), taken at x = 0
-    gf = make_float2(fmaf(t.z, el, t.x), fmaf(-t.z, el, t.y));
-    sv = make_float2(-t.z, t.z);
-    nx = lam + t.w;
+    r.x = fmaf(r.z, el, r.x);
+    r.y = fmaf(-r.z, el, r.y);
     addr = static_cast<uint32_t>(__cvta_generic_to_shared(row0 + j * RS));
   }
 };
@@ -1423,41 +1419,37 @@ __device__ __forceinline__ void hist_walk_rows(const float4 *crow, int B, float 
   // the centre needs only the density and the next edge of its bin: the
   // (z, w) half of each row
   uint32_t addr_c = static_cast<uint32_t>(__cvta_generic_to_shared(crow + RS)) + 8u;
-  float dens, nxc;
+  float2 dc;  // (density, next edge) of the centre's current bin
   {
     const float4 t = crow[0];
-    dens = t.z;
-    nxc = t.w;
+    dc = make_float2(t.z, t.w);
   }
-  auto pair = [&](int i, float2 v) {
-    if constexpr (SADDLE) return sg[i] > 0 ? v : make_float2(v.y, v.x);
-    else return v;
+  auto pair = [&](int i, float g, float ff) {
+    if constexpr (SADDLE) return sg[i] > 0 ? make_float2(g, ff) : make_float2(ff, g);
+    else return make_float2(g, ff);
   };
   float2 acc = make_float2(0.f, 0.f);
   float x0 = 0.f;
   const int max_steps = 5 * (B + 1) + 4;
 #pragma unroll 1
   for (int step = 0; step < max_steps && x0 < W1; ++step) {
-    const float x1 = fminf(fminf(fminf(nw[0].nx, nw[1].nx), fminf(nw[2].nx, nw[3].nx)), nxc);
+    const float x1 =
+        fminf(fminf(fminf(nw[0].nx(), nw[1].nx()), fminf(nw[2].nx(), nw[3].nx())), dc.y);
     const float d = x1 - x0;
-    float2 pr[4], L[4], Rv[4];
+    float g1[4], f1[4];
+    float2 L[4], Rv[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      pr[i] = nw[i].at(d);
-      L[i] = pair(i, nw[i].gf);
-      Rv[i] = pair(i, pr[i]);
+      g1[i] = fmaf(-nw[i].r.z, d, nw[i].r.x);
+      f1[i] = fmaf(nw[i].r.z, d, nw[i].r.y);
+      L[i] = pair(i, nw[i].r.x, nw[i].r.y);
+      Rv[i] = pair(i, g1[i], f1[i]);
     }
-    const float wgt = d * dens;
+    const float wgt = d * dc.x;
     acc = __ffma2_rn(make_float2(wgt, wgt), bern_mean4_pairs_x2(L, Rv), acc);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) nw[i].step<RS>(x1, pr[i]);
-    {
-      const bool cr = nxc <= x1;
-      const float2 t = lds64_if(cr, addr_c);
-      dens = cr ? t.x : dens;
-      nxc = cr ? t.y : nxc;
-      addr_c += cr ? (uint32_t)(RS * 16) : 0u;
-    }
+    for (int i = 0; i < 4; ++i) nw[i].step<RS>(x1, g1[i], f1[i]);
+    lds64_cross<(unsigned)(RS * 16)>(dc.y, x1, addr_c, dc);
     x0 = x1;
   }
   pmin = fmaxf(acc.x, 0.f);

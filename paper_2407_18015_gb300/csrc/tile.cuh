@@ -461,11 +461,14 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
   for (int i = 0; i < (1 << 20); ++i) {
     uint32_t done;
+    // each poll may suspend the thread for up to about a microsecond (the
+    // time hint, in ns) until the phase completes, so the waiting warp
+    // takes few issue slots
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
         " selp.u32 %0, 1, 0, p;\n}"
         : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "n"(1000)
         : "memory");
     if (done) return true;
   }
@@ -638,7 +641,7 @@ __device__ __forceinline__ bool stage_members_tma(const Field &f, float *sm, flo
           if (!wide) {
 #pragma unroll 4
             for (int k = 0; k < kn; ++k)
-              c8[p] += 1ull << (hist_bin(col[k * PLANE], mn[p], sc[p], B) << 3);
+              c8[p] += 1ull << (hist_bin_nonneg(col[k * PLANE], mn[p], sc[p], B) << 3);
           } else {
             for (int k = 0; k < kn; ++k) {
               const int j = hist_bin(col[k * PLANE], mn[p], sc[p], B);
@@ -1001,7 +1004,10 @@ __device__ __forceinline__ void integrate_tile(const Field &f, int ty0, int tx0,
           }
           const float lo = sm[nl[i]], hi = sm[HALO + nl[i]];
           h.init(R4 + nl[i], lo - lo1, T[i]);
-          h.seek0<RS>(R4 + nl[i], B, lo == hi ? 0.f : (hi - lo) / (float)B);
+          // the bin width only estimates how many edges lie below 0 (seek0
+          // checks the estimate against the edges of the rows), so it need
+          // not be the rows' own (hi - lo) / B
+          h.seek0<RS>(R4 + nl[i], B, lo == hi ? 0.f : (hi - lo) * (1.f / (float)B));
         }
         if constexpr (!SADDLE) {
           hist_walk_rows<RS>(R4 + l, B, hi1 - lo1, nw, pmin, pmax);
