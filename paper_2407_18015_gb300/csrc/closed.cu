@@ -87,36 +87,28 @@ __global__ void __launch_bounds__(256) fit_kernel(Field f) {
 // ---------------------------------------------------------------------------
 // tile kernel
 
-// resident CTAs per SM each model's register budget is tuned for (ROWS:
-// histogram tiles that walk per-bin rows, four CTAs per SM when their
-// members are staged by the tensor memory accelerator)
-template <int MODEL, bool ROWS = false>
+// resident CTAs per SM each model's register budget is tuned for.  RB > 0:
+// histogram tiles that walk per-bin rows of at most RB bins -- four CTAs
+// per SM for 8 bins, two for 16 (their rows' shared memory allows no more).
+template <int MODEL, int RB = 0>
 struct TileOcc {
   static constexpr int value =
       MODEL == kUniform ? 5
                         : (MODEL == kEpan ? 5
-                                          : (MODEL == kHist ? (ROWS ? 4 : 3)
+                                          : (MODEL == kHist ? (RB == 8 ? 4 : (RB == 16 ? 2 : 3))
                                                             : (MODEL == kSemi ? 4 : 2)));
 };
 
 // tile height: 8 rows for the uniform and histogram models and the
 // estimator (a 20-member box fits next to the parameter tile, and the
-// histogram's per-bin rows fit at three CTAs per SM), 16 for the Gaussian
-// and, from parameters, Epanechnikov models (a smaller halo share).  The
-// fused Epanechnikov kernel takes 8 rows when all members fit one box of 8
-// rows, else 16: with several boxes either way, the halo's share of the
-// compensated sums outweighs the extra boxes.  Histograms with more bins
-// than the per-bin rows allow take 16 rows.
+// histogram's per-bin rows fit), 16 for the Gaussian and, from parameters,
+// Epanechnikov models (a smaller halo share).  The fused Epanechnikov kernel
+// takes 8 rows when all members fit one box of 8 rows, else 16: with several
+// boxes either way, the halo's share of the compensated sums outweighs the
+// extra boxes.  Histograms without per-bin rows take 16 rows.
 template <int MODEL>
 struct TileH {
   static constexpr int value = (MODEL == kGauss || MODEL == kEpan) ? TY : 8;
-};
-
-// histograms walk per-bin rows at 8-row tiles (the launcher takes 8 rows
-// only when they fit), the segment walker at 16
-template <int MODEL, int TYm>
-struct HistRows {
-  static constexpr bool value = MODEL == kHist && TYm == 8;
 };
 
 // floats of the parameter tile: the model's tile, or for per-bin-row
@@ -133,38 +125,39 @@ __host__ __device__ constexpr int r4_floats(int B, int TYv) {
   return 4 * hist_r4_rows(B) * hist_r4_stride((TYv + 2) * (TX + 2));
 }
 
-// Shared memory: the parameter tile, then (HistRows) the per-bin rows,
+// Shared memory: the parameter tile, then (RB > 0) the per-bin rows,
 // 16-byte aligned.
-template <int MODEL, bool FROM_MEMBERS, bool SADDLE, int TYm>
-__global__ void __launch_bounds__(NTHREADS, TileOcc<MODEL>::value) tile_kernel(Field f, int tiles_x) {
+template <int MODEL, bool FROM_MEMBERS, bool SADDLE, int TYm, int RB>
+__global__ void __launch_bounds__(NTHREADS, (TileOcc<MODEL, RB>::value))
+    tile_kernel(Field f, int tiles_x) {
   extern __shared__ __align__(16) float sm[];
   const int tile = blockIdx.x;
-  constexpr bool ROWS = HistRows<MODEL, TYm>::value;
+  constexpr bool ROWS = RB > 0;
   float4 *R4 = nullptr;
   if constexpr (ROWS)
     R4 = reinterpret_cast<float4 *>(
         sm + ((param_tile_floats<MODEL, TYm, ROWS>(f.B, true) + 3) & ~3LL));
-  process_tile<MODEL, FROM_MEMBERS, TYm, SADDLE, false, ROWS>(
+  process_tile<MODEL, FROM_MEMBERS, TYm, SADDLE, false, RB>(
       f, f.y0 + (tile / tiles_x) * TYm, (tile % tiles_x) * TX, sm, nullptr, nullptr, nullptr, R4);
 }
 
 // The same with the members staged by the tensor memory accelerator: shared
 // memory holds the member box (nc x (TYm + 2) x 40 floats, 128-byte
-// aligned) -- for HistRows histograms the same room then takes the per-bin
-// rows, once the box is no longer read -- then the parameter tile, then the
+// aligned) -- for per-bin-row histograms the same room then takes the rows,
+// once the box is no longer read -- then the parameter tile, then the
 // mbarrier.
-template <int MODEL, bool SADDLE, int TYm>
-__global__ void __launch_bounds__(NTHREADS, (TileOcc<MODEL, HistRows<MODEL, TYm>::value>::value))
+template <int MODEL, bool SADDLE, int TYm, int RB>
+__global__ void __launch_bounds__(NTHREADS, (TileOcc<MODEL, RB>::value))
     tile_kernel_tma(Field f, int tiles_x, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(128) float smem[];
   const int tile = blockIdx.x;
   const int box_floats = f.tma_nc * (TYm + 2) * kBoxW;
-  constexpr bool ROWS = HistRows<MODEL, TYm>::value;
+  constexpr bool ROWS = RB > 0;
   const int r4 = ROWS ? r4_floats(f.B, TYm) : 0;
   float *sm = smem + max(box_floats, r4);
   const long long tile_f = param_tile_floats<MODEL, TYm, ROWS>(f.B, false);
   uint64_t *bar = reinterpret_cast<uint64_t *>(sm + ((tile_f + 1) & ~1LL));
-  process_tile<MODEL, true, TYm, SADDLE, true, ROWS>(
+  process_tile<MODEL, true, TYm, SADDLE, true, RB>(
       f, f.y0 + (tile / tiles_x) * TYm, (tile % tiles_x) * TX, sm, &tmap, smem, bar,
       ROWS ? reinterpret_cast<float4 *>(smem) : nullptr);
 }
@@ -224,13 +217,13 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 // Members per TMA box next to a TYm-row parameter tile at the model's
 // occupancy (0: not even one), capped at N and at the box limit of 256.
-template <int MODEL, int TYm>
+template <int MODEL, int TYm, int RB>
 static int tma_box_members(int N, int B) {
-  constexpr bool ROWS = HistRows<MODEL, TYm>::value;
+  constexpr bool ROWS = RB > 0;
   const size_t tile_b =
       (size_t)((param_tile_floats<MODEL, TYm, ROWS>(B, false) + 1) & ~1LL) * sizeof(float) + 16;
   const size_t per_member = (size_t)(TYm + 2) * kBoxW * sizeof(float);
-  const size_t budget = (size_t)227 * 1024 / TileOcc<MODEL, ROWS>::value - 1024;
+  const size_t budget = (size_t)227 * 1024 / TileOcc<MODEL, RB>::value - 1024;
   if (budget < tile_b + per_member) return 0;
   const size_t nc = (budget - tile_b) / per_member;
   return (int)std::min<size_t>(nc, (size_t)std::min(N, 256));
@@ -239,19 +232,19 @@ static int tma_box_members(int N, int B) {
 // Launch with TMA member staging when the members allow it (W % 4 == 0, a
 // 16-byte aligned base) and a box of at least one member fits next to the
 // parameter tile at the model's occupancy; returns false to fall back.
-template <int MODEL, bool SADDLE, int TYm>
+template <int MODEL, bool SADDLE, int TYm, int RB>
 static bool launch_tile_tma(const Field &f, int tiles_x, int tiles, cudaStream_t s,
                             cudaError_t *err) {
   if (f.W % 4 != 0 || (reinterpret_cast<uintptr_t>(f.ens) & 15) != 0) return false;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
   // histogram per-bin rows, in the room of the member box
-  constexpr bool ROWS = HistRows<MODEL, TYm>::value;
+  constexpr bool ROWS = RB > 0;
   const size_t tile_b =
       (size_t)((param_tile_floats<MODEL, TYm, ROWS>(f.B, false) + 1) & ~1LL) * sizeof(float) + 16;
   const size_t per_member = (size_t)(TYm + 2) * kBoxW * sizeof(float);
-  const size_t budget = (size_t)227 * 1024 / TileOcc<MODEL, ROWS>::value - 1024;
-  const int nc = tma_box_members<MODEL, TYm>(f.N, f.B);
+  const size_t budget = (size_t)227 * 1024 / TileOcc<MODEL, RB>::value - 1024;
+  const int nc = tma_box_members<MODEL, TYm, RB>(f.N, f.B);
   if (nc < 1) return false;
   const size_t r4_b = ROWS ? (size_t)r4_floats(f.B, TYm) * sizeof(float) : 0;
   if (tile_b + r4_b > budget) return false;
@@ -274,7 +267,7 @@ static bool launch_tile_tma(const Field &f, int tiles_x, int tiles, cudaStream_t
     return false;
   }
   if (!attr_set[dev].load(std::memory_order_acquire)) {
-    if (cudaFuncSetAttribute(tile_kernel_tma<MODEL, SADDLE, TYm>,
+    if (cudaFuncSetAttribute(tile_kernel_tma<MODEL, SADDLE, TYm, RB>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
         cudaSuccess) {
       cudaGetLastError();
@@ -285,16 +278,16 @@ static bool launch_tile_tma(const Field &f, int tiles_x, int tiles, cudaStream_t
   Field g = f;
   g.tma_nc = nc;
   const size_t smem = std::max((size_t)nc * per_member, r4_b) + tile_b;
-  tile_kernel_tma<MODEL, SADDLE, TYm><<<tiles, NTHREADS, smem, s>>>(g, tiles_x, map);
+  tile_kernel_tma<MODEL, SADDLE, TYm, RB><<<tiles, NTHREADS, smem, s>>>(g, tiles_x, map);
   *err = cudaGetLastError();
   return true;
 }
 
-template <int MODEL, bool FM, bool SADDLE, int TYm>
+template <int MODEL, bool FM, bool SADDLE, int TYm, int RB>
 static cudaError_t launch_tile_h(const Field &f, cudaStream_t s) {
   size_t smem = (size_t)tile_floats(MODEL, f.B, TYm) * sizeof(float);
   // histogram per-bin rows after the tile (launch_tile checked that they fit)
-  if constexpr (HistRows<MODEL, TYm>::value)
+  if constexpr (RB > 0)
     smem = (size_t)((param_tile_floats<MODEL, TYm, true>(f.B, true) + 3) & ~3LL) * sizeof(float) +
            (size_t)r4_floats(f.B, TYm) * sizeof(float);
   // per device: the attribute is set once (several host threads may race to
@@ -309,8 +302,8 @@ static cudaError_t launch_tile_h(const Field &f, cudaStream_t s) {
     // table, total, status and ordering scratch, the estimator its running
     // mass sums: 95 KB and 173 KB at 10 x 34), or the per-bin rows' bound
     const size_t most = std::max((size_t)tile_floats(MODEL, kMaxBins, TYm) * sizeof(float),
-                                 MODEL == kHist ? (size_t)227 * 1024 / TileOcc<MODEL>::value : 0);
-    e = cudaFuncSetAttribute(tile_kernel<MODEL, FM, SADDLE, TYm>,
+                                 MODEL == kHist ? (size_t)227 * 1024 : (size_t)0);
+    e = cudaFuncSetAttribute(tile_kernel<MODEL, FM, SADDLE, TYm, RB>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
     if (e != cudaSuccess) {
       cudaGetLastError();  // do not leave the failed call as the last error
@@ -326,32 +319,42 @@ static cudaError_t launch_tile_h(const Field &f, cudaStream_t s) {
   if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
   if constexpr (FM) {
     cudaError_t te = cudaSuccess;
-    if (launch_tile_tma<MODEL, SADDLE, TYm>(g, tiles_x, (int)tiles, s, &te)) return te;
+    if (launch_tile_tma<MODEL, SADDLE, TYm, RB>(g, tiles_x, (int)tiles, s, &te)) return te;
   }
-  tile_kernel<MODEL, FM, SADDLE, TYm><<<(int)tiles, NTHREADS, smem, s>>>(g, tiles_x);
+  tile_kernel<MODEL, FM, SADDLE, TYm, RB><<<(int)tiles, NTHREADS, smem, s>>>(g, tiles_x);
   return cudaGetLastError();
+}
+
+// bytes of a per-bin-row histogram tile of TYm rows at B bins, the fused
+// kernel's layout (members counted in registers: small parameter tile)
+static size_t hist_rows_bytes(int B, int TYm) {
+  return (size_t)((hist_rows_tile_floats(B, TYm, false) + 3) & ~3LL) * sizeof(float) +
+         (size_t)r4_floats(B, TYm) * sizeof(float) + 16;
 }
 
 template <int MODEL, bool FM, bool SADDLE>
 static cudaError_t launch_tile(const Field &f, cudaStream_t s) {
   if constexpr (MODEL == kEpan && FM) {
-    if (f.N <= tma_box_members<kEpan, 8>(f.N, f.B)) return launch_tile_h<MODEL, FM, SADDLE, 8>(f, s);
+    if (f.N <= tma_box_members<kEpan, 8, 0>(f.N, f.B))
+      return launch_tile_h<MODEL, FM, SADDLE, 8, 0>(f, s);
   }
   if constexpr (MODEL == kHist) {
-    // Per-bin rows on 8-row tiles when they fit at four CTAs per SM next to
-    // the small parameter tile (counts in registers: at most 8 bins and
-    // 65535 members); otherwise the segment walker on 16-row tiles, where
-    // the smaller halo wins.  The per-thread staging (members not TMA
-    // aligned) and the from-parameters path hold the masses in the tile
-    // and run the same rows at three CTAs per SM.
-    const size_t rows_end = (size_t)((hist_rows_tile_floats(f.B, 8, false) + 3) & ~3LL) *
-                                sizeof(float) +
-                            (size_t)r4_floats(f.B, 8) * sizeof(float) + 16;
-    if (f.B > 8 || (FM && f.N > 65535) ||
-        rows_end > (size_t)227 * 1024 / TileOcc<kHist, true>::value - 1024)
-      return launch_tile_h<MODEL, FM, SADDLE, TY>(f, s);
+    // Per-bin rows on 8-row tiles: up to 8 bins at four CTAs per SM, up to
+    // 16 (fitted from members, counts in registers: at most 65535 members)
+    // at two; otherwise the segment walker on 16-row tiles, where the
+    // smaller halo wins.  The per-thread staging (members not TMA aligned)
+    // and the from-parameters path hold the masses in the tile and run the
+    // same rows.
+    const bool counts_ok = !FM || f.N <= 65535;
+    if (counts_ok && f.B <= 8 &&
+        hist_rows_bytes(f.B, 8) <= (size_t)227 * 1024 / TileOcc<kHist, 8>::value - 1024)
+      return launch_tile_h<MODEL, FM, SADDLE, 8, 8>(f, s);
+    if (FM && counts_ok && f.B <= 16 &&
+        hist_rows_bytes(f.B, 8) <= (size_t)227 * 1024 / TileOcc<kHist, 16>::value - 1024)
+      return launch_tile_h<MODEL, FM, SADDLE, 8, 16>(f, s);
+    return launch_tile_h<MODEL, FM, SADDLE, TY, 0>(f, s);
   }
-  return launch_tile_h<MODEL, FM, SADDLE, TileH<MODEL>::value>(f, s);
+  return launch_tile_h<MODEL, FM, SADDLE, TileH<MODEL>::value, 0>(f, s);
 }
 
 template <bool SADDLE>

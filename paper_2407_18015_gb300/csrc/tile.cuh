@@ -378,14 +378,14 @@ __device__ __forceinline__ void hist_row_table(float *sm, float4 *R, int l, int 
 // nf marks non-finite members (all parameters NaN), mn == mx a point mass
 // (mass 1 in bin 0).  The same masses, total, rows and status as the
 // parameter tile and hist_row_table give.
-template <int HALO, int RS, typename Mass>
+template <int HALO, int RS, int RB, typename Mass>
 __device__ __forceinline__ void hist_row_table_counts(float *sm, float4 *R, int l, int B, bool nf,
                                                       float mn, float mx, Mass cnt_mass) {
-  // at most 8 bins: every loop unrolled to 8 with the bins past B idle
-  float m[8];
+  // at most RB bins: every loop unrolled to RB with the bins past B idle
+  float m[RB];
   float t = 0.f;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
+  for (int q = 0; q < RB; ++q) {
     m[q] = 0.f;
     if (q < B) {
       m[q] = nf ? qnan() : (mn == mx ? (q == 0 ? 1.f : 0.f) : cnt_mass(q));
@@ -398,7 +398,7 @@ __device__ __forceinline__ void hist_row_table_counts(float *sm, float4 *R, int 
   const float4 beyond = make_float4(0.f, t, 0.f, kFar);
   if (a == b) {
 #pragma unroll
-    for (int k = 0; k < 9; ++k)
+    for (int k = 0; k <= RB; ++k)
       if (k <= B) R[k * RS] = beyond;
   } else {
     // as hist_rows_build
@@ -406,7 +406,7 @@ __device__ __forceinline__ void hist_row_table_counts(float *sm, float4 *R, int 
     const float h = (B & (B - 1)) == 0 ? w * (1.f / (float)B) : w / (float)B, ih = frcp(h);
     float c = 0.f, sk = t;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < RB; ++k) {
       if (k < B) {
         c += m[k];
         const float sn = k + 1 < B ? t - c : 0.f;
@@ -481,7 +481,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
 // ROWS: histogram per-bin rows into R4 in place of the tail tables (R4 may
 // overlap the box: the rows are written after the barrier that ends the last
 // read of the box).
-template <int MODEL, int TYv, bool ROWS>
+template <int MODEL, int TYv, int RB>
 __device__ __forceinline__ bool stage_members_tma(const Field &f, float *sm, float *box,
                                                   uint64_t *bar, const CUtensorMap *tmap,
                                                   int ty0, int tx0, float4 *R4) {
@@ -506,7 +506,7 @@ __device__ __forceinline__ bool stage_members_tma(const Field &f, float *sm, flo
     mbar_init(bar, 1);
     mbar_init_fence();
   }
-  if constexpr (MODEL == kHist && ROWS) {
+  if constexpr (MODEL == kHist && RB > 0) {
     // the masses count / N of up to 255 members (see the per-bin rows below)
     if (N <= 255)
       for (int c = threadIdx.x; c <= N; c += NTHREADS)
@@ -596,29 +596,27 @@ __device__ __forceinline__ bool stage_members_tma(const Field &f, float *sm, flo
       sm[HALO + l] = nf[p] ? qnan() : mx[p];
     }
   }
-  if constexpr (MODEL == kHist && ROWS) {
-    // per-bin rows (at most 8 bins): the bin counts of every owned vertex
-    // stay in registers across the boxes, packed 8-bit counters for up to
-    // 255 members, 16-bit ones for more; the rows are built from them once
-    // the last box has been read (they take the box's room).  Masses count /
-    // N come from a table of the N + 1 possible values (ROWS_MASS_TABLE
-    // floats after the parameter tile, filled at the start of the staging)
-    // for up to 255 members.
+  if constexpr (MODEL == kHist && RB > 0) {
+    // per-bin rows (at most RB bins): the bin counts of every owned vertex
+    // stay in registers across the boxes, packed 8-bit counters (eight per
+    // 64-bit word) for up to 255 members, 16-bit ones (four per word) for
+    // more; the rows are built from them once the last box has been read
+    // (they take the box's room).  Masses count / N come from a table of
+    // the N + 1 possible values (ROWS_MASS_TABLE floats after the parameter
+    // tile, filled at the start of the staging) for up to 255 members.
     constexpr int RS = hist_r4_stride(HALO);
+    constexpr int NW8 = RB / 8, NW16 = RB / 4;
     const int B = f.B;
     const bool wide = N > 255;
     const float *mtab = sm + 4 * HALO;
     float sc[PER];
     bool bin[PER];
     bool any = false;
-    // 8-bit counters of bins 0..7 in one 64-bit word (up to 255 members);
-    // 16-bit counters of bins 2q, 2q+1 in cA..cD (more members)
-    unsigned long long c8[PER];
-    uint32_t cA[PER], cB[PER], cC[PER], cD[PER];
+    unsigned long long cw[PER][NW16];
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
-      c8[p] = 0ull;
-      cA[p] = cB[p] = cC[p] = cD[p] = 0u;
+#pragma unroll
+      for (int w = 0; w < NW16; ++w) cw[p][w] = 0ull;
       bin[p] = in[p] && !nf[p] && mn[p] != mx[p];
       sc[p] = bin[p] ? __fdiv_rn((float)B, __fsub_rn(mx[p], mn[p])) : 0.f;
       any |= bin[p];
@@ -640,17 +638,22 @@ __device__ __forceinline__ bool stage_members_tma(const Field &f, float *sm, flo
           const float *col = box + off[p];
           if (!wide) {
 #pragma unroll 4
-            for (int k = 0; k < kn; ++k)
-              c8[p] += 1ull << (hist_bin_nonneg(col[k * PLANE], mn[p], sc[p], B) << 3);
+            for (int k = 0; k < kn; ++k) {
+              const int j = hist_bin_nonneg(col[k * PLANE], mn[p], sc[p], B);
+              const unsigned long long inc = 1ull << ((j & 7) << 3);
+              if constexpr (NW8 == 1) {
+                cw[p][0] += inc;
+              } else {
+#pragma unroll
+                for (int w = 0; w < NW8; ++w) cw[p][w] += (j >> 3) == w ? inc : 0ull;
+              }
+            }
           } else {
             for (int k = 0; k < kn; ++k) {
-              const int j = hist_bin(col[k * PLANE], mn[p], sc[p], B);
-              const uint32_t inc = 1u << ((j & 1) << 4);
-              const int q = j >> 1;
-              cA[p] += q == 0 ? inc : 0u;
-              cB[p] += q == 1 ? inc : 0u;
-              cC[p] += q == 2 ? inc : 0u;
-              cD[p] += q == 3 ? inc : 0u;
+              const int j = hist_bin_nonneg(col[k * PLANE], mn[p], sc[p], B);
+              const unsigned long long inc = 1ull << ((j & 3) << 4);
+#pragma unroll
+              for (int w = 0; w < NW16; ++w) cw[p][w] += (j >> 2) == w ? inc : 0ull;
             }
           }
         }
@@ -660,11 +663,11 @@ __device__ __forceinline__ bool stage_members_tma(const Field &f, float *sm, flo
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
       if (!in[p]) continue;
-      hist_row_table_counts<HALO, RS>(
+      hist_row_table_counts<HALO, RS, RB>(
           sm, R4, lv[p], B, nf[p], mn[p], mx[p], [&](int k) -> float {
-            if (!wide) return mtab[(unsigned)(c8[p] >> (k << 3)) & 255u];
-            const uint32_t w = k < 2 ? cA[p] : (k < 4 ? cB[p] : (k < 6 ? cC[p] : cD[p]));
-            return __fdiv_rn((float)((w >> ((k & 1) << 4)) & 0xFFFFu), (float)N);
+            if (!wide) return mtab[(unsigned)(cw[p][k >> 3] >> ((k & 7) << 3)) & 255u];
+            return __fdiv_rn((float)((unsigned)(cw[p][k >> 2] >> ((k & 3) << 4)) & 0xFFFFu),
+                             (float)N);
           });
     }
     return true;
@@ -786,12 +789,13 @@ __device__ __forceinline__ void integrate_tile(const Field &f, int ty0, int tx0,
 // of the tile.  SADDLE selects the saddle probability (Eq. saddleProb)
 // instead of the minimum / maximum: a separate instance, so neither pays for
 // the other.  TMA: the members are staged through the tensor map tmap into
-// `box`, with the mbarrier `bar` (FROM_MEMBERS only).  ROWS (histograms):
-// the walk runs over per-bin rows in R4 (hist_r4_rows x halo float4, 16-byte
-// aligned; it may overlap `box`) instead of the segment walker's tail table;
-// each kernel instance carries one of the two walks.
+// `box`, with the mbarrier `bar` (FROM_MEMBERS only).  RB > 0 (histograms
+// of at most RB bins): the walk runs over per-bin rows in R4 (hist_r4_rows
+// rows of hist_r4_stride float4, 16-byte aligned; it may overlap `box`)
+// instead of the segment walker's tail table; each kernel instance carries
+// one of the two walks.
 template <int MODEL, bool FROM_MEMBERS, int TYv, bool SADDLE = false, bool TMA = false,
-          bool ROWS = false>
+          int RB = 0>
 __device__ __forceinline__ void process_tile(const Field &f, int ty0, int tx0, float *sm,
                                              const CUtensorMap *tmap = nullptr,
                                              float *box = nullptr, uint64_t *bar = nullptr,
@@ -802,7 +806,7 @@ __device__ __forceinline__ void process_tile(const Field &f, int ty0, int tx0, f
 
   bool staged = true;
   if constexpr (FROM_MEMBERS && TMA) {
-    staged = stage_members_tma<MODEL, TY, ROWS>(f, sm, box, bar, tmap, ty0, tx0, R4);
+    staged = stage_members_tma<MODEL, TY, RB>(f, sm, box, bar, tmap, ty0, tx0, R4);
   } else if (FROM_MEMBERS) {
     // work items per halo row: the two halo columns (scalar) and eight
     // groups of four interior columns (one float4 per member when aligned)
@@ -837,7 +841,7 @@ __device__ __forceinline__ void process_tile(const Field &f, int ty0, int tx0, f
     mark_tile_timeout<TY, SADDLE>(f, ty0, tx0);
     return;
   }
-  integrate_tile<MODEL, TY, SADDLE, FROM_MEMBERS && TMA, ROWS>(f, ty0, tx0, sm, R4);
+  integrate_tile<MODEL, TY, SADDLE, FROM_MEMBERS && TMA, (RB > 0)>(f, ty0, tx0, sm, R4);
 }
 
 // Phase 2 of a tile whose parameters (and, if TABLES_BUILT, histogram tail
