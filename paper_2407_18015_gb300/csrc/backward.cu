@@ -891,6 +891,327 @@ __global__ void __launch_bounds__(NTHREADS, 2)
   }
 }
 
+// ---------------------------------------------------------------------------
+// histogram adjoint over per-bin rows (at most RB bins, non-degenerate
+// centres): the forward's row tables and walkers (device.cuh), built here
+// from the parameters, mirrored for the maximum as above.  Per piece all
+// factors are linear; the own product (degree 4), each leave-one-out product
+// LOO_n (degree 3) and LOO_n times the in-bin weight (e_{k+1} - x) / h_n
+// (degree 4) are integrated exactly by the 3-point Gauss-Legendre rule at
+// shared nodes, the leave-one-out products from pair products.  Every lane
+// runs the same steps; row reads at crossings are predicated, partials are
+// stored when a neighbour leaves a bin (or the centre leaves one of its own).
+
+// Per-bin rows, lo, hi, total and status of one staged vertex straight from
+// its parameters (mirrored: -X, bins reversed), the masses held in
+// registers; the same rows and status as hist_row_table builds from a
+// parameter tile.
+template <int HALO, int RS, int RB>
+__device__ __forceinline__ void hist_rows_from_params(const Field &f, float *sm, float4 *R, int l,
+                                                      long long gi, int B, bool mirrored) {
+  const long long plane = f.plane;
+  const float a0 = f.params[gi], b0 = f.params[plane + gi];
+  const float a = mirrored ? -b0 : a0, b = mirrored ? -a0 : b0;
+  uint8_t st = (!isfinite(a) || !isfinite(b)) ? V_NONFINITE
+                                             : (a > b ? V_BAD : (a == b ? V_DEGENERATE : 0));
+  float m[RB];
+  float t = 0.f;
+#pragma unroll
+  for (int q = 0; q < RB; ++q) {
+    m[q] = 0.f;
+    if (q < B) {
+      m[q] = __ldg(f.params + (long long)(2 + (mirrored ? B - 1 - q : q)) * plane + gi);
+      if (!isfinite(m[q])) st |= V_NONFINITE;
+      else if (m[q] < 0.f) st |= V_BAD;
+      t += m[q];
+    }
+  }
+  R += l;
+  const float4 beyond = make_float4(0.f, t, 0.f, kFar);
+  if (a == b) {
+#pragma unroll
+    for (int k = 0; k <= RB; ++k)
+      if (k <= B) R[k * RS] = beyond;
+  } else {
+    // as hist_rows_build
+    const float w = b - a;
+    const float h = (B & (B - 1)) == 0 ? w * (1.f / (float)B) : w / (float)B, ih = frcp(h);
+    float c = 0.f, sk = t;
+#pragma unroll
+    for (int k = 0; k < RB; ++k) {
+      if (k < B) {
+        c += m[k];
+        const float sn = k + 1 < B ? t - c : 0.f;
+        R[k * RS] = make_float4(sk, t - sk, (sk - sn) * ih, k + 1 < B ? (float)(k + 1) * h : w);
+        sk = sn;
+      }
+    }
+    R[B * RS] = beyond;
+  }
+  sm[l] = a;
+  sm[HALO + l] = b;
+  sm[2 * HALO + l] = t;
+  sm[3 * HALO + l] = (float)st;
+}
+
+// the bin width of the rows of a support of width w (as hist_rows_build)
+__device__ __forceinline__ float rows_bin_width(float w, int B) {
+  return (B & (B - 1)) == 0 ? w * (1.f / (float)B) : w / (float)B;
+}
+
+// a 4-byte global store that happens only where p holds (one predicated
+// instruction, no branch); the address is not touched where p is false
+__device__ __forceinline__ void stg_if(bool p, float *ptr, float v) {
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.b32 q, %2, 0;\n @q st.global.f32 [%0], %1;\n}" ::"l"(ptr),
+      "f"(v), "r"((int)p)
+      : "memory");
+}
+
+// One neighbour's crossing in the adjoint walk, without a branch: if its
+// next edge nx is at or below x1 -- store `val` (its partial of the bin it
+// leaves) at optr if it was inside a bin (ihe != 0), move optr to the next
+// bin's partial, restart Cs = C and inb = 0, read the next row into r (and
+// advance addr), and set ihe to 1/h inside a bin (ih) or 0 beyond the
+// support (the beyond row's next edge is kFar).
+template <unsigned stride>
+__device__ __forceinline__ void adj_cross(float nx, float x1, float val, float *&optr,
+                                          long long qs, float C, float &Cs, float &inb,
+                                          uint32_t &addr, float4 &r, float ih, float &ihe) {
+  asm volatile(
+      "{\n .reg .pred q, e, n;\n"
+      " setp.le.f32 q, %9, %10;\n"
+      " setp.ne.and.f32 e, %8, 0f00000000, q;\n"
+      " @e st.global.f32 [%4], %11;\n"
+      " @q add.s64 %4, %4, %12;\n"
+      " @q mov.f32 %6, %13;\n"
+      " @q mov.f32 %7, 0f00000000;\n"
+      " @q ld.shared.v4.f32 {%0, %1, %2, %3}, [%5];\n"
+      " @q add.u32 %5, %5, %14;\n"
+      " setp.lt.and.f32 n, %3, 0f7E61B1E6, q;\n"
+      " @q selp.f32 %8, %15, 0f00000000, n;\n}"
+      : "+f"(r.x), "+f"(r.y), "+f"(r.z), "+f"(r.w), "+l"(optr), "+r"(addr), "+f"(Cs),
+        "+f"(inb), "+f"(ihe)
+      : "f"(nx), "f"(x1), "f"(val), "l"(qs * (long long)sizeof(float)), "f"(C), "n"(stride),
+        "f"(ih)
+      : "memory");
+}
+
+template <int HALO, int RS>
+__device__ __forceinline__ void hist_adj_walk(const float *sm, const float4 *R4, int l,
+                                              const int *nl, const bool *present, int B,
+                                              bool mirrored, float wv, float *rows,
+                                              long long plane, long long gi) {
+  const float lo1 = sm[l], hi1 = sm[HALO + l];
+  const float W1 = hi1 - lo1;
+  // partial of slot s (0 centre, 1 + i neighbour i) and bin q (mirrored:
+  // the bins are reversed) at out0 + s * B * plane + q * qstride
+  const long long qstride = mirrored ? -plane : plane;
+  float *const out0 = rows + gi + (mirrored ? (long long)(B - 1) * plane : 0);
+  auto out = [&](int slot, int q) -> float * {
+    return out0 + (long long)slot * B * plane + (long long)q * qstride;
+  };
+  if (!(W1 <= 1e38f)) {  // a support too wide for the walk's frame: no partials
+    for (int s = 0; s < 5; ++s)
+      if (s == 0 || present[s - 1])
+        for (int q = 0; q < B; ++q) *out(s, q) = __int_as_float(0x7fc00000);
+    return;
+  }
+  HistRowWalker nw[4];
+  // per neighbour: C = int_0^x pdf_1 LOO, Cs = C at the start of its current
+  // bin, inb = the in-bin integral of that bin, ihe = 1/h inside a bin (0
+  // before or beyond its support, and for a point mass), kb = its bin (-1
+  // before the support, B beyond; a point mass moves from -1 to 0 at its
+  // position and stays there)
+  float2 C01 = {0.f, 0.f}, C23 = {0.f, 0.f}, inb01 = {0.f, 0.f}, inb23 = {0.f, 0.f};
+  float Cs[4] = {0.f, 0.f, 0.f, 0.f}, ih[4], ihe[4];
+  int kb[4];
+  bool pm[4];
+  float *optr[4];  // the partial of neighbour i's current bin (used inside a bin only)
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    pm[i] = false;
+    ih[i] = ihe[i] = 0.f;
+    optr[i] = rows;
+    if (!present[i]) {
+      nw[i].init_absent();
+      kb[i] = B;
+      continue;
+    }
+    const float lo = sm[nl[i]], hi = sm[HALO + nl[i]];
+    pm[i] = lo == hi;
+    const float h = pm[i] ? 0.f : rows_bin_width(hi - lo, B);
+    ih[i] = pm[i] ? 0.f : frcp(h);
+    nw[i].init(R4 + nl[i], lo - lo1, sm[2 * HALO + nl[i]]);
+    const int j = nw[i].seek0<RS>(R4 + nl[i], B, h);
+    kb[i] = j - 1;
+    ihe[i] = (kb[i] >= 0 && kb[i] < B) ? ih[i] : 0.f;
+    optr[i] = out(1 + i, 0) + (long long)kb[i] * qstride;
+    // bins entirely below the centre's support: their survival is 0 there
+    if (!pm[i])
+      for (int q = 0; q < j - 1; ++q) *out(1 + i, q) = 0.f;
+  }
+  const float ih1 = frcp(rows_bin_width(W1, B));
+  uint32_t addr_c = static_cast<uint32_t>(__cvta_generic_to_shared(R4 + l + RS)) + 8u;
+  float2 dc;  // (density, next edge) of the centre's current bin
+  {
+    const float4 t = R4[l];
+    dc = make_float2(t.z, t.w);
+  }
+  int jc = 0;
+  float own = 0.f;
+  const float wvh = wv * ih1;
+  float x0 = 0.f;
+  const int max_steps = 5 * (B + 1) + 4;
+#pragma unroll 1
+  for (int step = 0; step < max_steps && x0 < W1; ++step) {
+    float e[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) e[i] = nw[i].nx();
+    const float x1 = fminf(fminf(fminf(e[0], e[1]), fminf(e[2], e[3])), dc.y);
+    const float d = x1 - x0, a = d * dc.x;
+    // the four factors in the pairs (0, 2) and (1, 3): values at x0 (g0),
+    // their change over the piece (dg); in-bin weights (e - x) / h at x0
+    // (w0) and their change (dw)
+    const float2 gA = make_float2(nw[0].r.x, nw[2].r.x), gB = make_float2(nw[1].r.x, nw[3].r.x);
+    const float2 sA = make_float2(-nw[0].r.z, -nw[2].r.z), sB = make_float2(-nw[1].r.z, -nw[3].r.z);
+    const float2 dd = make_float2(d, d);
+    const float2 dgA = __fmul2_rn(sA, dd), dgB = __fmul2_rn(sB, dd);
+    const float2 ihA = make_float2(ihe[0], ihe[2]), ihB = make_float2(ihe[1], ihe[3]);
+    const float2 w0A = __fmul2_rn(__fadd2_rn(make_float2(e[0], e[2]), make_float2(-x0, -x0)), ihA);
+    const float2 w0B = __fmul2_rn(__fadd2_rn(make_float2(e[1], e[3]), make_float2(-x0, -x0)), ihB);
+    const float2 dwA = __fmul2_rn(ihA, make_float2(-d, -d)), dwB = __fmul2_rn(ihB, make_float2(-d, -d));
+    // 3-point Gauss-Legendre on [0, 1]: nodes 1/2 -+ sqrt(3/5)/2, weights 5/18, 8/18
+    float so = 0.f;
+    float2 scA = {0.f, 0.f}, scB = {0.f, 0.f}, siA = {0.f, 0.f}, siB = {0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float tq = q == 0 ? 0.11270166537925831f : (q == 1 ? 0.5f : 0.88729833462074169f);
+      const float wq = q == 1 ? 8.f / 18.f : 5.f / 18.f;
+      const float2 tt = make_float2(tq, tq), ww = make_float2(wq, wq);
+      const float2 fA = __ffma2_rn(dgA, tt, gA), fB = __ffma2_rn(dgB, tt, gB);  // (f0,f2),(f1,f3)
+      const float2 P = __fmul2_rn(fA, fB);                                       // (p01, p23)
+      const float2 Ps = make_float2(P.y, P.x);                                   // (p23, p01)
+      // leave-one-out products: (L0, L2) = (f1 p23, f3 p01), (L1, L3) = (f0 p23, f2 p01)
+      const float2 wLA = __fmul2_rn(ww, __fmul2_rn(fB, Ps));
+      const float2 wLB = __fmul2_rn(ww, __fmul2_rn(fA, Ps));
+      so = fmaf(wq, P.x * P.y, so);
+      scA = __fadd2_rn(scA, wLA);
+      scB = __fadd2_rn(scB, wLB);
+      siA = __ffma2_rn(__ffma2_rn(dwA, tt, w0A), wLA, siA);
+      siB = __ffma2_rn(__ffma2_rn(dwB, tt, w0B), wLB, siB);
+    }
+    own = fmaf(d, so, own);
+    const float2 aa = make_float2(a, a);
+    // back to the neighbour order (0, 1) and (2, 3)
+    C01 = __ffma2_rn(aa, make_float2(scA.x, scB.x), C01);
+    C23 = __ffma2_rn(aa, make_float2(scA.y, scB.y), C23);
+    inb01 = __ffma2_rn(aa, make_float2(siA.x, siB.x), inb01);
+    inb23 = __ffma2_rn(aa, make_float2(siA.y, siB.y), inb23);
+    float C[4] = {C01.x, C01.y, C23.x, C23.y}, inb[4] = {inb01.x, inb01.y, inb23.x, inb23.y};
+    // crossings: a neighbour leaving bin k stores its partial C(e_k) + in-bin
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      nw[i].r.x = fmaf(-nw[i].r.z, d, nw[i].r.x);
+      adj_cross<(unsigned)(RS * 16)>(e[i], x1, wv * (Cs[i] + inb[i]), optr[i], qstride, C[i],
+                                     Cs[i], inb[i], nw[i].addr, nw[i].r, ih[i], ihe[i]);
+    }
+    inb01 = make_float2(inb[0], inb[1]);
+    inb23 = make_float2(inb[2], inb[3]);
+    {
+      const bool cr = dc.y <= x1;
+      stg_if(cr && jc < B, out(0, jc), wvh * own);
+      own = cr ? 0.f : own;
+      jc += cr ? 1 : 0;
+      lds64_cross<(unsigned)(RS * 16)>(dc.y, x1, addr_c, dc);
+    }
+    x0 = x1;
+  }
+  if (jc < B) *out(0, jc) = wvh * own;
+  for (int q = jc + 1; q < B; ++q) *out(0, q) = 0.f;
+  const float C[4] = {C01.x, C01.y, C23.x, C23.y}, inb[4] = {inb01.x, inb01.y, inb23.x, inb23.y};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if (!present[i]) continue;
+    kb[i] = (int)((optr[i] - out(1 + i, 0)) / qstride);  // the bin the walker ended in
+    if (kb[i] >= 0 && kb[i] < B) *out(1 + i, kb[i]) = wv * (Cs[i] + inb[i]);
+    // bins entirely above the walk: their survival is 1 on the whole support
+    // (a point mass: every mass partial is the integral below its position,
+    // Cs once it has been reached, else the whole integral)
+    const float above = pm[i] && kb[i] >= 0 ? Cs[i] : C[i];
+    for (int q = (kb[i] < 0 ? 0 : kb[i] + 1); q < B; ++q) *out(1 + i, q) = wv * above;
+  }
+}
+
+template <int RB>
+__global__ void __launch_bounds__(NTHREADS, 2)
+    hist_adj_tile(Field f, int tiles_x, int want_max, const float *__restrict__ weight,
+                  float *__restrict__ rows) {
+  extern __shared__ __align__(16) float smem[];
+  constexpr int TY = 8, TX = 32, HY = TY + 2, HX = TX + 2, HALO = HY * HX;
+  constexpr int RS = hist_r4_stride(HALO);
+  const int B = f.B;
+  const long long plane = f.plane;
+  float4 *R4 = reinterpret_cast<float4 *>(smem);
+  float *sm = smem + 4 * hist_r4_rows(B) * RS;  // lo, hi, T, status
+  const int ty0 = f.y0 + ((int)blockIdx.x / tiles_x) * TY, tx0 = ((int)blockIdx.x % tiles_x) * TX;
+  const int ylim = min(f.H, f.y1 + 1);
+  const bool mirrored = want_max != 0;
+  for (int l = threadIdx.x; l < HALO; l += NTHREADS) {
+    const int r = l / HX, c = l - r * HX;
+    const int gy = ty0 + r - 1, gx = tx0 + c - 1;
+    if (gy < 0 || gy >= ylim || gx < 0 || gx >= f.W) continue;
+    hist_rows_from_params<HALO, RS, RB>(f, sm, R4, l, (long long)gy * f.W + gx, B, mirrored);
+  }
+  __syncthreads();
+  for (int v = threadIdx.x; v < TY * TX; v += NTHREADS) {
+    const int r = v / TX + 1, c = v % TX + 1;
+    const int gy = ty0 + r - 1, gx = tx0 + c - 1;
+    if (gy >= f.y1 || gx >= f.W) continue;
+    const int l = r * HX + c;
+    const long long gi = (long long)gy * f.W + gx;
+    bool present[4];
+    int nl[4];
+    long long ni[4];
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int yy = gy + kDy[i], xx = gx + kDx[i];
+      present[i] = (yy >= 0 && yy < f.H && xx >= 0 && xx < f.W);
+      nl[i] = l + kDy[i] * HX + kDx[i];
+      ni[i] = present[i] ? (long long)yy * f.W + xx : gi;
+      k += present[i];
+    }
+    int st = (int)sm[3 * HALO + l];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (present[i]) st |= (int)sm[3 * HALO + nl[i]] & (V_NONFINITE | V_BAD);
+    const float wv = weight[gi];
+    if ((st & (V_NONFINITE | V_BAD)) || (f.boundary == 1 && k < 4)) {
+      const float fill = (st & (V_NONFINITE | V_BAD)) ? qnan() : 0.f;
+      for (int s = 0; s < 5; ++s)
+        for (int q = 0; q < B; ++q) rows[((long long)s * B + q) * plane + gi] = fill;
+      continue;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (!present[i])
+        for (int q = 0; q < B; ++q) rows[((long long)(1 + i) * B + q) * plane + gi] = 0.f;
+    if (sm[l] == sm[HALO + l]) {
+      // a point-mass centre: the product of tails (global-memory path)
+      hist_grad_vertex(f.params, plane, gi, ni, present, B, mirrored, wv, rows);
+    } else {
+      hist_adj_walk<HALO, RS>(sm, R4, l, nl, present, B, mirrored, wv, rows, plane, gi);
+    }
+  }
+}
+
+// shared-memory bytes of hist_adj_tile at B bins
+static size_t hist_adj_smem(int B) {
+  constexpr int HALO = 10 * 34;
+  return ((size_t)4 * hist_r4_rows(B) * hist_r4_stride(HALO) + 4 * HALO) * sizeof(float);
+}
+
 // pass 2: grad[q][u] = own row + the rows u's neighbours wrote about u
 __global__ void __launch_bounds__(256) gather_kernel(Field f, int Q, const float *__restrict__ rows,
                                                      float *__restrict__ grad) {
@@ -925,6 +1246,40 @@ cudaError_t launch_backward(const Field &f, int model, int cptype, const float *
     case kUniform: partials_kernel<kUniform><<<(int)b, 128, 0, s>>>(f, want_max, weight, rows); break;
     case kEpan: partials_kernel<kEpan><<<(int)b, 128, 0, s>>>(f, want_max, weight, rows); break;
     case kHist: {
+      if (f.B <= 16) {
+        // per-bin rows: 8-row tiles, two CTAs per SM
+        static std::atomic<bool> attr_rows[2][128] = {};
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+        const int which = f.B <= 8 ? 0 : 1;
+        if (!attr_rows[which][dev].load(std::memory_order_acquire)) {
+          e = which == 0 ? cudaFuncSetAttribute(hist_adj_tile<8>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)hist_adj_smem(8))
+                         : cudaFuncSetAttribute(hist_adj_tile<16>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)hist_adj_smem(16));
+          if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e;
+          }
+          attr_rows[which][dev].store(true, std::memory_order_release);
+        }
+        const int tiles_x = (f.W + TX - 1) / TX, tiles_y = (f.y1 - f.y0 + 7) / 8;
+        const long long tiles = (long long)tiles_x * tiles_y;
+        if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+        if (tiles > 0) {
+          if (which == 0)
+            hist_adj_tile<8><<<(int)tiles, NTHREADS, hist_adj_smem(f.B), s>>>(f, tiles_x, want_max,
+                                                                              weight, rows);
+          else
+            hist_adj_tile<16><<<(int)tiles, NTHREADS, hist_adj_smem(f.B), s>>>(f, tiles_x,
+                                                                               want_max, weight, rows);
+        }
+        break;
+      }
       constexpr int TYg = kGradTY;
       // per device: the attribute is set once (host threads may race to set
       // it; setting it twice is harmless, the flag itself is atomic)

@@ -1372,10 +1372,11 @@ struct HistRowWalker {
   // From the initial state, cross every edge at or below 0 at once (the
   // state step() would reach edge by edge; the count of such edges comes
   // from -lam / h and is checked against the edges of the rows), and set G
-  // and F to their values at 0.
+  // and F to their values at 0.  Returns the number of edges crossed (a
+  // point mass: 1), 0 if the first edge is above 0.
   template <int RS>
-  __device__ __forceinline__ void seek0(const float4 *row0, int B, float h) {
-    if (nx() > 0.f) return;  // the first edge is above 0 (also: absent)
+  __device__ __forceinline__ int seek0(const float4 *row0, int B, float h) {
+    if (nx() > 0.f) return 0;  // the first edge is above 0 (also: absent)
     int j = 1;               // edges e_0 .. e_{j-1} are at or below 0
     float el;
     if (h > 0.f) {
@@ -1393,6 +1394,7 @@ struct HistRowWalker {
     r.x = fmaf(r.z, el, r.x);
     r.y = fmaf(-r.z, el, r.y);
     addr = static_cast<uint32_t>(__cvta_generic_to_shared(row0 + j * RS));
+    return j;
   }
 };
 
