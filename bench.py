@@ -180,10 +180,13 @@ MVN_OPS_PER_SAMPLE = 250
 # integral and one leave-one-out product integral per neighbour, each counted
 # as a forward piece integral.
 ADJ_HIST_FLOPS_PER_PIECE = 5 * HIST_FLOPS_PER_PIECE_TYPE
-# Epanechnikov adjoint of P_min: per vertex the derivative integrals with
-# respect to (m, w) of the centre and of each of the four neighbours, ten
-# integrals, each counted as one forward vertex integral of one type.
-ADJ_EPAN_FLOPS_PER_VERTEX = 10 * EPAN_FLOPS_PER_VERTEX_TYPE
+# Epanechnikov adjoint of P_min: at every Gauss-Legendre node of every piece
+# the forward's factors and product, plus the derivative factor of each of
+# the four neighbours (its density, times (x - m)/w for the width), the two
+# derivatives of the centre's density and the ten derivative accumulations:
+# about twice the forward's work per node, counted as two forward vertex
+# integrals of one type.
+ADJ_EPAN_FLOPS_PER_VERTEX = 2 * EPAN_FLOPS_PER_VERTEX_TYPE
 
 
 # DRAM bytes (read + write) per launch of each headline kernel from the ncu
@@ -620,7 +623,7 @@ def other_rows(torch, ucp, ctx, dev, args, flush, peaks):
                 row["adjoint_roofline"] = {
                     "bound": "alu", "achieved": ach, "peak": fp32, "unit": "TFLOP/s",
                     "frac": ach / fp32, "work": f"{ADJ_EPAN_FLOPS_PER_VERTEX} flops per vertex "
-                    "(ten derivative integrals)", "peak_source": fp32_src}
+                    "(two forward vertex integrals)", "peak_source": fp32_src}
                 row["oracle"] = oracle_fwd_bwd_rate(e4, Wt, m, b)
             else:
                 # adjoint: params (2 planes) and W read, 2 gradient planes written

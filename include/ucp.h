@@ -309,16 +309,21 @@ int ucp_backward(ucp_ctx *ctx, const float *params, int H, int W, const ucp_mode
  * running -- an application whose own allocator already owns the device
  * memory budget, or a latency-critical path on which cudaMalloc / cudaFree,
  * which may synchronise the whole device, are not acceptable.  This entry
- * point takes no context and allocates nothing: its partial-row scratch is a
- * fixed file-scope device array of ucp_backward_static_capacity() floats
- * (16 MiB), held by every device that loads the library until exit.  Inputs
- * and outputs are as for ucp_backward, on the CURRENT device.  5 * Q * H * W
- * must not exceed the capacity (Q = 2, or bins for histograms), else
- * UCP_ERR_SHAPE and nothing runs.  The first call on a device looks up the
- * array's device address (once, with that device current); make that first
- * call before any stream capture.  All calls on a device share the array:
- * calls that can overlap on the GPU (unordered streams) race on it.  It keeps
- * the last call's contents; no part of it needs to start at zero.  The
+ * point takes no context and allocates nothing: its scratch is a fixed
+ * file-scope device array of ucp_backward_static_capacity() floats (16 MiB),
+ * held by every device that loads the library until exit.  Inputs and
+ * outputs are as for ucp_backward, on the CURRENT device.  The scratch must
+ * fit the array, else UCP_ERR_SHAPE and nothing runs: 5 * 2 * H * W floats
+ * for uniform and Epanechnikov (and 5 * bins * H * W for histograms of more
+ * than 16 bins); for histograms of at most 16 bins 80 * bins floats per tile
+ * of 8 x 32 vertices plus one block of 1280 * bins floats (more blocks, up to
+ * four per SM, when they fit; fewer make the call slower, not wrong) plus
+ * 64 floats of block flags.  The first call on a device looks up the
+ * array's device address and the device's SM count (once, with that device
+ * current); make that first call before any stream capture.  All calls on a
+ * device share the array: calls that can overlap on the GPU (unordered
+ * streams) race on it.  It keeps the last call's contents; the block flags,
+ * which must start at zero, are cleared on the stream by every call.  The
  * looked-up address is kept for the life of the process: do not call this
  * entry point on a device after cudaDeviceReset (or any other reset of its
  * primary context) in the same process, since the array then lives at a new

@@ -453,9 +453,6 @@ int ucp_backward(ucp_ctx *ctx, const float *params, int H, int W, const ucp_mode
   if (rc) return rc;
   DeviceGuard g(ctx->device);
   if (g.err != cudaSuccess) return ucp_set_error(ctx, g.err);
-  const int Q = desc->model == UCP_HISTOGRAM ? desc->bins : 2;
-  const size_t bytes = (size_t)5 * Q * H * W * sizeof(float);
-  if ((rc = ucp_ensure_work(ctx, bytes))) return rc;
   Field f{};
   f.params = params;
   f.plane = (long long)H * W;
@@ -463,8 +460,13 @@ int ucp_backward(ucp_ctx *ctx, const float *params, int H, int W, const ucp_mode
   f.y0 = 0; f.y1 = H;
   f.boundary = desc->boundary;
   f.cptypes = (unsigned)cptype;
+  // scratch blocks of the histogram adjoint: twice the CTAs that can be
+  // resident at once (two per SM)
+  const int ctas = 4 * ctx->sm_count;
+  const size_t floats = backward_scratch_floats(f, desc->model, ctas);
+  if ((rc = ucp_ensure_work(ctx, floats * sizeof(float)))) return rc;
   return ucp_set_error(ctx, launch_backward(f, desc->model, cptype, weight, (float *)ctx->work,
-                                            grad_params, (cudaStream_t)stream));
+                                            floats, ctas, grad_params, (cudaStream_t)stream));
 }
 
 }  // extern "C"

@@ -18,6 +18,7 @@
 //     Epanechnikov differentiates the density (it vanishes at the ends);
 //     histogram: dP/dw_j = (1/h) int_{bin j} prod G.
 // Maxima use the negated variables (P_max(theta) = P_min(-theta)).
+#include <algorithm>
 #include <atomic>
 
 #include "device.cuh"
@@ -386,10 +387,10 @@ struct NWalk {
   float C, Cstart, inbin;
 };
 
-__device__ __forceinline__ void nwalk_advance(NWalk &n, float *rows_n, long long plane,
-                                              long long vi, float wv) {
+__device__ __forceinline__ void nwalk_advance(NWalk &n, float *rows_n, long long ostride,
+                                              float wv) {
   // leaving bin j (if inside the support): its partial is C(e_j) + within-bin
-  if (n.j >= 0 && n.j < n.B) rows_n[(long long)n.v.orig(n.j) * plane + vi] = wv * (n.Cstart + n.inbin);
+  if (n.j >= 0 && n.j < n.B) rows_n[(long long)n.v.orig(n.j) * ostride] = wv * (n.Cstart + n.inbin);
   ++n.j;
   n.Cstart = n.C;
   n.inbin = 0.f;
@@ -411,9 +412,12 @@ __device__ __forceinline__ float nwalk_G(const NWalk &n, float x) {
   return fmaxf(fmaf(-n.slope, x - n.eleft, n.S), 0.f);
 }
 
-__device__ void hist_grad_vertex(const float *params, long long plane, long long vi,
+// Partials of one centre vi (the point-mass path and the general walk in
+// global memory): slot s (0 the centre, 1 + i neighbour i) and bin q go to
+// out[(s * B + q) * ostride].
+__device__ __noinline__ void hist_grad_vertex(const float *params, long long plane, long long vi,
                                  const long long *ni, const bool *present, int B, bool want_max,
-                                 float wv, float *rows) {
+                                 float wv, float *out, long long ostride) {
   const HistView cv{params + vi, plane, B, want_max};
   const float lo1 = cv.lo(), hi1 = cv.hi();
   float T[4];
@@ -427,7 +431,7 @@ __device__ void hist_grad_vertex(const float *params, long long plane, long long
     for (int q = 0; q < B; ++q) t += nw[i].v.mass(q);
     T[i] = t;
   }
-  float *own = rows;  // slot 0
+  float *own = out;  // slot 0
   if (lo1 == hi1) {
     // point-mass centre at c (total T1): P = T1 prod_n S_n(c)
     const float c = lo1;
@@ -458,11 +462,11 @@ __device__ void hist_grad_vertex(const float *params, long long plane, long long
     float lo4[4];
     loo4(S, lo4);
     const float Pn = lo4[0] * S[0];
-    for (int q = 0; q < B; ++q) own[(long long)cv.orig(q) * plane + vi] = wv * Pn;
+    for (int q = 0; q < B; ++q) own[(long long)cv.orig(q) * ostride] = wv * Pn;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       if (!present[i]) continue;
-      float *rn = rows + (long long)(1 + i) * B * plane;
+      float *rn = out + (long long)(1 + i) * B * ostride;
       const HistView &v = nw[i].v;
       const float lo = v.lo(), hi = v.hi();
       const float h = (hi - lo) / (float)B;
@@ -474,7 +478,7 @@ __device__ void hist_grad_vertex(const float *params, long long plane, long long
           const float e0 = lo + (float)q * h, e1 = (q + 1 < B) ? lo + (float)(q + 1) * h : hi;
           d = c < e0 ? 1.f : (c >= e1 ? 0.f : (e1 - c) / (e1 - e0));
         }
-        rn[(long long)v.orig(q) * plane + vi] = wv * T1 * d * lo4[i];
+        rn[(long long)v.orig(q) * ostride] = wv * T1 * d * lo4[i];
       }
     }
     return;
@@ -498,12 +502,12 @@ __device__ void hist_grad_vertex(const float *params, long long plane, long long
     n.enext = n.lam;
     n.C = n.Cstart = n.inbin = 0.f;
     n.T = T[i];
-    float *rn = rows + (long long)(1 + i) * B * plane;
+    float *rn = out + (long long)(1 + i) * B * ostride;
     if (n.B == 0) {
       // point mass: every mass partial is int_{x < c} pdf_1 prod_{m!=n} G; filled at the end
       continue;
     }
-    for (int g = 0; g <= B && n.enext <= 0.f && n.j < n.B; ++g) nwalk_advance(n, rn, plane, vi, wv);
+    for (int g = 0; g <= B && n.enext <= 0.f && n.j < n.B; ++g) nwalk_advance(n, rn, ostride, wv);
   }
   const float h1 = W1 / (float)B, ih1 = frcp(h1);
   int j1 = 0;
@@ -553,7 +557,7 @@ __device__ void hist_grad_vertex(const float *params, long long plane, long long
     }
     if (x1 >= W1) break;
     if (e1 <= x1) {
-      own[(long long)cv.orig(j1) * plane + vi] = wv * own_acc * ih1;
+      own[(long long)cv.orig(j1) * ostride] = wv * own_acc * ih1;
       own_acc = 0.f;
       ++j1;
       p1 = (j1 < B) ? cv.mass(j1) * ih1 : 0.f;
@@ -564,30 +568,30 @@ __device__ void hist_grad_vertex(const float *params, long long plane, long long
       if (present[i] && nw[i].enext <= x1) {
         NWalk &n = nw[i];
         if (n.B == 0) pmC[i] = n.C;  // crossing a point mass
-        nwalk_advance(n, rows + (long long)(1 + i) * B * plane, plane, vi, wv);
+        nwalk_advance(n, out + (long long)(1 + i) * B * ostride, ostride, wv);
         Gr[i] = nwalk_G(n, x1);
       }
       Gl[i] = Gr[i];
     }
     x0 = x1;
   }
-  if (j1 < B) own[(long long)cv.orig(j1) * plane + vi] = wv * own_acc * ih1;
-  for (int q = j1 + 1; q < B; ++q) own[(long long)cv.orig(q) * plane + vi] = 0.f;
+  if (j1 < B) own[(long long)cv.orig(j1) * ostride] = wv * own_acc * ih1;
+  for (int q = j1 + 1; q < B; ++q) own[(long long)cv.orig(q) * ostride] = 0.f;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     if (!present[i]) continue;
     NWalk &n = nw[i];
-    float *rn = rows + (long long)(1 + i) * B * plane;
+    float *rn = out + (long long)(1 + i) * B * ostride;
     if (n.B == 0) {
       // point mass at lam: partial = int_{x < lam} ...; never crossed -> whole integral
       const float v = (n.j < 0) ? (n.lam <= 0.f ? 0.f : n.C) : pmC[i];
-      for (int q = 0; q < B; ++q) rn[(long long)q * plane + vi] = wv * v;
+      for (int q = 0; q < B; ++q) rn[(long long)q * ostride] = wv * v;
       continue;
     }
-    if (n.j >= 0 && n.j < n.B) rn[(long long)n.v.orig(n.j) * plane + vi] = wv * (n.Cstart + n.inbin);
+    if (n.j >= 0 && n.j < n.B) rn[(long long)n.v.orig(n.j) * ostride] = wv * (n.Cstart + n.inbin);
     // bins entirely above the walk: the survival of the bin is 1 on [0, W1]
     for (int q = (n.j < 0 ? 0 : n.j + 1); q < n.B; ++q)
-      rn[(long long)n.v.orig(q) * plane + vi] = wv * n.C;
+      rn[(long long)n.v.orig(q) * ostride] = wv * n.C;
   }
 }
 
@@ -884,7 +888,7 @@ __global__ void __launch_bounds__(NTHREADS, 2)
         for (int q = 0; q < B; ++q) rows[((long long)(1 + i) * B + q) * plane + gi] = 0.f;
     if (sm[l] == sm[HALO + l]) {
       // a point-mass centre: the product of tails (global-memory path)
-      hist_grad_vertex(f.params, plane, gi, ni, present, B, want_max != 0, wv, rows);
+      hist_grad_vertex(f.params, plane, gi, ni, present, B, want_max != 0, wv, rows + gi, plane);
     } else {
       hist_grad_walk<HALO>(S0, l, nl, present, B, want_max != 0, wv, rows, plane, gi);
     }
@@ -1000,16 +1004,16 @@ __device__ __forceinline__ void adj_cross(float nx, float x1, float val, float *
 template <int HALO, int RS>
 __device__ __forceinline__ void hist_adj_walk(const float *sm, const float4 *R4, int l,
                                               const int *nl, const bool *present, int B,
-                                              bool mirrored, float wv, float *rows,
-                                              long long plane, long long gi) {
+                                              bool mirrored, float wv, float *outc,
+                                              long long ostride) {
   const float lo1 = sm[l], hi1 = sm[HALO + l];
   const float W1 = hi1 - lo1;
   // partial of slot s (0 centre, 1 + i neighbour i) and bin q (mirrored:
-  // the bins are reversed) at out0 + s * B * plane + q * qstride
-  const long long qstride = mirrored ? -plane : plane;
-  float *const out0 = rows + gi + (mirrored ? (long long)(B - 1) * plane : 0);
+  // the bins are reversed) at outc[(s * B + q) * ostride]
+  const long long qstride = mirrored ? -ostride : ostride;
+  float *const out0 = outc + (mirrored ? (long long)(B - 1) * ostride : 0);
   auto out = [&](int slot, int q) -> float * {
-    return out0 + (long long)slot * B * plane + (long long)q * qstride;
+    return out0 + (long long)slot * B * ostride + (long long)q * qstride;
   };
   if (!(W1 <= 1e38f)) {  // a support too wide for the walk's frame: no partials
     for (int s = 0; s < 5; ++s)
@@ -1032,7 +1036,7 @@ __device__ __forceinline__ void hist_adj_walk(const float *sm, const float4 *R4,
   for (int i = 0; i < 4; ++i) {
     pm[i] = false;
     ih[i] = ihe[i] = 0.f;
-    optr[i] = rows;
+    optr[i] = outc;
     if (!present[i]) {
       nw[i].init_absent();
       kb[i] = B;
@@ -1143,20 +1147,101 @@ __device__ __forceinline__ void hist_adj_walk(const float *sm, const float4 *R4,
   }
 }
 
+// Tiles of 8 x 32 centres, one per CTA.  Each CTA claims one of nslots
+// scratch blocks of partials [5][B][256] (slot, bin, centre of the tile) in
+// global memory for its lifetime (a flag per block, taken with an atomic
+// compare-and-swap and released at the end), so the blocks -- as many as the
+// CTAs that can be resident at once, with room to spare -- are rewritten
+// tile after tile and stay in L2.  After a tile's walks the same
+// CTA sums, for every vertex u of the tile, its own partials and those that
+// its neighbours inside the tile wrote about it -- in the fixed order own,
+// e, n, w, s -- into grad.  The partials about vertices outside the tile
+// (the n slot of the top row, s of the bottom row, w of the left column, e
+// of the right column) go to the tile's ring (N, S: B x 32; W, E: B x 8 each,
+// 80 B floats), which hist_adj_fixup adds to the edge vertices of the
+// neighbouring tiles afterwards.  Deterministic, no atomics.
+constexpr int kAdjTY = 8, kAdjTV = kAdjTY * 32, kAdjRing = 80;
+
+// The partials of one centre (gy, gx), staged at l, into out[(s * B + q) *
+// kAdjTV]: NaN or 0 for a centre whose probability is invalid or 0 by the
+// boundary rule, 0 for absent neighbours, else the walk (or the point-mass
+// path).
+template <int HALO, int RS>
+__device__ __forceinline__ void hist_adj_centre(const Field &f, const float *sm, const float4 *R4,
+                                             int gy, int gx, int l, bool mirrored,
+                                             const float *__restrict__ weight, float *out) {
+  constexpr int HX = 34;
+  const int B = f.B;
+  const long long plane = f.plane;
+  const long long gi = (long long)gy * f.W + gx;
+  bool present[4];
+  int nl[4];
+  long long ni[4];
+  int k = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int yy = gy + kDy[i], xx = gx + kDx[i];
+    present[i] = (yy >= 0 && yy < f.H && xx >= 0 && xx < f.W);
+    nl[i] = l + kDy[i] * HX + kDx[i];
+    ni[i] = present[i] ? (long long)yy * f.W + xx : gi;
+    k += present[i];
+  }
+  int st = (int)sm[3 * HALO + l];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (present[i]) st |= (int)sm[3 * HALO + nl[i]] & (V_NONFINITE | V_BAD);
+  const float wv = weight[gi];
+  if ((st & (V_NONFINITE | V_BAD)) || (f.boundary == 1 && k < 4)) {
+    const float fill = (st & (V_NONFINITE | V_BAD)) ? qnan() : 0.f;
+    for (int q = 0; q < 5 * B; ++q) out[q * kAdjTV] = fill;
+    return;
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (!present[i])
+      for (int q = 0; q < B; ++q) out[((1 + i) * B + q) * kAdjTV] = 0.f;
+  if (sm[l] == sm[HALO + l]) {
+    // a point-mass centre: the product of tails (global-memory path)
+    hist_grad_vertex(f.params, plane, gi, ni, present, B, mirrored, wv, out, kAdjTV);
+  } else {
+    hist_adj_walk<HALO, RS>(sm, R4, l, nl, present, B, mirrored, wv, out, kAdjTV);
+  }
+}
+
 template <int RB>
 __global__ void __launch_bounds__(NTHREADS, 2)
     hist_adj_tile(Field f, int tiles_x, int want_max, const float *__restrict__ weight,
-                  float *__restrict__ rows) {
+                  int *__restrict__ flags, int nslots, float *__restrict__ scratch,
+                  float *__restrict__ ring, float *__restrict__ grad) {
   extern __shared__ __align__(16) float smem[];
-  constexpr int TY = 8, TX = 32, HY = TY + 2, HX = TX + 2, HALO = HY * HX;
+  constexpr int TY = kAdjTY, TX = 32, HY = TY + 2, HX = TX + 2, HALO = HY * HX, TV = kAdjTV;
   constexpr int RS = hist_r4_stride(HALO);
+  static_assert(TV == NTHREADS, "one centre and one gathered vertex per thread");
   const int B = f.B;
   const long long plane = f.plane;
   float4 *R4 = reinterpret_cast<float4 *>(smem);
   float *sm = smem + 4 * hist_r4_rows(B) * RS;  // lo, hi, T, status
-  const int ty0 = f.y0 + ((int)blockIdx.x / tiles_x) * TY, tx0 = ((int)blockIdx.x % tiles_x) * TX;
-  const int ylim = min(f.H, f.y1 + 1);
   const bool mirrored = want_max != 0;
+  const int tile = blockIdx.x;
+  const int ty0 = f.y0 + (tile / tiles_x) * TY, tx0 = (tile % tiles_x) * TX;
+  const int ylim = min(f.H, f.y1 + 1);
+  // claim a scratch block: try the ones after 2 x (this SM's index) first;
+  // the polls are bounded (a block is released when its CTA ends)
+  __shared__ int slot_sm;
+  if (threadIdx.x == 0) {
+    unsigned smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    int got = -1;
+    for (int it = 0; it < (1 << 22) && got < 0; ++it) {
+      for (int k = 0; k < nslots && got < 0; ++k) {
+        const int sl = (int)((2u * smid + (unsigned)k) % (unsigned)nslots);
+        if (atomicCAS(flags + sl, 0, 1) == 0) got = sl;
+      }
+      if (got < 0) __nanosleep(1000);
+    }
+    __threadfence();
+    slot_sm = got;
+  }
   for (int l = threadIdx.x; l < HALO; l += NTHREADS) {
     const int r = l / HX, c = l - r * HX;
     const int gy = ty0 + r - 1, gx = tx0 + c - 1;
@@ -1164,44 +1249,106 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     hist_rows_from_params<HALO, RS, RB>(f, sm, R4, l, (long long)gy * f.W + gx, B, mirrored);
   }
   __syncthreads();
-  for (int v = threadIdx.x; v < TY * TX; v += NTHREADS) {
-    const int r = v / TX + 1, c = v % TX + 1;
-    const int gy = ty0 + r - 1, gx = tx0 + c - 1;
-    if (gy >= f.y1 || gx >= f.W) continue;
-    const int l = r * HX + c;
+  const int slot = slot_sm;
+  const int v = threadIdx.x;
+  const int r = v / TX + 1, c = v % TX + 1;
+  const int gy = ty0 + r - 1, gx = tx0 + c - 1;
+  const bool live = gy < f.y1 && gx < f.W;
+  if (slot < 0) {  // no scratch block within the bound: NaN gradient
+    if (live)
+      for (int q = 0; q < B; ++q) grad[(long long)q * plane + (long long)gy * f.W + gx] = qnan();
+    return;
+  }
+  float *const sc = scratch + (long long)slot * 5 * B * TV;
+  // walks: one centre per thread, partials into the scratch block
+  if (live) hist_adj_centre<HALO, RS>(f, sm, R4, gy, gx, r * HX + c, mirrored, weight, sc + v);
+  __syncthreads();
+  // gather: vertex u = v of the tile
+  if (live) {
     const long long gi = (long long)gy * f.W + gx;
-    bool present[4];
-    int nl[4];
-    long long ni[4];
-    int k = 0;
+    const int lr = r - 1, lc = c - 1;  // local row and column
+    bool in_tile[4];
+    int vn[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int yy = gy + kDy[i], xx = gx + kDx[i];
-      present[i] = (yy >= 0 && yy < f.H && xx >= 0 && xx < f.W);
-      nl[i] = l + kDy[i] * HX + kDx[i];
-      ni[i] = present[i] ? (long long)yy * f.W + xx : gi;
-      k += present[i];
+    for (int d = 0; d < 4; ++d) {
+      const int yy = gy + kDy[d], xx = gx + kDx[d];
+      const int rr = lr + kDy[d], cc = lc + kDx[d];
+      in_tile[d] = yy >= 0 && yy < f.y1 && xx >= 0 && xx < f.W && rr >= 0 && rr < TY &&
+                   cc >= 0 && cc < TX;
+      vn[d] = rr * TX + cc;
     }
-    int st = (int)sm[3 * HALO + l];
+    float *ring_t = ring + (long long)tile * kAdjRing * B;
+    for (int q = 0; q < B; ++q) {
+      float acc = sc[q * TV + v];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-      if (present[i]) st |= (int)sm[3 * HALO + nl[i]] & (V_NONFINITE | V_BAD);
-    const float wv = weight[gi];
-    if ((st & (V_NONFINITE | V_BAD)) || (f.boundary == 1 && k < 4)) {
-      const float fill = (st & (V_NONFINITE | V_BAD)) ? qnan() : 0.f;
-      for (int s = 0; s < 5; ++s)
-        for (int q = 0; q < B; ++q) rows[((long long)s * B + q) * plane + gi] = fill;
-      continue;
+      for (int d = 0; d < 4; ++d) {
+        // u is the opposite-direction neighbour of v = u + dir d
+        const int opp = (d + 2) & 3;
+        if (in_tile[d]) acc += sc[((1 + opp) * B + q) * TV + vn[d]];
+      }
+      grad[(long long)q * plane + gi] = acc;
+      // this centre's partials about vertices of other tiles
+      if (lr == 0) ring_t[q * 32 + lc] = sc[((1 + 1) * B + q) * TV + v];               // n
+      if (lr == TY - 1) ring_t[(B + q) * 32 + lc] = sc[((1 + 3) * B + q) * TV + v];    // s
+      if (lc == 0) ring_t[64 * B + q * 8 + lr] = sc[((1 + 2) * B + q) * TV + v];       // w
+      if (lc == TX - 1) ring_t[72 * B + q * 8 + lr] = sc[((1 + 0) * B + q) * TV + v];  // e
     }
+  }
+  // every read of the block is done: release it
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicExch(flags + slot, 0);
+  }
+}
+
+// Adds to every vertex on the edge of a tile the partials that centres of
+// the neighbouring tiles wrote about it (their rings), in the order e, n,
+// w, s: one thread per (tile, edge position); edge positions 0..31 top row,
+// 32..63 bottom row, 64..69 left column rows 1..6, 70..75 right column.
+__global__ void __launch_bounds__(256) hist_adj_fixup(Field f, int tiles_x, int ntiles,
+                                                      const float *__restrict__ ring,
+                                                      float *__restrict__ grad) {
+  constexpr int TY = kAdjTY, TX = 32, NP = 2 * TX + 2 * (TY - 2);
+  const int B = f.B;
+  const long long plane = f.plane;
+  const long long total = (long long)ntiles * NP;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int tile = (int)(t / NP), p = (int)(t % NP);
+    const int tr = tile / tiles_x, tc = tile % tiles_x;
+    int lr, lc;
+    if (p < TX) { lr = 0; lc = p; }
+    else if (p < 2 * TX) { lr = TY - 1; lc = p - TX; }
+    else if (p < 2 * TX + TY - 2) { lr = 1 + (p - 2 * TX); lc = 0; }
+    else { lr = 1 + (p - 2 * TX - (TY - 2)); lc = TX - 1; }
+    const int gy = f.y0 + tr * TY + lr, gx = tc * TX + lc;
+    if (gy >= f.y1 || gx >= f.W) continue;
+    const long long gi = (long long)gy * f.W + gx;
+    // the neighbouring tile's ring entry in direction d, if that neighbour
+    // is in the grid but outside this tile
+    const float *src[4];
+    bool have[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-      if (!present[i])
-        for (int q = 0; q < B; ++q) rows[((long long)(1 + i) * B + q) * plane + gi] = 0.f;
-    if (sm[l] == sm[HALO + l]) {
-      // a point-mass centre: the product of tails (global-memory path)
-      hist_grad_vertex(f.params, plane, gi, ni, present, B, mirrored, wv, rows);
-    } else {
-      hist_adj_walk<HALO, RS>(sm, R4, l, nl, present, B, mirrored, wv, rows, plane, gi);
+    for (int d = 0; d < 4; ++d) {
+      const int yy = gy + kDy[d], xx = gx + kDx[d];
+      const int rr = lr + kDy[d], cc = lc + kDx[d];
+      have[d] = yy >= 0 && yy < f.y1 && xx >= 0 && xx < f.W && !(rr >= 0 && rr < TY && cc >= 0 && cc < TX);
+      src[d] = ring;
+      if (!have[d]) continue;
+      const int nt = tile + (rr < 0 ? -tiles_x : (rr >= TY ? tiles_x : 0)) + (cc < 0 ? -1 : (cc >= TX ? 1 : 0));
+      const float *rt = ring + (long long)nt * kAdjRing * B;
+      if (d == 0) src[d] = rt + 64 * B + lr;        // e: the right tile's w ring (its left column)
+      else if (d == 1) src[d] = rt + B * 32 + lc;   // n: the upper tile's s ring (its bottom row)
+      else if (d == 2) src[d] = rt + 72 * B + lr;   // w: the left tile's e ring (its right column)
+      else src[d] = rt + lc;                        // s: the lower tile's n ring (its top row)
+    }
+    for (int q = 0; q < B; ++q) {
+      float acc = grad[(long long)q * plane + gi];
+#pragma unroll
+      for (int d = 0; d < 4; ++d)
+        if (have[d]) acc += src[d][(d == 0 || d == 2) ? q * 8 : q * 32];
+      grad[(long long)q * plane + gi] = acc;
     }
   }
 }
@@ -1236,8 +1383,36 @@ __global__ void __launch_bounds__(256) gather_kernel(Field f, int Q, const float
 
 }  // namespace
 
+// tiles of the per-bin-row histogram adjoint over the computed rows
+static long long adj_tiles(const Field &f, int *tiles_x) {
+  *tiles_x = (f.W + 31) / 32;
+  const long long tiles_y = (f.y1 - f.y0 + kAdjTY - 1) / kAdjTY;
+  return tiles_y > 0 ? (long long)*tiles_x * tiles_y : 0;
+}
+
+// scratch of the per-bin-row histogram adjoint: nslots claim flags (in 64
+// floats' room each 64 flags), the ring, nslots partial blocks
+static size_t adj_layout(long long nt, int B, long long nslots, long long *flags_f,
+                         long long *ring_f) {
+  *flags_f = (nslots + 63) / 64 * 64;
+  *ring_f = nt * kAdjRing * B;
+  return (size_t)(*flags_f + *ring_f + nslots * 5LL * B * kAdjTV);
+}
+
+size_t backward_scratch_floats(const Field &f, int model, int ctas) {
+  if (model == kHist && f.B <= 16) {
+    int tx;
+    const long long nt = adj_tiles(f, &tx);
+    long long a, b;
+    return adj_layout(nt, f.B, std::max(1, ctas), &a, &b);
+  }
+  const int Q = model == kHist ? f.B : 2;
+  return (size_t)5 * Q * (size_t)f.plane;
+}
+
 cudaError_t launch_backward(const Field &f, int model, int cptype, const float *weight,
-                            float *rows, float *grad, cudaStream_t s) {
+                            float *rows, size_t rows_floats, int max_ctas, float *grad,
+                            cudaStream_t s) {
   const int Q = model == kHist ? f.B : 2;
   long long b = (f.plane + 127) / 128;
   if (b > (1LL << 30)) b = 1LL << 30;
@@ -1247,7 +1422,9 @@ cudaError_t launch_backward(const Field &f, int model, int cptype, const float *
     case kEpan: partials_kernel<kEpan><<<(int)b, 128, 0, s>>>(f, want_max, weight, rows); break;
     case kHist: {
       if (f.B <= 16) {
-        // per-bin rows: 8-row tiles, two CTAs per SM
+        // per-bin rows, 8 x 32 tiles, two CTAs per SM; partials of a tile in
+        // its CTA's scratch block, gathered in place; ring partials after the
+        // tiles (see hist_adj_tile)
         static std::atomic<bool> attr_rows[2][128] = {};
         int dev = 0;
         cudaError_t e = cudaGetDevice(&dev);
@@ -1267,18 +1444,30 @@ cudaError_t launch_backward(const Field &f, int model, int cptype, const float *
           }
           attr_rows[which][dev].store(true, std::memory_order_release);
         }
-        const int tiles_x = (f.W + TX - 1) / TX, tiles_y = (f.y1 - f.y0 + 7) / 8;
-        const long long tiles = (long long)tiles_x * tiles_y;
-        if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-        if (tiles > 0) {
-          if (which == 0)
-            hist_adj_tile<8><<<(int)tiles, NTHREADS, hist_adj_smem(f.B), s>>>(f, tiles_x, want_max,
-                                                                              weight, rows);
-          else
-            hist_adj_tile<16><<<(int)tiles, NTHREADS, hist_adj_smem(f.B), s>>>(f, tiles_x,
-                                                                               want_max, weight, rows);
-        }
-        break;
+        int tiles_x;
+        const long long nt = adj_tiles(f, &tiles_x);
+        if (nt > 0x7fffffffLL) return cudaErrorInvalidValue;
+        if (nt == 0) return cudaSuccess;
+        // as many scratch blocks as fit, at most max_ctas
+        long long ns = std::max(1, max_ctas), flags_f, ring_f;
+        while (ns > 1 && adj_layout(nt, f.B, ns, &flags_f, &ring_f) > rows_floats) --ns;
+        if (adj_layout(nt, f.B, ns, &flags_f, &ring_f) > rows_floats) return cudaErrorInvalidValue;
+        int *flags = reinterpret_cast<int *>(rows);
+        float *ring = rows + flags_f, *scratch = ring + ring_f;
+        e = cudaMemsetAsync(flags, 0, (size_t)ns * sizeof(int), s);
+        if (e != cudaSuccess) return e;
+        if (which == 0)
+          hist_adj_tile<8><<<(int)nt, NTHREADS, hist_adj_smem(f.B), s>>>(
+              f, tiles_x, want_max, weight, flags, (int)ns, scratch, ring, grad);
+        else
+          hist_adj_tile<16><<<(int)nt, NTHREADS, hist_adj_smem(f.B), s>>>(
+              f, tiles_x, want_max, weight, flags, (int)ns, scratch, ring, grad);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const long long fx = (nt * (2 * 32 + 2 * (kAdjTY - 2)) + 255) / 256;
+        hist_adj_fixup<<<(int)std::min<long long>(fx, 1LL << 30), 256, 0, s>>>(f, tiles_x, (int)nt,
+                                                                              ring, grad);
+        return cudaGetLastError();
       }
       constexpr int TYg = kGradTY;
       // per device: the attribute is set once (host threads may race to set

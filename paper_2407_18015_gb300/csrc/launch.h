@@ -63,8 +63,15 @@ cudaError_t launch_hist_table(const float *params, long long V, int B, float *ta
 cudaError_t launch_stencil(const StencilField &f, int model, int stencil, int sm_count,
                            cudaStream_t s);
 
-// Adjoint: partial rows into `rows` ([5][Q][H][W]) then the gather into grad.
+// Adjoint.  Scratch `rows` of rows_floats floats: uniform, Epanechnikov and
+// histograms of more than 16 bins write partial rows [5][Q][H][W], then
+// gather them into grad; histograms of at most 16 bins use a ring of 80 B
+// floats per 8 x 32 tile plus a partial block of 5 * B * 256 floats per CTA
+// (at most max_ctas CTAs, fewer if the scratch is smaller).
+// backward_scratch_floats: the scratch the adjoint uses with `ctas` CTAs.
+size_t backward_scratch_floats(const Field &f, int model, int ctas);
 cudaError_t launch_backward(const Field &f, int model, int cptype, const float *weight,
-                            float *rows, float *grad, cudaStream_t s);
+                            float *rows, size_t rows_floats, int max_ctas, float *grad,
+                            cudaStream_t s);
 
 }  // namespace ucp

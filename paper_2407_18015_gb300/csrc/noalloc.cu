@@ -16,8 +16,10 @@
 // (cudaDeviceReset), which reloads the module.  Every call on a device shares
 // the one array: calls whose work
 // overlaps on the GPU (different streams, no ordering between them) race on
-// it.  The array keeps the last call's contents; nothing in it needs to start
-// at zero, because the partials pass writes every entry the gather pass reads.
+// it.  The array keeps the last call's contents; the histogram adjoint's
+// block flags, which must start at zero, are cleared by every call (a memset
+// on the stream, no allocation); every other entry read is first written by
+// the same call.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -30,29 +32,37 @@ using namespace ucp;
 
 namespace {
 
-// 16 MiB of partial rows: 5 * Q * H * W floats must fit (Q = 2 for uniform /
-// Epanechnikov, Q = bins for histograms).
+// 16 MiB of adjoint scratch: 5 * Q * H * W floats of partial rows (Q = 2 for
+// uniform / Epanechnikov, Q = bins for histograms of more than 16 bins); for
+// histograms of at most 16 bins the block flags, the ring (80 * B floats per
+// 8 x 32 tile) and at least one partial block of 1280 * B floats.
 constexpr size_t kStaticRowsFloats = size_t(4) << 20;
 
 __device__ __align__(256) float g_static_rows[kStaticRowsFloats];
 
 constexpr int kMaxDevices = 128;
 float *g_rows_dev[kMaxDevices] = {};
+int g_sms_dev[kMaxDevices] = {};
 std::mutex g_rows_mutex;
 
-int static_rows(int dev, float **out) {
+// the array's device address and the device's SM count, looked up once per
+// device (with that device current)
+int static_rows(int dev, float **out, int *sms) {
   if (dev < 0 || dev >= kMaxDevices) return UCP_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_rows_mutex);
   if (!g_rows_dev[dev]) {
     void *p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_rows);
-    if (e != cudaSuccess || p == nullptr) {
+    int n = 0;
+    if (cudaGetSymbolAddress(&p, g_static_rows) != cudaSuccess || p == nullptr ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
       cudaGetLastError();
       return UCP_ERR_CUDA;
     }
     g_rows_dev[dev] = static_cast<float *>(p);
+    g_sms_dev[dev] = n;
   }
   *out = g_rows_dev[dev];
+  *sms = g_sms_dev[dev];
   return UCP_OK;
 }
 
@@ -67,16 +77,6 @@ extern "C" int ucp_backward_static(const float *params, int H, int W,
   // the same checks, in the same order, as ucp_backward
   const int vrc = ucp_valid_backward(desc, cptype, H, W);
   if (vrc) return vrc;
-  const size_t Q = desc->model == UCP_HISTOGRAM ? (size_t)desc->bins : 2;
-  if ((size_t)H * (size_t)W > kStaticRowsFloats / (5 * Q)) return UCP_ERR_SHAPE;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
-    cudaGetLastError();
-    return UCP_ERR_CUDA;
-  }
-  float *rows = nullptr;
-  const int rc = static_rows(dev, &rows);
-  if (rc) return rc;
   Field f{};
   f.params = params;
   f.plane = (long long)H * W;
@@ -88,7 +88,19 @@ extern "C" int ucp_backward_static(const float *params, int H, int W,
   f.y1 = H;
   f.boundary = desc->boundary;
   f.cptypes = (unsigned)cptype;
-  const cudaError_t e = launch_backward(f, desc->model, cptype, weight, rows, grad_params,
-                                        (cudaStream_t)stream);
+  // the adjoint's scratch with a single CTA must fit the array (more CTAs
+  // take what is left)
+  if (backward_scratch_floats(f, desc->model, 1) > kStaticRowsFloats) return UCP_ERR_SHAPE;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return UCP_ERR_CUDA;
+  }
+  float *rows = nullptr;
+  int sms = 0;
+  const int rc = static_rows(dev, &rows, &sms);
+  if (rc) return rc;
+  const cudaError_t e = launch_backward(f, desc->model, cptype, weight, rows, kStaticRowsFloats,
+                                        4 * sms, grad_params, (cudaStream_t)stream);
   return e == cudaSuccess ? UCP_OK : UCP_ERR_CUDA;
 }

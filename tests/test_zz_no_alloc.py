@@ -48,16 +48,25 @@ def test_static_adjoint_matches_context_adjoint(ucp, model, mid, bins):
 
 
 def test_static_adjoint_rejects_oversize(ucp):
+    """Shapes whose scratch exceeds the fixed array are refused before any
+    launch: 5 * 2 * H * W floats for uniform / Epanechnikov; for histograms
+    of at most 16 bins 80 * B floats per 8 x 32 tile plus 1280 * B."""
     cap = ucp.ucp_backward_static_capacity()
     assert cap == 4 << 20
-    desc = ucp.make_desc("histogram", bins=16)
-    side = int((cap // (5 * 16)) ** 0.5) + 2
-    p = torch.zeros((18, side, side), device="cuda")
-    W = torch.zeros((side, side), device="cuda")
-    g = torch.zeros((16, side, side), device="cuda")
-    with pytest.raises(ucp.UcpError) as e:
-        ucp.ucp_backward_static(p, desc, ucp.UCP_MIN, W, g)
-    assert e.value.status == ucp.UCP_ERR_SHAPE
+    cases = [("histogram", 16, 8 * 60, 32 * 60),       # 3600 tiles: ring alone too large
+             ("uniform", 8, 700, 700)]                  # 4.9 M floats of partial rows
+    for model, bins, Hh, Ww in cases:
+        desc = ucp.make_desc(model, bins=bins)
+        P = 2 + bins if model == "histogram" else 2
+        Q = bins if model == "histogram" else 2
+        assert (model != "histogram" or
+                ((Hh + 7) // 8) * ((Ww + 31) // 32) * 80 * bins + 1280 * bins > cap)
+        p = torch.zeros((P, Hh, Ww), device="cuda")
+        W = torch.zeros((Hh, Ww), device="cuda")
+        g = torch.zeros((Q, Hh, Ww), device="cuda")
+        with pytest.raises(ucp.UcpError) as e:
+            ucp.ucp_backward_static(p, desc, ucp.UCP_MIN, W, g)
+        assert e.value.status == ucp.UCP_ERR_SHAPE
 
 
 def test_static_adjoint_checks_shapes_before_launch(ucp):
