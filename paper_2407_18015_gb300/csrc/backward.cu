@@ -906,58 +906,6 @@ __global__ void __launch_bounds__(NTHREADS, 2)
 // runs the same steps; row reads at crossings are predicated, partials are
 // stored when a neighbour leaves a bin (or the centre leaves one of its own).
 
-// Per-bin rows, lo, hi, total and status of one staged vertex straight from
-// its parameters (mirrored: -X, bins reversed), the masses held in
-// registers; the same rows and status as hist_row_table builds from a
-// parameter tile.
-template <int HALO, int RS, int RB>
-__device__ __forceinline__ void hist_rows_from_params(const Field &f, float *sm, float4 *R, int l,
-                                                      long long gi, int B, bool mirrored) {
-  const long long plane = f.plane;
-  const float a0 = f.params[gi], b0 = f.params[plane + gi];
-  const float a = mirrored ? -b0 : a0, b = mirrored ? -a0 : b0;
-  uint8_t st = (!isfinite(a) || !isfinite(b)) ? V_NONFINITE
-                                             : (a > b ? V_BAD : (a == b ? V_DEGENERATE : 0));
-  float m[RB];
-  float t = 0.f;
-#pragma unroll
-  for (int q = 0; q < RB; ++q) {
-    m[q] = 0.f;
-    if (q < B) {
-      m[q] = __ldg(f.params + (long long)(2 + (mirrored ? B - 1 - q : q)) * plane + gi);
-      if (!isfinite(m[q])) st |= V_NONFINITE;
-      else if (m[q] < 0.f) st |= V_BAD;
-      t += m[q];
-    }
-  }
-  R += l;
-  const float4 beyond = make_float4(0.f, t, 0.f, kFar);
-  if (a == b) {
-#pragma unroll
-    for (int k = 0; k <= RB; ++k)
-      if (k <= B) R[k * RS] = beyond;
-  } else {
-    // as hist_rows_build
-    const float w = b - a;
-    const float h = (B & (B - 1)) == 0 ? w * (1.f / (float)B) : w / (float)B, ih = frcp(h);
-    float c = 0.f, sk = t;
-#pragma unroll
-    for (int k = 0; k < RB; ++k) {
-      if (k < B) {
-        c += m[k];
-        const float sn = k + 1 < B ? t - c : 0.f;
-        R[k * RS] = make_float4(sk, t - sk, (sk - sn) * ih, k + 1 < B ? (float)(k + 1) * h : w);
-        sk = sn;
-      }
-    }
-    R[B * RS] = beyond;
-  }
-  sm[l] = a;
-  sm[HALO + l] = b;
-  sm[2 * HALO + l] = t;
-  sm[3 * HALO + l] = (float)st;
-}
-
 // the bin width of the rows of a support of width w (as hist_rows_build)
 __device__ __forceinline__ float rows_bin_width(float w, int B) {
   return (B & (B - 1)) == 0 ? w * (1.f / (float)B) : w / (float)B;

@@ -27,6 +27,12 @@ namespace ucp {
 template <int MODEL>
 __global__ void __launch_bounds__(256) fit_kernel(Field f) {
   const long long plane = f.plane;
+  // histogram masses count / N of up to 255 members, as a table
+  __shared__ float mtab[256];
+  if (MODEL == kHist && f.N <= 255) {
+    for (int c = threadIdx.x; c <= f.N; c += blockDim.x) mtab[c] = __fdiv_rn((float)c, (float)f.N);
+    __syncthreads();
+  }
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < plane;
        i += (long long)gridDim.x * blockDim.x) {
     const float *p = f.ens + i;
@@ -64,6 +70,28 @@ __global__ void __launch_bounds__(256) fit_kernel(Field f) {
       if (nf) {
         for (int q = 0; q < 2 + B; ++q) out[q * plane + i] = __int_as_float(0x7fc00000);
         st |= V_NONFINITE;
+      } else if (B <= 16 && f.N <= 255) {
+        // 8-bit bin counters packed in two 64-bit registers (no local memory)
+        unsigned long long c0 = 0ull, c1 = 0ull;
+        if (mn == mx) {
+          c0 = (unsigned long long)f.N;
+          st |= V_DEGENERATE;
+        } else {
+          const float s = __fdiv_rn((float)B, __fsub_rn(mx, mn));
+#pragma unroll 4
+          for (int k = 0; k < f.N; ++k) {
+            const int j = hist_bin_nonneg(__ldg(p + (long long)k * plane), mn, s, B);
+            const unsigned long long inc = 1ull << ((j & 7) << 3);
+            c0 += j < 8 ? inc : 0ull;
+            c1 += j < 8 ? 0ull : inc;
+          }
+        }
+        out[i] = mn;
+        out[plane + i] = mx;
+        for (int q = 0; q < B; ++q) {
+          const unsigned c = (unsigned)((q < 8 ? c0 : c1) >> ((q & 7) << 3)) & 255u;
+          out[(2 + q) * plane + i] = mtab[c];
+        }
       } else {
         int cnt[kMaxBins];
         for (int q = 0; q < B; ++q) cnt[q] = 0;
@@ -134,9 +162,11 @@ __global__ void __launch_bounds__(NTHREADS, (TileOcc<MODEL, RB>::value))
   const int tile = blockIdx.x;
   constexpr bool ROWS = RB > 0;
   float4 *R4 = nullptr;
+  // the per-thread staging counts into masses held in the tile; from
+  // parameters the rows are built from registers (small tile)
   if constexpr (ROWS)
     R4 = reinterpret_cast<float4 *>(
-        sm + ((param_tile_floats<MODEL, TYm, ROWS>(f.B, true) + 3) & ~3LL));
+        sm + ((param_tile_floats<MODEL, TYm, ROWS>(f.B, FROM_MEMBERS) + 3) & ~3LL));
   process_tile<MODEL, FROM_MEMBERS, TYm, SADDLE, false, RB>(
       f, f.y0 + (tile / tiles_x) * TYm, (tile % tiles_x) * TX, sm, nullptr, nullptr, nullptr, R4);
 }
@@ -288,7 +318,7 @@ static cudaError_t launch_tile_h(const Field &f, cudaStream_t s) {
   size_t smem = (size_t)tile_floats(MODEL, f.B, TYm) * sizeof(float);
   // histogram per-bin rows after the tile (launch_tile checked that they fit)
   if constexpr (RB > 0)
-    smem = (size_t)((param_tile_floats<MODEL, TYm, true>(f.B, true) + 3) & ~3LL) * sizeof(float) +
+    smem = (size_t)((param_tile_floats<MODEL, TYm, true>(f.B, FM) + 3) & ~3LL) * sizeof(float) +
            (size_t)r4_floats(f.B, TYm) * sizeof(float);
   // per device: the attribute is set once (several host threads may race to
   // set it; setting it twice is harmless, the flag itself is atomic)
@@ -340,16 +370,15 @@ static cudaError_t launch_tile(const Field &f, cudaStream_t s) {
   }
   if constexpr (MODEL == kHist) {
     // Per-bin rows on 8-row tiles: up to 8 bins at four CTAs per SM, up to
-    // 16 (fitted from members, counts in registers: at most 65535 members)
-    // at two; otherwise the segment walker on 16-row tiles, where the
-    // smaller halo wins.  The per-thread staging (members not TMA aligned)
-    // and the from-parameters path hold the masses in the tile and run the
-    // same rows.
+    // 16 at two (members counted in registers: at most 65535 of them);
+    // otherwise the segment walker on 16-row tiles, where the smaller halo
+    // wins.  The per-thread staging (members not TMA aligned) holds the
+    // masses in the tile; from parameters the rows are built from registers.
     const bool counts_ok = !FM || f.N <= 65535;
     if (counts_ok && f.B <= 8 &&
         hist_rows_bytes(f.B, 8) <= (size_t)227 * 1024 / TileOcc<kHist, 8>::value - 1024)
       return launch_tile_h<MODEL, FM, SADDLE, 8, 8>(f, s);
-    if (FM && counts_ok && f.B <= 16 &&
+    if (counts_ok && f.B <= 16 &&
         hist_rows_bytes(f.B, 8) <= (size_t)227 * 1024 / TileOcc<kHist, 16>::value - 1024)
       return launch_tile_h<MODEL, FM, SADDLE, 8, 16>(f, s);
     return launch_tile_h<MODEL, FM, SADDLE, TY, 0>(f, s);

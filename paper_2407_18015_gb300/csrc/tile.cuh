@@ -420,6 +420,58 @@ __device__ __forceinline__ void hist_row_table_counts(float *sm, float4 *R, int 
   sm[3 * HALO + l] = (float)st;
 }
 
+// Per-bin rows, lo, hi, total and status of one staged vertex straight from
+// its parameters (mirrored: -X, bins reversed), the masses held in
+// registers; the same rows and status as hist_row_table builds from a
+// parameter tile.
+template <int HALO, int RS, int RB>
+__device__ __forceinline__ void hist_rows_from_params(const Field &f, float *sm, float4 *R, int l,
+                                                      long long gi, int B, bool mirrored) {
+  const long long plane = f.plane;
+  const float a0 = f.params[gi], b0 = f.params[plane + gi];
+  const float a = mirrored ? -b0 : a0, b = mirrored ? -a0 : b0;
+  uint8_t st = (!isfinite(a) || !isfinite(b)) ? V_NONFINITE
+                                             : (a > b ? V_BAD : (a == b ? V_DEGENERATE : 0));
+  float m[RB];
+  float t = 0.f;
+#pragma unroll
+  for (int q = 0; q < RB; ++q) {
+    m[q] = 0.f;
+    if (q < B) {
+      m[q] = __ldg(f.params + (long long)(2 + (mirrored ? B - 1 - q : q)) * plane + gi);
+      if (!isfinite(m[q])) st |= V_NONFINITE;
+      else if (m[q] < 0.f) st |= V_BAD;
+      t += m[q];
+    }
+  }
+  R += l;
+  const float4 beyond = make_float4(0.f, t, 0.f, kFar);
+  if (a == b) {
+#pragma unroll
+    for (int k = 0; k <= RB; ++k)
+      if (k <= B) R[k * RS] = beyond;
+  } else {
+    // as hist_rows_build
+    const float w = b - a;
+    const float h = (B & (B - 1)) == 0 ? w * (1.f / (float)B) : w / (float)B, ih = frcp(h);
+    float c = 0.f, sk = t;
+#pragma unroll
+    for (int k = 0; k < RB; ++k) {
+      if (k < B) {
+        c += m[k];
+        const float sn = k + 1 < B ? t - c : 0.f;
+        R[k * RS] = make_float4(sk, t - sk, (sk - sn) * ih, k + 1 < B ? (float)(k + 1) * h : w);
+        sk = sn;
+      }
+    }
+    R[B * RS] = beyond;
+  }
+  sm[l] = a;
+  sm[HALO + l] = b;
+  sm[2 * HALO + l] = t;
+  sm[3 * HALO + l] = (float)st;
+}
+
 // ---------------------------------------------------------------------------
 // Member staging with the tensor memory accelerator: one bulk tensor copy
 // brings a box of nc members x (TYv + 2) rows x 40 columns (x from tx0 - 4, a
@@ -828,6 +880,15 @@ __device__ __forceinline__ void process_tile(const Field &f, int ty0, int tx0, f
         }
       }
     }
+  } else if constexpr (MODEL == kHist && RB > 0) {
+    // per-bin rows straight from the parameters (masses in registers)
+    constexpr int RS = hist_r4_stride(HALO);
+    for (int l = threadIdx.x; l < HALO; l += NTHREADS) {
+      const int r = l / HX, c = l - r * HX;
+      const int gy = ty0 + r - 1, gx = tx0 + c - 1;
+      if (gy < 0 || gy >= ylim || gx < 0 || gx >= f.W) continue;
+      hist_rows_from_params<HALO, RS, RB>(f, sm, R4, l, (long long)gy * f.W + gx, f.B, false);
+    }
   } else {
     for (int l = threadIdx.x; l < HALO; l += NTHREADS) {
       const int r = l / HX, c = l - r * HX;
@@ -841,7 +902,8 @@ __device__ __forceinline__ void process_tile(const Field &f, int ty0, int tx0, f
     mark_tile_timeout<TY, SADDLE>(f, ty0, tx0);
     return;
   }
-  integrate_tile<MODEL, TY, SADDLE, FROM_MEMBERS && TMA, (RB > 0)>(f, ty0, tx0, sm, R4);
+  integrate_tile<MODEL, TY, SADDLE, (FROM_MEMBERS && TMA) || (!FROM_MEMBERS && RB > 0),
+                 (RB > 0)>(f, ty0, tx0, sm, R4);
 }
 
 // Phase 2 of a tile whose parameters (and, if TABLES_BUILT, histogram tail
