@@ -250,10 +250,14 @@ int ucp_probability_host(ucp_ctx *ctx, const float *ens_host, int N, int H, int 
 
 #define UCP_MAX_MODELS 16
 
-/* Several models of one ensemble, device arrays: the models' kernels run
- * concurrently on the context's compute streams, forked from `stream` and
- * joined back into it (asynchronous; the results are those of
- * ucp_probability for each model).  descs[0..nmodels-1], 1 <= nmodels <=
+/* Several models of one ensemble, device arrays: one uniform, one
+ * Epanechnikov and one histogram model of at most 8 bins (in any order, one
+ * boundary rule, members 16-byte aligned with W a multiple of 4) run as one
+ * fused kernel on `stream` that stages the members once for all three;
+ * otherwise the models' kernels run concurrently on the context's compute
+ * streams, forked from `stream` and joined back into it (asynchronous
+ * either way; the results are those of ucp_probability for each model, bit
+ * for bit).  descs[0..nmodels-1], 1 <= nmodels <=
  * UCP_MAX_MODELS, none with a larger stencil (UCP_ERR_UNSUPPORTED);
  * cptypes applies to every model.  out_min[m] / out_max[m]: [H][W] device
  * arrays of model m for the types in cptypes, an entry may be NULL (that

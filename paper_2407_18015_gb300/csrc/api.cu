@@ -115,6 +115,51 @@ int ucp_ensure_work(ucp_ctx *ctx, size_t bytes) {
   return UCP_OK;
 }
 
+// The fused three-model kernel (fused.cu) when `descs` are one uniform, one
+// Epanechnikov and one histogram of at most 8 bins with one boundary rule:
+// order[m] = the kernel's model slot of descs[m] (0 uniform, 1
+// Epanechnikov, 2 histogram); false otherwise.
+bool ucp_fusable3(const ucp_model_desc *descs, int nmodels, int order[3]) {
+  if (nmodels != 3) return false;
+  bool seen[3] = {false, false, false};
+  for (int m = 0; m < 3; ++m) {
+    const ucp_model_desc &d = descs[m];
+    int slot = d.model == UCP_UNIFORM ? 0 : d.model == UCP_EPANECHNIKOV ? 1
+             : d.model == UCP_HISTOGRAM ? 2 : -1;
+    if (slot < 0 || seen[slot] || d.stencil != UCP_STENCIL_4 || d.depth > 1) return false;
+    if (slot == 2 && d.bins > 8) return false;
+    if (d.boundary != descs[0].boundary) return false;
+    seen[slot] = true;
+    order[m] = slot;
+  }
+  return true;
+}
+
+// Fused launch of the three models on rows [y0, y1) of ens; *launched tells
+// whether it applied.
+int ucp_launch_fused3(ucp_ctx *ctx, const float *ens, int N, int H, int W,
+                      const ucp_model_desc *descs, const int order[3], unsigned cptypes,
+                      float *const *out_min, float *const *out_max, uint8_t *const *status,
+                      int y0, int y1, cudaStream_t stream, bool *launched) {
+  Field3 F{};
+  Field &f = F.f;
+  f.ens = ens;
+  f.plane = (long long)H * W;
+  f.N = N; f.H = H; f.W = W;
+  f.y0 = y0; f.y1 = y1;
+  f.boundary = descs[0].boundary;
+  f.cptypes = cptypes;
+  for (int m = 0; m < 3; ++m) {
+    const int sl = order[m];
+    if (sl == 1) f.epan_scale = epan_scale(descs + m);
+    if (sl == 2) f.B = descs[m].bins;
+    F.out_min[sl] = (cptypes & 1u) ? out_min[m] : nullptr;
+    F.out_max[sl] = (cptypes & 2u) ? out_max[m] : nullptr;
+    F.status[sl] = status ? status[m] : nullptr;
+  }
+  return ucp_set_error(ctx, launch_closed3(F, stream, launched));
+}
+
 extern "C" {
 
 const char *ucp_status_string(int status) {
@@ -393,6 +438,14 @@ int ucp_probability_models(ucp_ctx *ctx, const float *ens, int N, int H, int W,
   }
   DeviceGuard g(ctx->device);
   if (g.err != cudaSuccess) return ucp_set_error(ctx, g.err);
+  // uniform + Epanechnikov + histogram: one fused kernel on `stream`
+  int order[3];
+  if (ucp_fusable3(descs, nmodels, order)) {
+    bool launched = false;
+    rc = ucp_launch_fused3(ctx, ens, N, H, W, descs, order, cptypes, out_min, out_max,
+                           vertex_status, 0, H, (cudaStream_t)stream, &launched);
+    if (rc || launched) return rc;
+  }
   if ((rc = ucp_ensure_pipe(ctx))) return rc;
   const int ncs = nmodels < ucp_ctx::kPipeCompute ? nmodels : ucp_ctx::kPipeCompute;
   // fork: every compute stream starts after the work queued on `stream`

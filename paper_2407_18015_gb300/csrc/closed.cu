@@ -245,6 +245,8 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
+void *tensor_map_encoder_fn() { return reinterpret_cast<void *>(tensor_map_encoder()); }
+
 // Members per TMA box next to a TYm-row parameter tile at the model's
 // occupancy (0: not even one), capped at N and at the box limit of 256.
 template <int MODEL, int TYm, int RB>

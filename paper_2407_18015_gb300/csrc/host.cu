@@ -119,11 +119,28 @@ int ucp_host_pipeline(ucp_ctx *ctx, const float *ens_host, int N, int H, int W,
     }
     if (e == cudaSuccess) e = cudaEventRecord(ctx->pipe_ev[0][nstrips], s_in);
   }
+  // uniform + Epanechnikov + histogram: the fused kernel, one launch per strip
+  int order[3];
+  const bool fuse = ucp_fusable3(descs, nmodels, order);
+  int fused_rc = UCP_OK;
   for (int i = 0; i < nstrips && e == cudaSuccess; ++i) {
     const int r0 = start[i], r1 = start[i + 1];
     for (int c = 0; c < ncs && e == cudaSuccess; ++c)
       e = cudaStreamWaitEvent(ctx->pipe[2 + c], ctx->pipe_ev[0][i], 0);
-    for (int m = 0; m < nmodels && e == cudaSuccess; ++m) {
+    bool fused = false;
+    if (fuse && e == cudaSuccess) {
+      float *omin[3], *omax[3];
+      uint8_t *ost[3];
+      for (int m = 0; m < 3; ++m) {
+        omin[m] = d_out + (size_t)(2 * m) * plane;
+        omax[m] = d_out + (size_t)(2 * m + 1) * plane;
+        ost[m] = d_st + (size_t)m * plane;
+      }
+      fused_rc = ucp_launch_fused3(ctx, ctx->host_ens, N, H, W, descs, order, cptypes, omin,
+                                   omax, ost, r0, r1, ctx->pipe[2], &fused);
+      if (fused_rc) break;
+    }
+    for (int m = 0; m < nmodels && e == cudaSuccess && !fused; ++m) {
       cudaStream_t s_cmp = ctx->pipe[2 + m % ncs];
       const ucp_model_desc *desc = descs + m;
       Field f{};
@@ -169,5 +186,6 @@ int ucp_host_pipeline(ucp_ctx *ctx, const float *ens_host, int N, int H, int W,
     const cudaError_t ek = cudaStreamSynchronize(ctx->pipe[k]);
     if (e == cudaSuccess) e = ek;
   }
+  if (fused_rc) return fused_rc;
   return ucp_set_error(ctx, e);
 }

@@ -34,6 +34,24 @@ inline int param_planes(int model, int B) {
   return (model == 2 || model == 4) ? 2 + B : (model == 3 ? 20 : 2);
 }
 
+// The uniform, Epanechnikov and histogram (at most 8 bins) models of one
+// ensemble in one kernel (fused.cu): the members staged once, every model
+// integrated per tile with the arithmetic of its own kernel.  f carries the
+// ensemble, grid, rows, boundary, Epanechnikov scale and types; the outputs
+// and status arrays of model m (0 uniform, 1 Epanechnikov, 2 histogram) are
+// out_min[m], out_max[m], status[m] (each may be null when not wanted).
+struct Field3 {
+  Field f;
+  float *out_min[3];
+  float *out_max[3];
+  uint8_t *status[3];
+};
+// Launches the fused kernel when it applies (members TMA aligned, at most 8
+// bins and 65535 members); *launched tells whether it did.
+cudaError_t launch_closed3(const Field3 &f, cudaStream_t s, bool *launched);
+// cuTensorMapEncodeTiled from the driver (nullptr if unavailable)
+void *tensor_map_encoder_fn();
+
 cudaError_t launch_fit(const Field &f, int model, cudaStream_t s);
 cudaError_t launch_closed(const Field &f, int model, bool from_members, cudaStream_t s);
 cudaError_t launch_eb_params(const float *d, float eb, long long n, float *params,

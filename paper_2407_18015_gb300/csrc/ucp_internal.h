@@ -40,6 +40,14 @@ int ucp_set_error(ucp_ctx *ctx, cudaError_t e);
 int ucp_valid_desc(const ucp_model_desc *d, bool allow_sampled);
 int ucp_valid_shape(long long N, long long H, long long W);
 int ucp_valid_backward(const ucp_model_desc *desc, int cptype, int H, int W);
+// the fused three-model kernel (uniform, Epanechnikov, histogram of at most 8
+// bins, one boundary rule): whether `descs` qualify, with each one's model
+// slot, and its launch on rows [y0, y1)
+bool ucp_fusable3(const ucp_model_desc *descs, int nmodels, int order[3]);
+int ucp_launch_fused3(ucp_ctx *ctx, const float *ens, int N, int H, int W,
+                      const ucp_model_desc *descs, const int order[3], unsigned cptypes,
+                      float *const *out_min, float *const *out_max, uint8_t *const *status,
+                      int y0, int y1, cudaStream_t stream, bool *launched);
 int ucp_ensure_work(ucp_ctx *ctx, size_t bytes);
 // the context's streams and events of the multi-model entry points (once)
 int ucp_ensure_pipe(ucp_ctx *ctx);

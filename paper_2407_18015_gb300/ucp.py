@@ -251,10 +251,12 @@ def ucp_probability_host(ctx, ens_host, desc, cptypes, out_min_host, out_max_hos
 
 def ucp_probability_models(ctx, ens, descs, cptypes, out_min, out_max, vertex_status=None,
                            stream=None):
-    """Several models of one ensemble (device tensors), their kernels
-    concurrent on the context's streams, forked from and joined back into the
-    current stream.  descs, out_min, out_max (and vertex_status, if given) are
-    sequences of the same length; an output entry may be None."""
+    """Several models of one ensemble (device tensors): uniform,
+    Epanechnikov and a histogram of at most 8 bins in one fused kernel on the
+    current stream, other sets as kernels concurrent on the context's
+    streams, forked from and joined back into the current stream.  descs,
+    out_min, out_max (and vertex_status, if given) are sequences of the same
+    length; an output entry may be None."""
     H, W = _grid(ens, descs[0], "ens")
     n = len(descs)
     if len(out_min) != n or len(out_max) != n or \
