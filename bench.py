@@ -3,10 +3,10 @@
 Headline workload (one step): a 1024 x 1024 grid with N = 20 float32 members
 (seeded bimodal mixture around a smooth sinusoid base), probability of local
 minimum and maximum under the uniform, Epanechnikov and 8-bin histogram
-models, each a fused statistics + integration kernel, the three launched by one
-ucp_probability_models call (their kernels concurrent on the context's
-streams).  value = grid vertices per second with all three models evaluated
-(whole job over all ranks).
+models, one ucp_probability_models call: one fused kernel stages the members
+once and integrates all three models.  value = grid vertices per second with
+all three models evaluated (whole job over all ranks).  per_model times each
+model's own kernel (ucp_probability) on the same workload.
 
 Also measured in the same run (key "rows"): the multivariate-Gaussian Monte
 Carlo workload (512^2 x 40, 10,000 Philox samples per vertex), the forward +
@@ -189,12 +189,11 @@ ADJ_HIST_FLOPS_PER_PIECE = 5 * HIST_FLOPS_PER_PIECE_TYPE
 ADJ_EPAN_FLOPS_PER_VERTEX = 2 * EPAN_FLOPS_PER_VERTEX_TYPE
 
 
-# DRAM bytes (read + write) per launch of each headline kernel from the ncu
-# capture summarised in profiles/; None once a kernel has changed since its
-# counters were taken
-TRAFFIC_BYTES = {"uniform": 83.921408e6 + 4.750592e6,
-                 "epanechnikov": 83.937536e6 + 4.673024e6,
-                 "histogram": 83.967488e6 + 5.478144e6}
+# DRAM bytes (read + write) per launch of the step's kernel (the fused
+# three-model kernel) and of each model's own kernel, from the ncu captures
+# summarised in profiles/; None once a kernel has changed since its counters
+# were taken
+TRAFFIC_BYTES = {"fused": None, "uniform": None, "epanechnikov": None, "histogram": None}
 
 
 def work_of(model, N, HW, params=None, bins=BINS2):
@@ -382,8 +381,7 @@ def run_ours(args):
     omax = [outs[m][1] for m, _ in MODELS2]
 
     def step(ev):
-        # the three models of one ensemble, their kernels concurrent on the
-        # context's streams (forked from and joined into this stream)
+        # the three models of one ensemble: one fused kernel on this stream
         ucp.ucp_probability_models(ctx.handle, ens, dlist, ucp.UCP_MIN | ucp.UCP_MAX, omin, omax)
 
     def step_seq(ev):
@@ -418,6 +416,7 @@ def run_ours(args):
     # per-kernel durations (separate pass, same launches, events between kernels)
     _, kms = timed_steps(torch, step_seq, max(5, args.steps // 2), 1, flush,
                          per_kernel_events=True)
+    local_ms = total_ms
     total_ms, _, value = replicas.job_throughput(total_ms, H2 * W2 * args.steps, device=dev)
 
     peaks = measured_peaks()
@@ -433,17 +432,34 @@ def run_ours(args):
             ach, peak, unit = amount / (avg / 1e3) / 1e12, fp32_peak_tflops(
                 peaks["sm_max_mhz"]), "TFLOP/s"
         per_model[m] = {"ms": avg, "vertices_per_s": H2 * W2 / (avg / 1e3),
+                        "kernel": "the model's own fused fit + integrate kernel",
                         "roofline": {"bound": bound, "achieved": ach, "peak": peak,
-                                     "unit": unit, "frac": ach / peak}}
+                                     "unit": unit, "frac": ach / peak,
+                                     "traffic": TRAFFIC_BYTES[m]}}
         shares[m] = avg
-    dom = max(shares, key=shares.get)
-    rf = dict(per_model[dom]["roofline"])
-    rf["kernel"] = f"tile_kernel_tma<{dom}> (members staged by TMA)"
-    rf["traffic"] = TRAFFIC_BYTES.get(dom)
-    rf["traffic_source"] = "profiles/tile_kernels_1024x1024x20.md (ncu dram__bytes_read/write)"
-    rf["peak_source"] = ("MEASURED_PEAKS.json hbm_gbs" if rf["bound"] == "hbm" else
-                         f"152 SMs x 128 FP32 lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz")
-    rf["share"] = shares[dom] / sum(shares.values())
+    # The step is one launch of the fused kernel (uniform + Epanechnikov +
+    # histogram, members staged once): its duration is the step's.  Its
+    # algorithmic work is the FP32 work of the Epanechnikov and histogram
+    # integrations (the uniform model has none), both types.
+    t_kernel = local_ms / args.steps
+    hist_params = ctx.fit(ens, descs["histogram"])
+    fl = (2.0 * EPAN_FLOPS_PER_VERTEX_TYPE * H2 * W2 +
+          2.0 * HIST_FLOPS_PER_PIECE_TYPE * float(hist_piece_counts(hist_params, BINS2).sum().item()))
+    del hist_params
+    pk = fp32_peak_tflops(peaks["sm_max_mhz"])
+    ach = fl / (t_kernel / 1e3) / 1e12
+    hbm_b = (4.0 * N2 + 6 * 4.0) * H2 * W2
+    rf = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+          "kernel": "tile3_kernel (uniform + Epanechnikov + histogram-8 of one ensemble, "
+                    "members staged once by TMA)",
+          "traffic": TRAFFIC_BYTES["fused"],
+          "traffic_source": "profiles/fused_kernel_1024x1024x20.md (ncu dram__bytes_read/write)",
+          "work": f"{EPAN_FLOPS_PER_VERTEX_TYPE} flops per vertex and type (Epanechnikov) + "
+                  f"{HIST_FLOPS_PER_PIECE_TYPE} per merged histogram piece and type",
+          "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz (derived)",
+          "hbm_achieved_gbs": hbm_b / (t_kernel / 1e3) / 1e9,
+          "hbm_frac": hbm_b / (t_kernel / 1e3) / 1e9 / peaks["hbm_gbs"],
+          "share": 1.0}
 
     line = {
         "metric": "critical-point probability vertices/s (uniform + Epanechnikov + "
@@ -457,7 +473,7 @@ def run_ours(args):
                    "grid": [H2, W2], "members": N2, "bins": BINS2,
                    "parallelism": f"replicas x{world}",
                    "l2": "flushed between timed steps (512 MB written, then another 512 MB read)"},
-        "gpu_launches": len(MODELS2) * args.steps,
+        "gpu_launches": args.steps,
         "clocks": clocks,
         "roofline": rf,
         "per_model": per_model,

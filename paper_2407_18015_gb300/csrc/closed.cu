@@ -377,10 +377,14 @@ static cudaError_t launch_tile(const Field &f, cudaStream_t s) {
     // wins.  The per-thread staging (members not TMA aligned) holds the
     // masses in the tile; from parameters the rows are built from registers.
     const bool counts_ok = !FM || f.N <= 65535;
+    // members the tensor memory accelerator cannot stage are staged per
+    // thread with their masses in the tile: too much shared memory beside
+    // 16-bin rows (one CTA per SM), so those take the segment walker
+    const bool tma_ok = f.W % 4 == 0 && (reinterpret_cast<uintptr_t>(f.ens) & 15) == 0;
     if (counts_ok && f.B <= 8 &&
         hist_rows_bytes(f.B, 8) <= (size_t)227 * 1024 / TileOcc<kHist, 8>::value - 1024)
       return launch_tile_h<MODEL, FM, SADDLE, 8, 8>(f, s);
-    if (counts_ok && f.B <= 16 &&
+    if (counts_ok && f.B <= 16 && (!FM || tma_ok) &&
         hist_rows_bytes(f.B, 8) <= (size_t)227 * 1024 / TileOcc<kHist, 16>::value - 1024)
       return launch_tile_h<MODEL, FM, SADDLE, 8, 16>(f, s);
     return launch_tile_h<MODEL, FM, SADDLE, TY, 0>(f, s);
