@@ -16,6 +16,7 @@
 // a batch of that model's fields alone (CUDA events on the caller's stream,
 // best of three), and the fastest is kept; results are cached in a small JSON
 // file keyed by model, bin count and a member-count class.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -100,6 +101,88 @@ __global__ void __launch_bounds__(NTHREADS, 3)
   }
 }
 
+// ---------------------------------------------------------------------------
+// classes of fields whose members the tensor memory accelerator stages: one
+// persistent kernel per class (model, tile height, per-bin rows), each at
+// its own occupancy, with the single-field kernels' layout and tile body;
+// every field carries the tensor map of its members in the device work list
+
+struct alignas(64) TmaItem {
+  CUtensorMap tmap;  // the members' box of this field (64-byte aligned)
+  Field f;           // f.tma_nc: members per box
+  int tiles_x;
+  long long first;   // index of the field's first tile in the class's list
+};
+
+struct TmaClass {
+  int model, ty, rb;
+};
+constexpr int kNumTmaCls = 6;
+constexpr TmaClass kTmaCls[kNumTmaCls] = {{kUniform, 8, 0}, {kUniform, 16, 0}, {kEpan, 8, 0},
+                                          {kEpan, 16, 0},    {kHist, 8, 8},     {kHist, 8, 16}};
+
+// resident CTAs per SM of a class kernel: the single-field kernel's, at
+// most four (the persistent loop's own registers do not fit beside the
+// tile body's at five)
+template <int MODEL, int RB>
+struct BatchOcc {
+  static constexpr int value = TileOcc<MODEL, RB>::value > 4 ? 4 : TileOcc<MODEL, RB>::value;
+};
+
+template <int MODEL, int TYm, int RB>
+__global__ void __launch_bounds__(NTHREADS, (BatchOcc<MODEL, RB>::value))
+    batch_tma_kernel(const TmaItem *__restrict__ items, int nitems, long long total,
+                     unsigned long long *__restrict__ counter) {
+  extern __shared__ __align__(128) float smem[];
+  __shared__ long long s_tile;
+  __shared__ int s_item;
+  // the current field's description, read from shared memory where used
+  // (as the single-field kernel reads its parameter), not held in registers
+  __shared__ __align__(16) Field s_f;
+  constexpr bool ROWS = RB > 0;
+  static_assert(sizeof(Field) % 4 == 0, "copied as words");
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const long long t = (long long)atomicAdd(counter, 1ull);
+      int lo = 0, hi = nitems - 1;
+      if (t < total) {
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (items[mid].first <= t) lo = mid;
+          else hi = mid - 1;
+        }
+      }
+      s_tile = t;
+      s_item = lo;
+    }
+    __syncthreads();
+    const long long t = s_tile;
+    if (t >= total) break;
+    const TmaItem &it = items[s_item];
+    for (int w = threadIdx.x; w < (int)(sizeof(Field) / 4); w += NTHREADS)
+      reinterpret_cast<int *>(&s_f)[w] = reinterpret_cast<const int *>(&it.f)[w];
+    __syncthreads();
+    const Field &f = s_f;
+    const long long local = t - it.first;
+    const int ty0 = f.y0 + (int)(local / it.tiles_x) * TYm, tx0 = (int)(local % it.tiles_x) * 32;
+    // the single-field kernel's layout: member box (per-bin rows in its
+    // room), parameter tile, mbarrier
+    const int box_floats = f.tma_nc * (TYm + 2) * kBoxW;
+    const int r4 = ROWS ? r4_floats(f.B, TYm) : 0;
+    float *sm = smem + max(box_floats, r4);
+    const long long tile_f = param_tile_floats<MODEL, TYm, ROWS>(f.B, false);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + ((tile_f + 1) & ~1LL));
+    const bool ok = process_tile<MODEL, true, TYm, false, true, RB>(
+        f, ty0, tx0, sm, &it.tmap, smem, bar, ROWS ? reinterpret_cast<float4 *>(smem) : nullptr);
+    __syncthreads();
+    // a copy that gave up may still land: this CTA takes no further tile
+    if (!ok) break;
+    // the barrier's room may hold other data in the next tile
+    if (threadIdx.x == 0) mbar_inval(bar);
+    __syncthreads();
+  }
+}
+
 // relative cost of one vertex (bench-calibrated magnitudes; only the order
 // of fields matters)
 double vertex_cost(int model, int N, int B) {
@@ -173,11 +256,19 @@ struct ucp_batch {
   bool dirty = true;
   BatchItem *d_items = nullptr;
   size_t d_cap = 0;
-  unsigned long long *d_counter = nullptr;
+  unsigned long long *d_counter = nullptr;  // generic list, then one per TMA class
   long long total = 0;
   int nitems = 0;
   size_t smem = 0;
   int grid = 0;
+  // TMA classes: items of class c at d_tma[tma_off[c] .. + tma_n[c])
+  TmaItem *d_tma = nullptr;
+  size_t d_tma_cap = 0;
+  size_t tma_off[kNumTmaCls] = {};
+  int tma_n[kNumTmaCls] = {};
+  long long tma_total[kNumTmaCls] = {};
+  size_t tma_smem[kNumTmaCls] = {};
+  int tma_grid[kNumTmaCls] = {};
 };
 
 namespace {
@@ -189,13 +280,98 @@ size_t tile_smem(const BatchItem &b) {
 // dynamic shared memory one CTA may use on this architecture (227 KB)
 constexpr size_t kSmemPerBlock = 227 * 1024;
 
-// order, tile and upload a list (synchronous: not inside a stream capture);
-// an item whose tile at the requested height would not fit in shared memory
-// (histograms with many bins) takes the next lower height
-int finalize(ucp_batch *b, std::vector<BatchItem> list, const int *th) {
+// the class kernel of class c
+const void *tma_kernel(int c) {
+  switch (c) {
+    case 0: return reinterpret_cast<const void *>(batch_tma_kernel<kUniform, 8, 0>);
+    case 1: return reinterpret_cast<const void *>(batch_tma_kernel<kUniform, 16, 0>);
+    case 2: return reinterpret_cast<const void *>(batch_tma_kernel<kEpan, 8, 0>);
+    case 3: return reinterpret_cast<const void *>(batch_tma_kernel<kEpan, 16, 0>);
+    case 4: return reinterpret_cast<const void *>(batch_tma_kernel<kHist, 8, 8>);
+    default: return reinterpret_cast<const void *>(batch_tma_kernel<kHist, 8, 16>);
+  }
+}
+
+// the TMA class of an item at the tuned tile heights, -1 for none
+int tma_class_of(const BatchItem &it, const int *th) {
+  if (it.model == kUniform || it.model == kEpan) {
+    const int ty = kTileHeights[th[it.model]];
+    if (ty > 16) return -1;
+    return (it.model == kUniform ? 0 : 2) + (ty == 16 ? 1 : 0);
+  }
+  if (it.f.B <= 8) return 4;
+  return it.f.B <= 16 ? 5 : -1;
+}
+
+// order, tile and upload a list (synchronous: not inside a stream capture).
+// Fields whose members the tensor memory accelerator can stage go to their
+// class (tile heights of uniform and Epanechnikov as tuned, 8 or 16; 8 for
+// histograms of up to 16 bins), the rest to the generic list; a generic
+// item whose tile at the requested height would not fit in shared memory
+// (histograms with many bins) takes the next lower height.
+int finalize(ucp_batch *b, std::vector<BatchItem> all, const int *th) {
+  std::vector<BatchItem> list;
+  std::vector<TmaItem> cls[kNumTmaCls];
+  size_t csm[kNumTmaCls] = {};
+  for (const auto &it : all) {
+    const int c = tma_class_of(it, th);
+    size_t sm = 0;
+    const int nc = c < 0 ? 0 : tma_plan(kTmaCls[c].model, kTmaCls[c].ty, kTmaCls[c].rb, it.f, &sm);
+    TmaItem ti{};
+    ti.f = it.f;
+    ti.f.tma_nc = nc;
+    if (nc > 0 && encode_member_map(&ti.tmap, ti.f, kTmaCls[c].ty, nc)) {
+      ti.tiles_x = (it.f.W + 31) / 32;
+      cls[c].push_back(ti);
+      csm[c] = std::max(csm[c], sm);
+    } else {
+      list.push_back(it);
+    }
+  }
+  std::vector<TmaItem> flat;
+  for (int c = 0; c < kNumTmaCls; ++c) {
+    const TmaClass &k = kTmaCls[c];
+    std::stable_sort(cls[c].begin(), cls[c].end(), [&k](const TmaItem &x, const TmaItem &y) {
+      return vertex_cost(k.model, x.f.N, x.f.B) > vertex_cost(k.model, y.f.N, y.f.B);
+    });
+    long long first = 0;
+    for (auto &ti : cls[c]) {
+      ti.first = first;
+      first += (long long)ti.tiles_x * ((ti.f.H + k.ty - 1) / k.ty);
+    }
+    b->tma_off[c] = flat.size();
+    b->tma_n[c] = (int)cls[c].size();
+    b->tma_total[c] = first;
+    b->tma_smem[c] = csm[c];
+    flat.insert(flat.end(), cls[c].begin(), cls[c].end());
+    b->tma_grid[c] = 0;
+    if (cls[c].empty()) continue;
+    // the plan keeps 1 KB of each CTA's share free, room for the kernel's
+    // static shared variables (the field and the claimed tile)
+    cudaError_t e = cudaFuncSetAttribute(tma_kernel(c), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)csm[c]);
+    int per_sm = 0;
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tma_kernel(c), NTHREADS, csm[c]);
+    if (e != cudaSuccess) return ucp_set_error(b->ctx, e);
+    b->tma_grid[c] = std::max(per_sm, 1) * b->ctx->sm_count;
+  }
+  if (flat.size() > b->d_tma_cap) {
+    if (b->d_tma) cudaFree(b->d_tma);
+    b->d_tma = nullptr;
+    b->d_tma_cap = 0;
+    cudaError_t e = cudaMalloc(&b->d_tma, flat.size() * sizeof(TmaItem));
+    if (e != cudaSuccess) return ucp_set_error(b->ctx, e);
+    b->d_tma_cap = flat.size();
+  }
+  if (!flat.empty()) {
+    cudaError_t e = cudaMemcpy(b->d_tma, flat.data(), flat.size() * sizeof(TmaItem),
+                               cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return ucp_set_error(b->ctx, e);
+  }
   for (auto &it : list) {
     it.th = th[it.model];
-    while (it.th > 0 && tile_smem(it) > kSmemPerBlock) --it.th;
+    while (it.th > 0 && tile_smem(it) > kSmemPerBlock - 1024) --it.th;
     it.tiles_x = (it.f.W + 31) / 32;
   }
   std::stable_sort(list.begin(), list.end(), [](const BatchItem &x, const BatchItem &y) {
@@ -239,13 +415,34 @@ int finalize(ucp_batch *b, std::vector<BatchItem> list, const int *th) {
 }
 
 int launch(ucp_batch *b, cudaStream_t s) {
-  if (b->total == 0) return UCP_OK;
-  cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), s);
+  cudaError_t e = cudaMemsetAsync(b->d_counter, 0, (1 + kNumTmaCls) * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return ucp_set_error(b->ctx, e);
-  const long long want = std::min<long long>(b->total, b->grid);
-  batch_kernel<<<(int)want, NTHREADS, b->smem, s>>>(b->d_items, b->nitems, b->total,
-                                                    b->d_counter);
-  return ucp_set_error(b->ctx, cudaGetLastError());
+  // the most expensive classes first: histograms, then Epanechnikov
+  for (int c = kNumTmaCls - 1; c >= 0 && e == cudaSuccess; --c) {
+    if (b->tma_total[c] == 0) continue;
+    const int g = (int)std::min<long long>(b->tma_total[c], b->tma_grid[c]);
+    const TmaItem *items = b->d_tma + b->tma_off[c];
+    const int n = b->tma_n[c];
+    const long long tot = b->tma_total[c];
+    unsigned long long *ctr = b->d_counter + 1 + c;
+    const size_t sm = b->tma_smem[c];
+    switch (c) {
+      case 0: batch_tma_kernel<kUniform, 8, 0><<<g, NTHREADS, sm, s>>>(items, n, tot, ctr); break;
+      case 1: batch_tma_kernel<kUniform, 16, 0><<<g, NTHREADS, sm, s>>>(items, n, tot, ctr); break;
+      case 2: batch_tma_kernel<kEpan, 8, 0><<<g, NTHREADS, sm, s>>>(items, n, tot, ctr); break;
+      case 3: batch_tma_kernel<kEpan, 16, 0><<<g, NTHREADS, sm, s>>>(items, n, tot, ctr); break;
+      case 4: batch_tma_kernel<kHist, 8, 8><<<g, NTHREADS, sm, s>>>(items, n, tot, ctr); break;
+      default: batch_tma_kernel<kHist, 8, 16><<<g, NTHREADS, sm, s>>>(items, n, tot, ctr); break;
+    }
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && b->total > 0) {
+    const long long want = std::min<long long>(b->total, b->grid);
+    batch_kernel<<<(int)want, NTHREADS, b->smem, s>>>(b->d_items, b->nitems, b->total,
+                                                      b->d_counter);
+    e = cudaGetLastError();
+  }
+  return ucp_set_error(b->ctx, e);
 }
 
 int apply_cache(ucp_batch *b) {
@@ -272,7 +469,7 @@ int ucp_batch_create(ucp_ctx *ctx, ucp_batch **batch) {
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(ctx->device);
-  cudaError_t e = cudaMalloc(&b->d_counter, sizeof(unsigned long long));
+  cudaError_t e = cudaMalloc(&b->d_counter, (1 + kNumTmaCls) * sizeof(unsigned long long));
   if (prev >= 0) cudaSetDevice(prev);
   if (e != cudaSuccess) {
     delete b;
@@ -396,6 +593,7 @@ int ucp_batch_destroy(ucp_batch *batch) {
   cudaGetDevice(&prev);
   cudaSetDevice(batch->ctx->device);
   if (batch->d_items) cudaFree(batch->d_items);
+  if (batch->d_tma) cudaFree(batch->d_tma);
   if (batch->d_counter) cudaFree(batch->d_counter);
   if (prev >= 0) cudaSetDevice(prev);
   delete batch;

@@ -115,18 +115,6 @@ __global__ void __launch_bounds__(256) fit_kernel(Field f) {
 // ---------------------------------------------------------------------------
 // tile kernel
 
-// resident CTAs per SM each model's register budget is tuned for.  RB > 0:
-// histogram tiles that walk per-bin rows of at most RB bins -- four CTAs
-// per SM for 8 bins, two for 16 (their rows' shared memory allows no more).
-template <int MODEL, int RB = 0>
-struct TileOcc {
-  static constexpr int value =
-      MODEL == kUniform ? 5
-                        : (MODEL == kEpan ? 5
-                                          : (MODEL == kHist ? (RB == 8 ? 4 : (RB == 16 ? 2 : 3))
-                                                            : (MODEL == kSemi ? 4 : 2)));
-};
-
 // tile height: 8 rows for the uniform and histogram models and the
 // estimator (a 20-member box fits next to the parameter tile, and the
 // histogram's per-bin rows fit), 16 for the Gaussian and, from parameters,
@@ -138,20 +126,6 @@ template <int MODEL>
 struct TileH {
   static constexpr int value = (MODEL == kGauss || MODEL == kEpan) ? TY : 8;
 };
-
-// floats of the parameter tile: the model's tile, or for per-bin-row
-// histogram tiles the smaller one of hist_rows_tile_floats (masses held in
-// it only when they are not counted in registers)
-template <int MODEL, int TYm, bool ROWS>
-__host__ __device__ constexpr long long param_tile_floats(int B, bool masses) {
-  return ROWS ? hist_rows_tile_floats(B, TYm, masses) : tile_floats(MODEL, B, TYm);
-}
-
-// rows of a histogram tile's per-bin tables (hist_r4_rows float4 per halo
-// vertex, rows hist_r4_stride apart), in floats
-__host__ __device__ constexpr int r4_floats(int B, int TYv) {
-  return 4 * hist_r4_rows(B) * hist_r4_stride((TYv + 2) * (TX + 2));
-}
 
 // Shared memory: the parameter tile, then (RB > 0) the per-bin rows,
 // 16-byte aligned.
@@ -313,6 +287,50 @@ static bool launch_tile_tma(const Field &f, int tiles_x, int tiles, cudaStream_t
   tile_kernel_tma<MODEL, SADDLE, TYm, RB><<<tiles, NTHREADS, smem, s>>>(g, tiles_x, map);
   *err = cudaGetLastError();
   return true;
+}
+
+// TMA staging of one field's members with TYm-row tiles at the occupancy
+// of (MODEL, RB): members per box (0: not possible) and the CTA's shared
+// memory bytes, as launch_tile_tma sets them up.
+template <int MODEL, int TYm, int RB>
+static int tma_plan_t(const Field &f, size_t *smem) {
+  if (f.W % 4 != 0 || (reinterpret_cast<uintptr_t>(f.ens) & 15) != 0) return 0;
+  constexpr bool ROWS = RB > 0;
+  const size_t tile_b =
+      (size_t)((param_tile_floats<MODEL, TYm, ROWS>(f.B, false) + 1) & ~1LL) * sizeof(float) + 16;
+  const size_t per_member = (size_t)(TYm + 2) * kBoxW * sizeof(float);
+  const size_t budget = (size_t)227 * 1024 / TileOcc<MODEL, RB>::value - 1024;
+  const int nc = tma_box_members<MODEL, TYm, RB>(f.N, f.B);
+  const size_t r4_b = ROWS ? (size_t)r4_floats(f.B, TYm) * sizeof(float) : 0;
+  if (nc < 1 || tile_b + r4_b > budget) return 0;
+  *smem = std::max((size_t)nc * per_member, r4_b) + tile_b;
+  return nc;
+}
+
+int tma_plan(int model, int TYm, int RB, const Field &f, size_t *smem) {
+  if (model == kUniform && RB == 0) return TYm == 8 ? tma_plan_t<kUniform, 8, 0>(f, smem)
+                                                    : tma_plan_t<kUniform, 16, 0>(f, smem);
+  if (model == kEpan && RB == 0) return TYm == 8 ? tma_plan_t<kEpan, 8, 0>(f, smem)
+                                                 : tma_plan_t<kEpan, 16, 0>(f, smem);
+  if (model == kHist && TYm == 8 && RB == 8 && f.B <= 8 && f.N <= 65535)
+    return tma_plan_t<kHist, 8, 8>(f, smem);
+  if (model == kHist && TYm == 8 && RB == 16 && f.B <= 16 && f.N <= 65535)
+    return tma_plan_t<kHist, 8, 16>(f, smem);
+  return 0;
+}
+
+bool encode_member_map(void *map, const Field &f, int TYm, int nc) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)f.W, (cuuint64_t)f.H, (cuuint64_t)f.N};
+  const cuuint64_t strides[2] = {(cuuint64_t)f.W * sizeof(float),
+                                 (cuuint64_t)f.plane * sizeof(float)};
+  const cuuint32_t box[3] = {(cuuint32_t)kBoxW, (cuuint32_t)(TYm + 2), (cuuint32_t)nc};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(static_cast<CUtensorMap *>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+             const_cast<float *>(f.ens), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <int MODEL, bool FM, bool SADDLE, int TYm, int RB>

@@ -51,6 +51,13 @@ struct Field3 {
 cudaError_t launch_closed3(const Field3 &f, cudaStream_t s, bool *launched);
 // cuTensorMapEncodeTiled from the driver (nullptr if unavailable)
 void *tensor_map_encoder_fn();
+// TMA staging plan of one field for the single-field tile kernels' layout
+// (model, TYm-row tiles, RB: per-bin rows of at most RB bins, 0 none): the
+// members per box, 0 if TMA staging does not apply; *smem = the CTA's
+// dynamic shared memory.  encode_member_map writes the tensor map of the
+// field's members for that box (map: a 64-byte aligned CUtensorMap).
+int tma_plan(int model, int TYm, int RB, const Field &f, size_t *smem);
+bool encode_member_map(void *map, const Field &f, int TYm, int nc);
 
 cudaError_t launch_fit(const Field &f, int model, cudaStream_t s);
 cudaError_t launch_closed(const Field &f, int model, bool from_members, cudaStream_t s);

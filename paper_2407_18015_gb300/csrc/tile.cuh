@@ -35,6 +35,32 @@ __host__ __device__ constexpr long long hist_rows_tile_floats(int B, int TYv, bo
   return masses ? (2 + B > 4 ? 2 + B : 4) * halo : 4 * halo + ROWS_MASS_TABLE;
 }
 
+// resident CTAs per SM each model's register budget is tuned for.  RB > 0:
+// histogram tiles that walk per-bin rows of at most RB bins -- four CTAs
+// per SM for 8 bins, two for 16 (their rows' shared memory allows no more).
+template <int MODEL, int RB = 0>
+struct TileOcc {
+  static constexpr int value =
+      MODEL == kUniform ? 5
+                        : (MODEL == kEpan ? 5
+                                          : (MODEL == kHist ? (RB == 8 ? 4 : (RB == 16 ? 2 : 3))
+                                                            : (MODEL == kSemi ? 4 : 2)));
+};
+
+// floats of the parameter tile: the model's tile, or for per-bin-row
+// histogram tiles the smaller one of hist_rows_tile_floats (masses held in
+// it only when they are not counted in registers)
+template <int MODEL, int TYm, bool ROWS>
+__host__ __device__ constexpr long long param_tile_floats(int B, bool masses) {
+  return ROWS ? hist_rows_tile_floats(B, TYm, masses) : tile_floats(MODEL, B, TYm);
+}
+
+// rows of a histogram tile's per-bin tables (hist_r4_rows float4 per halo
+// vertex, rows hist_r4_stride apart), in floats
+__host__ __device__ constexpr int r4_floats(int B, int TYv) {
+  return 4 * hist_r4_rows(B) * hist_r4_stride((TYv + 2) * 34);
+}
+
 // Number of pieces of the histogram walk of a tile vertex (0 for a vertex
 // that does not walk): the centre's B bins plus every neighbour edge inside
 // the centre's support.
@@ -489,6 +515,9 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
                : "memory");
 }
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ void mbar_init_fence() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
@@ -838,7 +867,8 @@ __device__ __forceinline__ void integrate_tile(const Field &f, int ty0, int tx0,
 // One tile of TYv x 32 vertices: phase 1 stages the parameters of the tile
 // and its one-vertex halo ((TYv + 2) x 34) in shared memory -- fitted from the
 // members or loaded -- and phase 2 (integrate_tile) integrates every vertex
-// of the tile.  SADDLE selects the saddle probability (Eq. saddleProb)
+// of the tile; returns false if the staging gave up (a bounded wait
+// expired; the tile is then marked).  SADDLE selects the saddle probability (Eq. saddleProb)
 // instead of the minimum / maximum: a separate instance, so neither pays for
 // the other.  TMA: the members are staged through the tensor map tmap into
 // `box`, with the mbarrier `bar` (FROM_MEMBERS only).  RB > 0 (histograms
@@ -848,7 +878,7 @@ __device__ __forceinline__ void integrate_tile(const Field &f, int ty0, int tx0,
 // one of the two walks.
 template <int MODEL, bool FROM_MEMBERS, int TYv, bool SADDLE = false, bool TMA = false,
           int RB = 0>
-__device__ __forceinline__ void process_tile(const Field &f, int ty0, int tx0, float *sm,
+__device__ __forceinline__ bool process_tile(const Field &f, int ty0, int tx0, float *sm,
                                              const CUtensorMap *tmap = nullptr,
                                              float *box = nullptr, uint64_t *bar = nullptr,
                                              float4 *R4 = nullptr) {
@@ -900,10 +930,11 @@ __device__ __forceinline__ void process_tile(const Field &f, int ty0, int tx0, f
   __syncthreads();
   if (!staged) {  // a bounded wait gave up (uniform over the CTA): NaN + flag
     mark_tile_timeout<TY, SADDLE>(f, ty0, tx0);
-    return;
+    return false;
   }
   integrate_tile<MODEL, TY, SADDLE, (FROM_MEMBERS && TMA) || (!FROM_MEMBERS && RB > 0),
                  (RB > 0)>(f, ty0, tx0, sm, R4);
+  return true;
 }
 
 // Phase 2 of a tile whose parameters (and, if TABLES_BUILT, histogram tail

@@ -381,12 +381,12 @@ def ucp_batch_add(batch, ens, desc, cptypes, out_min, out_max):
     _check(rc, "ucp_batch_add")
 
 
-def ucp_batch_tune(batch, stream=None):
-    _check(lib().ucp_batch_tune(batch, _stream(stream)), "ucp_batch_tune")
+def ucp_batch_tune(batch, stream=None, ctx=None):
+    _check(lib().ucp_batch_tune(batch, _stream(stream)), "ucp_batch_tune", ctx)
 
 
-def ucp_batch_run(batch, stream=None):
-    _check(lib().ucp_batch_run(batch, _stream(stream)), "ucp_batch_run")
+def ucp_batch_run(batch, stream=None, ctx=None):
+    _check(lib().ucp_batch_run(batch, _stream(stream)), "ucp_batch_run", ctx)
 
 
 def ucp_batch_destroy(batch):
@@ -526,10 +526,10 @@ class Batch:
         self._keep.append((ens, out_min, out_max))
 
     def tune(self, stream=None):
-        ucp_batch_tune(self.handle, stream)
+        ucp_batch_tune(self.handle, stream, self.ctx.handle)
 
     def run(self, stream=None):
-        ucp_batch_run(self.handle, stream)
+        ucp_batch_run(self.handle, stream, self.ctx.handle)
 
     def close(self):
         if self.handle is not None:
