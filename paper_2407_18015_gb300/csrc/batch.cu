@@ -117,9 +117,11 @@ struct alignas(64) TmaItem {
 struct TmaClass {
   int model, ty, rb;
 };
-constexpr int kNumTmaCls = 6;
-constexpr TmaClass kTmaCls[kNumTmaCls] = {{kUniform, 8, 0}, {kUniform, 16, 0}, {kEpan, 8, 0},
-                                          {kEpan, 16, 0},    {kHist, 8, 8},     {kHist, 8, 16}};
+// classes 0..5 stage members by the tensor memory accelerator, 6..11 (the
+// same kinds) by asynchronous copies (members it cannot address)
+constexpr int kNumKinds = 6, kNumTmaCls = 2 * kNumKinds;
+constexpr TmaClass kTmaCls[kNumKinds] = {{kUniform, 8, 0}, {kUniform, 16, 0}, {kEpan, 8, 0},
+                                         {kEpan, 16, 0},    {kHist, 8, 8},     {kHist, 8, 16}};
 
 // resident CTAs per SM of a class kernel: the single-field kernel's, at
 // most four (the persistent loop's own registers do not fit beside the
@@ -129,7 +131,7 @@ struct BatchOcc {
   static constexpr int value = TileOcc<MODEL, RB>::value > 4 ? 4 : TileOcc<MODEL, RB>::value;
 };
 
-template <int MODEL, int TYm, int RB>
+template <int MODEL, int TYm, int RB, bool ASYNC>
 __global__ void __launch_bounds__(NTHREADS, (BatchOcc<MODEL, RB>::value))
     batch_tma_kernel(const TmaItem *__restrict__ items, int nitems, long long total,
                      unsigned long long *__restrict__ counter) {
@@ -172,7 +174,7 @@ __global__ void __launch_bounds__(NTHREADS, (BatchOcc<MODEL, RB>::value))
     float *sm = smem + max(box_floats, r4);
     const long long tile_f = param_tile_floats<MODEL, TYm, ROWS>(f.B, false);
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + ((tile_f + 1) & ~1LL));
-    const bool ok = process_tile<MODEL, true, TYm, false, true, RB>(
+    const bool ok = process_tile<MODEL, true, TYm, false, true, RB, ASYNC>(
         f, ty0, tx0, sm, &it.tmap, smem, bar, ROWS ? reinterpret_cast<float4 *>(smem) : nullptr);
     __syncthreads();
     // a copy that gave up may still land: this CTA takes no further tile
@@ -269,6 +271,12 @@ struct ucp_batch {
   long long tma_total[kNumTmaCls] = {};
   size_t tma_smem[kNumTmaCls] = {};
   int tma_grid[kNumTmaCls] = {};
+  // the kernels of one run go to their own streams, forked from and joined
+  // back into the caller's, so that one kernel's last tiles overlap the next
+  // one's first (capturable: the graph gets parallel branches)
+  cudaStream_t lane[1 + kNumTmaCls] = {};
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[1 + kNumTmaCls] = {};
 };
 
 namespace {
@@ -283,30 +291,39 @@ constexpr size_t kSmemPerBlock = 227 * 1024;
 // the class kernel of class c
 const void *tma_kernel(int c) {
   switch (c) {
-    case 0: return reinterpret_cast<const void *>(batch_tma_kernel<kUniform, 8, 0>);
-    case 1: return reinterpret_cast<const void *>(batch_tma_kernel<kUniform, 16, 0>);
-    case 2: return reinterpret_cast<const void *>(batch_tma_kernel<kEpan, 8, 0>);
-    case 3: return reinterpret_cast<const void *>(batch_tma_kernel<kEpan, 16, 0>);
-    case 4: return reinterpret_cast<const void *>(batch_tma_kernel<kHist, 8, 8>);
-    default: return reinterpret_cast<const void *>(batch_tma_kernel<kHist, 8, 16>);
+    case 0: return reinterpret_cast<const void *>(batch_tma_kernel<kUniform, 8, 0, false>);
+    case 1: return reinterpret_cast<const void *>(batch_tma_kernel<kUniform, 16, 0, false>);
+    case 2: return reinterpret_cast<const void *>(batch_tma_kernel<kEpan, 8, 0, false>);
+    case 3: return reinterpret_cast<const void *>(batch_tma_kernel<kEpan, 16, 0, false>);
+    case 4: return reinterpret_cast<const void *>(batch_tma_kernel<kHist, 8, 8, false>);
+    case 5: return reinterpret_cast<const void *>(batch_tma_kernel<kHist, 8, 16, false>);
+    case 6: return reinterpret_cast<const void *>(batch_tma_kernel<kUniform, 8, 0, true>);
+    case 7: return reinterpret_cast<const void *>(batch_tma_kernel<kUniform, 16, 0, true>);
+    case 8: return reinterpret_cast<const void *>(batch_tma_kernel<kEpan, 8, 0, true>);
+    case 9: return reinterpret_cast<const void *>(batch_tma_kernel<kEpan, 16, 0, true>);
+    case 10: return reinterpret_cast<const void *>(batch_tma_kernel<kHist, 8, 8, true>);
+    default: return reinterpret_cast<const void *>(batch_tma_kernel<kHist, 8, 16, true>);
   }
 }
 
 // the TMA class of an item at the tuned tile heights, -1 for none
 int tma_class_of(const BatchItem &it, const int *th) {
+  const int async = it.f.vec4 ? 0 : kNumKinds;
   if (it.model == kUniform || it.model == kEpan) {
     const int ty = kTileHeights[th[it.model]];
     if (ty > 16) return -1;
-    return (it.model == kUniform ? 0 : 2) + (ty == 16 ? 1 : 0);
+    return (it.model == kUniform ? 0 : 2) + (ty == 16 ? 1 : 0) + async;
   }
-  if (it.f.B <= 8) return 4;
-  return it.f.B <= 16 ? 5 : -1;
+  if (it.f.B <= 8) return 4 + async;
+  return it.f.B <= 16 ? 5 + async : -1;
 }
 
 // order, tile and upload a list (synchronous: not inside a stream capture).
-// Fields whose members the tensor memory accelerator can stage go to their
-// class (tile heights of uniform and Epanechnikov as tuned, 8 or 16; 8 for
-// histograms of up to 16 bins), the rest to the generic list; a generic
+// Fields whose members fit a box staging go to their class (tile heights of
+// uniform and Epanechnikov as tuned, 8 or 16; 8 for histograms of up to 16
+// bins) -- with a tensor map when the tensor memory accelerator can address
+// them (f.vec4), else with an empty one, staged by asynchronous copies --
+// the rest to the generic list; a generic
 // item whose tile at the requested height would not fit in shared memory
 // (histograms with many bins) takes the next lower height.
 int finalize(ucp_batch *b, std::vector<BatchItem> all, const int *th) {
@@ -316,11 +333,12 @@ int finalize(ucp_batch *b, std::vector<BatchItem> all, const int *th) {
   for (const auto &it : all) {
     const int c = tma_class_of(it, th);
     size_t sm = 0;
-    const int nc = c < 0 ? 0 : tma_plan(kTmaCls[c].model, kTmaCls[c].ty, kTmaCls[c].rb, it.f, &sm);
+    const TmaClass *k = c < 0 ? nullptr : &kTmaCls[c % kNumKinds];
+    const int nc = k ? tma_plan(k->model, k->ty, k->rb, it.f, &sm) : 0;
     TmaItem ti{};
     ti.f = it.f;
     ti.f.tma_nc = nc;
-    if (nc > 0 && encode_member_map(&ti.tmap, ti.f, kTmaCls[c].ty, nc)) {
+    if (nc > 0 && (!ti.f.vec4 || encode_member_map(&ti.tmap, ti.f, k->ty, nc))) {
       ti.tiles_x = (it.f.W + 31) / 32;
       cls[c].push_back(ti);
       csm[c] = std::max(csm[c], sm);
@@ -330,7 +348,7 @@ int finalize(ucp_batch *b, std::vector<BatchItem> all, const int *th) {
   }
   std::vector<TmaItem> flat;
   for (int c = 0; c < kNumTmaCls; ++c) {
-    const TmaClass &k = kTmaCls[c];
+    const TmaClass &k = kTmaCls[c % kNumKinds];
     std::stable_sort(cls[c].begin(), cls[c].end(), [&k](const TmaItem &x, const TmaItem &y) {
       return vertex_cost(k.model, x.f.N, x.f.B) > vertex_cost(k.model, y.f.N, y.f.B);
     });
@@ -414,33 +432,61 @@ int finalize(ucp_batch *b, std::vector<BatchItem> all, const int *th) {
   return UCP_OK;
 }
 
-int launch(ucp_batch *b, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(b->d_counter, 0, (1 + kNumTmaCls) * sizeof(unsigned long long), s);
-  if (e != cudaSuccess) return ucp_set_error(b->ctx, e);
-  // the most expensive classes first: histograms, then Epanechnikov
-  for (int c = kNumTmaCls - 1; c >= 0 && e == cudaSuccess; --c) {
-    if (b->tma_total[c] == 0) continue;
-    const int g = (int)std::min<long long>(b->tma_total[c], b->tma_grid[c]);
-    const TmaItem *items = b->d_tma + b->tma_off[c];
-    const int n = b->tma_n[c];
-    const long long tot = b->tma_total[c];
-    unsigned long long *ctr = b->d_counter + 1 + c;
-    const size_t sm = b->tma_smem[c];
-    switch (c) {
-      case 0: batch_tma_kernel<kUniform, 8, 0><<<g, NTHREADS, sm, s>>>(items, n, tot, ctr); break;
-      case 1: batch_tma_kernel<kUniform, 16, 0><<<g, NTHREADS, sm, s>>>(items, n, tot, ctr); break;
-      case 2: batch_tma_kernel<kEpan, 8, 0><<<g, NTHREADS, sm, s>>>(items, n, tot, ctr); break;
-      case 3: batch_tma_kernel<kEpan, 16, 0><<<g, NTHREADS, sm, s>>>(items, n, tot, ctr); break;
-      case 4: batch_tma_kernel<kHist, 8, 8><<<g, NTHREADS, sm, s>>>(items, n, tot, ctr); break;
-      default: batch_tma_kernel<kHist, 8, 16><<<g, NTHREADS, sm, s>>>(items, n, tot, ctr); break;
-    }
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess && b->total > 0) {
+// launch one class kernel (c < kNumTmaCls) or the generic kernel (c ==
+// kNumTmaCls) on stream s
+cudaError_t launch_one(ucp_batch *b, int c, cudaStream_t s) {
+  if (c == kNumTmaCls) {
     const long long want = std::min<long long>(b->total, b->grid);
     batch_kernel<<<(int)want, NTHREADS, b->smem, s>>>(b->d_items, b->nitems, b->total,
                                                       b->d_counter);
-    e = cudaGetLastError();
+    return cudaGetLastError();
+  }
+  const int g = (int)std::min<long long>(b->tma_total[c], b->tma_grid[c]);
+  const TmaItem *items = b->d_tma + b->tma_off[c];
+  const int n = b->tma_n[c];
+  const long long tot = b->tma_total[c];
+  unsigned long long *ctr = b->d_counter + 1 + c;
+  const size_t sm = b->tma_smem[c];
+  switch (c) {
+#define UCP_CLS(M, T, R, A) \
+  batch_tma_kernel<M, T, R, A><<<g, NTHREADS, sm, s>>>(items, n, tot, ctr); \
+  break
+    case 0: UCP_CLS(kUniform, 8, 0, false);
+    case 1: UCP_CLS(kUniform, 16, 0, false);
+    case 2: UCP_CLS(kEpan, 8, 0, false);
+    case 3: UCP_CLS(kEpan, 16, 0, false);
+    case 4: UCP_CLS(kHist, 8, 8, false);
+    case 5: UCP_CLS(kHist, 8, 16, false);
+    case 6: UCP_CLS(kUniform, 8, 0, true);
+    case 7: UCP_CLS(kUniform, 16, 0, true);
+    case 8: UCP_CLS(kEpan, 8, 0, true);
+    case 9: UCP_CLS(kEpan, 16, 0, true);
+    case 10: UCP_CLS(kHist, 8, 8, true);
+    default: UCP_CLS(kHist, 8, 16, true);
+#undef UCP_CLS
+  }
+  return cudaGetLastError();
+}
+
+int launch(ucp_batch *b, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(b->d_counter, 0, (1 + kNumTmaCls) * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return ucp_set_error(b->ctx, e);
+  // the most expensive classes first: histograms, then Epanechnikov, then
+  // uniform, then the generic list
+  int order[1 + kNumTmaCls], n = 0;
+  for (int c = kNumKinds - 1; c >= 0; --c)
+    for (int a = 0; a < 2; ++a)
+      if (b->tma_total[c + a * kNumKinds] > 0) order[n++] = c + a * kNumKinds;
+  if (b->total > 0) order[n++] = kNumTmaCls;
+  if (n == 1) return ucp_set_error(b->ctx, launch_one(b, order[0], s));
+  if (n == 0) return UCP_OK;
+  e = cudaEventRecord(b->fork_ev, s);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    cudaStream_t l = b->lane[i];
+    e = cudaStreamWaitEvent(l, b->fork_ev, 0);
+    if (e == cudaSuccess) e = launch_one(b, order[i], l);
+    if (e == cudaSuccess) e = cudaEventRecord(b->join_ev[i], l);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->join_ev[i], 0);
   }
   return ucp_set_error(b->ctx, e);
 }
@@ -470,10 +516,16 @@ int ucp_batch_create(ucp_ctx *ctx, ucp_batch **batch) {
   cudaGetDevice(&prev);
   cudaSetDevice(ctx->device);
   cudaError_t e = cudaMalloc(&b->d_counter, (1 + kNumTmaCls) * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
+  for (int i = 0; i <= kNumTmaCls && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&b->lane[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join_ev[i], cudaEventDisableTiming);
+  }
   if (prev >= 0) cudaSetDevice(prev);
   if (e != cudaSuccess) {
-    delete b;
-    return ucp_set_error(ctx, e);
+    ucp_set_error(ctx, e);
+    ucp_batch_destroy(b);
+    return UCP_ERR_CUDA;
   }
   *batch = b;
   return UCP_OK;
@@ -595,6 +647,11 @@ int ucp_batch_destroy(ucp_batch *batch) {
   if (batch->d_items) cudaFree(batch->d_items);
   if (batch->d_tma) cudaFree(batch->d_tma);
   if (batch->d_counter) cudaFree(batch->d_counter);
+  for (int i = 0; i <= kNumTmaCls; ++i) {
+    if (batch->lane[i]) cudaStreamDestroy(batch->lane[i]);
+    if (batch->join_ev[i]) cudaEventDestroy(batch->join_ev[i]);
+  }
+  if (batch->fork_ev) cudaEventDestroy(batch->fork_ev);
   if (prev >= 0) cudaSetDevice(prev);
   delete batch;
   return UCP_OK;

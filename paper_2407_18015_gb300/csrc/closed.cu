@@ -14,6 +14,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "device.cuh"
 #include "launch.h"
@@ -145,12 +146,13 @@ __global__ void __launch_bounds__(NTHREADS, (TileOcc<MODEL, RB>::value))
       f, f.y0 + (tile / tiles_x) * TYm, (tile % tiles_x) * TX, sm, nullptr, nullptr, nullptr, R4);
 }
 
-// The same with the members staged by the tensor memory accelerator: shared
-// memory holds the member box (nc x (TYm + 2) x 40 floats, 128-byte
-// aligned) -- for per-bin-row histograms the same room then takes the rows,
-// once the box is no longer read -- then the parameter tile, then the
-// mbarrier.
-template <int MODEL, bool SADDLE, int TYm, int RB>
+// The same with the members staged in a box: shared memory holds the
+// member box (nc x (TYm + 2) x 40 floats, 128-byte aligned), filled by the
+// tensor memory accelerator or (ASYNC, members it cannot address) by
+// asynchronous copies -- for per-bin-row histograms the same room then
+// takes the rows, once the box is no longer read -- then the parameter
+// tile, then the mbarrier.
+template <int MODEL, bool SADDLE, int TYm, int RB, bool ASYNC>
 __global__ void __launch_bounds__(NTHREADS, (TileOcc<MODEL, RB>::value))
     tile_kernel_tma(Field f, int tiles_x, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(128) float smem[];
@@ -161,7 +163,7 @@ __global__ void __launch_bounds__(NTHREADS, (TileOcc<MODEL, RB>::value))
   float *sm = smem + max(box_floats, r4);
   const long long tile_f = param_tile_floats<MODEL, TYm, ROWS>(f.B, false);
   uint64_t *bar = reinterpret_cast<uint64_t *>(sm + ((tile_f + 1) & ~1LL));
-  process_tile<MODEL, true, TYm, SADDLE, true, RB>(
+  process_tile<MODEL, true, TYm, SADDLE, true, RB, ASYNC>(
       f, f.y0 + (tile / tiles_x) * TYm, (tile % tiles_x) * TX, sm, &tmap, smem, bar,
       ROWS ? reinterpret_cast<float4 *>(smem) : nullptr);
 }
@@ -235,15 +237,17 @@ static int tma_box_members(int N, int B) {
   return (int)std::min<size_t>(nc, (size_t)std::min(N, 256));
 }
 
-// Launch with TMA member staging when the members allow it (W % 4 == 0, a
-// 16-byte aligned base) and a box of at least one member fits next to the
-// parameter tile at the model's occupancy; returns false to fall back.
+// Launch with member staging into a shared-memory box when a box of at
+// least one member fits next to the parameter tile at the model's
+// occupancy; returns false to fall back.  The box is filled by the tensor
+// memory accelerator when the members allow it (W % 4 == 0, a 16-byte
+// aligned base: f.vec4), else by 4-byte asynchronous copies (the tensor map
+// is then left empty and never used).
 template <int MODEL, bool SADDLE, int TYm, int RB>
 static bool launch_tile_tma(const Field &f, int tiles_x, int tiles, cudaStream_t s,
                             cudaError_t *err) {
-  if (f.W % 4 != 0 || (reinterpret_cast<uintptr_t>(f.ens) & 15) != 0) return false;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-  if (!enc) return false;
+  if (f.vec4 && !enc) return false;
   // histogram per-bin rows, in the room of the member box
   constexpr bool ROWS = RB > 0;
   const size_t tile_b =
@@ -255,15 +259,18 @@ static bool launch_tile_tma(const Field &f, int tiles_x, int tiles, cudaStream_t
   const size_t r4_b = ROWS ? (size_t)r4_floats(f.B, TYm) * sizeof(float) : 0;
   if (tile_b + r4_b > budget) return false;
   CUtensorMap map;
-  const cuuint64_t dims[3] = {(cuuint64_t)f.W, (cuuint64_t)f.H, (cuuint64_t)f.N};
-  const cuuint64_t strides[2] = {(cuuint64_t)f.W * sizeof(float),
-                                 (cuuint64_t)f.plane * sizeof(float)};
-  const cuuint32_t box[3] = {(cuuint32_t)kBoxW, (cuuint32_t)(TYm + 2), (cuuint32_t)nc};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(f.ens), dims, strides, box,
-          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-    return false;
+  memset(&map, 0, sizeof(map));
+  if (f.vec4) {
+    const cuuint64_t dims[3] = {(cuuint64_t)f.W, (cuuint64_t)f.H, (cuuint64_t)f.N};
+    const cuuint64_t strides[2] = {(cuuint64_t)f.W * sizeof(float),
+                                   (cuuint64_t)f.plane * sizeof(float)};
+    const cuuint32_t box[3] = {(cuuint32_t)kBoxW, (cuuint32_t)(TYm + 2), (cuuint32_t)nc};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(f.ens), dims, strides,
+            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
   // per device: the attribute is set once (several host threads may race to
   // set it; setting it twice is harmless, the flag itself is atomic)
   static std::atomic<bool> attr_set[128] = {};
@@ -273,9 +280,12 @@ static bool launch_tile_tma(const Field &f, int tiles_x, int tiles, cudaStream_t
     return false;
   }
   if (!attr_set[dev].load(std::memory_order_acquire)) {
-    if (cudaFuncSetAttribute(tile_kernel_tma<MODEL, SADDLE, TYm, RB>,
+    if (cudaFuncSetAttribute(tile_kernel_tma<MODEL, SADDLE, TYm, RB, false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
-        cudaSuccess) {
+            cudaSuccess ||
+        cudaFuncSetAttribute(tile_kernel_tma<MODEL, SADDLE, TYm, RB, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+            cudaSuccess) {
       cudaGetLastError();
       return false;
     }
@@ -284,17 +294,20 @@ static bool launch_tile_tma(const Field &f, int tiles_x, int tiles, cudaStream_t
   Field g = f;
   g.tma_nc = nc;
   const size_t smem = std::max((size_t)nc * per_member, r4_b) + tile_b;
-  tile_kernel_tma<MODEL, SADDLE, TYm, RB><<<tiles, NTHREADS, smem, s>>>(g, tiles_x, map);
+  if (f.vec4)
+    tile_kernel_tma<MODEL, SADDLE, TYm, RB, false><<<tiles, NTHREADS, smem, s>>>(g, tiles_x, map);
+  else
+    tile_kernel_tma<MODEL, SADDLE, TYm, RB, true><<<tiles, NTHREADS, smem, s>>>(g, tiles_x, map);
   *err = cudaGetLastError();
   return true;
 }
 
-// TMA staging of one field's members with TYm-row tiles at the occupancy
+// Box staging of one field's members with TYm-row tiles at the occupancy
 // of (MODEL, RB): members per box (0: not possible) and the CTA's shared
-// memory bytes, as launch_tile_tma sets them up.
+// memory bytes, as launch_tile_tma sets them up (by the tensor memory
+// accelerator or, for members it cannot address, by asynchronous copies).
 template <int MODEL, int TYm, int RB>
 static int tma_plan_t(const Field &f, size_t *smem) {
-  if (f.W % 4 != 0 || (reinterpret_cast<uintptr_t>(f.ens) & 15) != 0) return 0;
   constexpr bool ROWS = RB > 0;
   const size_t tile_b =
       (size_t)((param_tile_floats<MODEL, TYm, ROWS>(f.B, false) + 1) & ~1LL) * sizeof(float) + 16;
@@ -392,17 +405,14 @@ static cudaError_t launch_tile(const Field &f, cudaStream_t s) {
     // Per-bin rows on 8-row tiles: up to 8 bins at four CTAs per SM, up to
     // 16 at two (members counted in registers: at most 65535 of them);
     // otherwise the segment walker on 16-row tiles, where the smaller halo
-    // wins.  The per-thread staging (members not TMA aligned) holds the
-    // masses in the tile; from parameters the rows are built from registers.
+    // wins.  From members the box staging (tensor memory accelerator or
+    // asynchronous copies) applies to every field; from parameters the rows
+    // are built from registers.
     const bool counts_ok = !FM || f.N <= 65535;
-    // members the tensor memory accelerator cannot stage are staged per
-    // thread with their masses in the tile: too much shared memory beside
-    // 16-bin rows (one CTA per SM), so those take the segment walker
-    const bool tma_ok = f.W % 4 == 0 && (reinterpret_cast<uintptr_t>(f.ens) & 15) == 0;
     if (counts_ok && f.B <= 8 &&
         hist_rows_bytes(f.B, 8) <= (size_t)227 * 1024 / TileOcc<kHist, 8>::value - 1024)
       return launch_tile_h<MODEL, FM, SADDLE, 8, 8>(f, s);
-    if (counts_ok && f.B <= 16 && (!FM || tma_ok) &&
+    if (counts_ok && f.B <= 16 &&
         hist_rows_bytes(f.B, 8) <= (size_t)227 * 1024 / TileOcc<kHist, 16>::value - 1024)
       return launch_tile_h<MODEL, FM, SADDLE, 8, 16>(f, s);
     return launch_tile_h<MODEL, FM, SADDLE, TY, 0>(f, s);

@@ -537,6 +537,17 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
 }
+// one 16-byte asynchronous copy global -> shared (both addresses 16-byte
+// aligned; no register round trip, not cached in L1), and the wait for all
+// of this thread's copies in flight
+__device__ __forceinline__ void cp_async16(void *dst, uintptr_t src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 // wait for the completion of phase `parity`; gives up after a bounded number
 // of polls (each poll itself returns after a bounded time)
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
@@ -562,7 +573,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
 // ROWS: histogram per-bin rows into R4 in place of the tail tables (R4 may
 // overlap the box: the rows are written after the barrier that ends the last
 // read of the box).
-template <int MODEL, int TYv, int RB>
+template <int MODEL, int TYv, int RB, bool ASYNC>
 __device__ __forceinline__ bool stage_members_tma(const Field &f, float *sm, float *box,
                                                   uint64_t *bar, const CUtensorMap *tmap,
                                                   int ty0, int tx0, float4 *R4) {
@@ -572,7 +583,13 @@ __device__ __forceinline__ bool stage_members_tma(const Field &f, float *sm, flo
   const int N = f.N, nc = f.tma_nc;
   const unsigned box_bytes = (unsigned)(PLANE * nc * sizeof(float));
   const int ylim = min(f.H, f.y1 + 1);
-  int off[PER], lv[PER];
+  // box filled by the tensor memory accelerator, or (ASYNC) by asynchronous
+  // copies with the element shifts described at `load` below (eb, pl, w4
+  // all 0 for the accelerator: no shift)
+  constexpr bool tma = !ASYNC;
+  const int eb = ASYNC ? (int)(reinterpret_cast<uintptr_t>(f.ens) >> 2) & 3 : 0;
+  const int pl = ASYNC ? (int)(f.plane & 3) : 0, w4 = ASYNC ? f.W & 3 : 0;
+  int off[PER], lv[PER], rq[PER];
   bool in[PER];
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
@@ -582,7 +599,10 @@ __device__ __forceinline__ bool stage_members_tma(const Field &f, float *sm, flo
     lv[p] = l;
     in[p] = l < HALO && gy >= 0 && gy < ylim && gx >= 0 && gx < f.W;
     off[p] = r * kBoxW + c + 3;
+    rq[p] = ((gy & 3) * w4) & 3;
   }
+  // the shift of member k0 (the box's first) at owned vertex p
+  auto shift0 = [&](int p, int k0) { return (eb + (k0 & 3) * pl + rq[p]) & 3; };
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     mbar_init_fence();
@@ -602,7 +622,58 @@ __device__ __forceinline__ bool stage_members_tma(const Field &f, float *sm, flo
   // other CTAs.  Once the phase is complete every thread tests it once
   // more (it returns at once), so each thread acquires the copied data
   // itself.
+  //
+  // Members the tensor memory accelerator cannot address (W not a multiple
+  // of 4, or a base that is not 16-byte aligned: f.vec4 false, ASYNC) are copied
+  // into the same box by 16-byte asynchronous copies of the aligned blocks
+  // that hold each (member, row) segment: the element of column c (x =
+  // tx0 - 4 + c) then lands at c + d, d = (its address / 4) mod 4, at most
+  // 3, so the columns the staged vertices read (3 .. 36) stay inside the
+  // 40-float row.  Five threads share a segment, two blocks each; only the
+  // blocks that hold a column a staged in-grid vertex reads are copied, so
+  // every block read holds an element of the members (no read leaves the
+  // allocation).  d = (eb + m pl + gy w4) mod 4 for member m and row gy (eb
+  // the base's offset in floats mod 4, pl = H W mod 4, w4 = W mod 4): the
+  // readers add it, per row, and per member when pl != 0.
   auto load = [&](int k0) -> bool {
+    if constexpr (ASYNC) {
+      constexpr int SLOTS = NTHREADS / 5, DM = SLOTS / HY, DR = SLOTS % HY;
+      const int nseg = min(nc, N - k0) * HY;
+      if (threadIdx.x < SLOTS * 5) {
+        const int q = threadIdx.x % 5;
+        int sg = threadIdx.x / 5;
+        const int m = sg / HY;
+        int r = sg - m * HY;
+        // smem columns (before the shift d) that staged vertices read
+        const int lo0 = max(tx0 - 1, 0) - tx0 + 4, hi0 = min(tx0 + 33, f.W) - tx0 + 4;
+        const uintptr_t rstep = (uintptr_t)f.W * 4u, pstep = (uintptr_t)f.plane * 4u;
+        uintptr_t a = reinterpret_cast<uintptr_t>(f.ens) +
+                      (uintptr_t)(((long long)(k0 + m) * f.plane +
+                                   (long long)(ty0 - 1 + r) * f.W + (tx0 - 4)) * 4);
+        float *dst = box + m * PLANE + r * kBoxW + 8 * q;
+        for (; sg < nseg; sg += SLOTS) {
+          const int gy = ty0 - 1 + r;
+          if ((unsigned)gy < (unsigned)ylim) {
+            const int d = (int)(a >> 2) & 3;
+            const int lo = lo0 + d, hi = hi0 + d, j = 8 * q;
+            const uintptr_t cb = (a & ~(uintptr_t)15) + 32u * q;
+            if (j + 4 > lo && j < hi) cp_async16(dst, cb);
+            if (j + 8 > lo && j + 4 < hi) cp_async16(dst + 4, cb + 16);
+          }
+          r += DR;
+          a += DM * pstep + DR * rstep;
+          dst += DM * PLANE + DR * kBoxW;
+          if (r >= HY) {
+            r -= HY;
+            a += pstep - HY * rstep;
+            dst += PLANE - HY * kBoxW;
+          }
+        }
+      }
+      cp_async_wait_all();
+      __syncthreads();
+      return true;
+    }
     if (threadIdx.x == 0) {
       proxy_async_fence();
       mbar_expect_tx(bar, box_bytes);
@@ -628,13 +699,13 @@ __device__ __forceinline__ bool stage_members_tma(const Field &f, float *sm, flo
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
       if (!in[p]) continue;
-      const float *col = box + off[p];
+      const int sh = shift0(p, k0);
+      const float *col = box + off[p] + sh;
       if (k0 == 0) {
         x0[p] = mn[p] = mx[p] = col[0];
         nf[p] = false;
       }
-      for (int k = 0; k < kn; ++k) {
-        const float v = col[k * PLANE];
+      auto add = [&](float v) {
         nf[p] |= !isfinite(v);
         mn[p] = fminf(mn[p], v);
         mx[p] = fmaxf(mx[p], v);
@@ -643,6 +714,11 @@ __device__ __forceinline__ bool stage_members_tma(const Field &f, float *sm, flo
           s1[p].add(d);
           s2[p].add(d * d);
         }
+      };
+      if (pl == 0) {
+        for (int k = 0; k < kn; ++k) add(col[k * PLANE]);
+      } else {
+        for (int k = 0; k < kn; ++k) add(col[k * PLANE + (((sh + k * pl) & 3) - sh)]);
       }
     }
     __syncthreads();
@@ -716,26 +792,35 @@ __device__ __forceinline__ bool stage_members_tma(const Field &f, float *sm, flo
 #pragma unroll
         for (int p = 0; p < PER; ++p) {
           if (!bin[p]) continue;
-          const float *col = box + off[p];
-          if (!wide) {
+          const int sh = shift0(p, k0);
+          const float *col = box + off[p] + sh;
+          auto count8 = [&](float v) {
+            const int j = hist_bin_nonneg(v, mn[p], sc[p], B);
+            const unsigned long long inc = 1ull << ((j & 7) << 3);
+            if constexpr (NW8 == 1) {
+              cw[p][0] += inc;
+            } else {
+#pragma unroll
+              for (int w = 0; w < NW8; ++w) cw[p][w] += (j >> 3) == w ? inc : 0ull;
+            }
+          };
+          auto count16 = [&](float v) {
+            const int j = hist_bin_nonneg(v, mn[p], sc[p], B);
+            const unsigned long long inc = 1ull << ((j & 3) << 4);
+#pragma unroll
+            for (int w = 0; w < NW16; ++w) cw[p][w] += (j >> 2) == w ? inc : 0ull;
+          };
+          if (pl != 0) {
+            for (int k = 0; k < kn; ++k) {
+              const float v = col[k * PLANE + (((sh + k * pl) & 3) - sh)];
+              if (!wide) count8(v);
+              else count16(v);
+            }
+          } else if (!wide) {
 #pragma unroll 4
-            for (int k = 0; k < kn; ++k) {
-              const int j = hist_bin_nonneg(col[k * PLANE], mn[p], sc[p], B);
-              const unsigned long long inc = 1ull << ((j & 7) << 3);
-              if constexpr (NW8 == 1) {
-                cw[p][0] += inc;
-              } else {
-#pragma unroll
-                for (int w = 0; w < NW8; ++w) cw[p][w] += (j >> 3) == w ? inc : 0ull;
-              }
-            }
+            for (int k = 0; k < kn; ++k) count8(col[k * PLANE]);
           } else {
-            for (int k = 0; k < kn; ++k) {
-              const int j = hist_bin_nonneg(col[k * PLANE], mn[p], sc[p], B);
-              const unsigned long long inc = 1ull << ((j & 3) << 4);
-#pragma unroll
-              for (int w = 0; w < NW16; ++w) cw[p][w] += (j >> 2) == w ? inc : 0ull;
-            }
+            for (int k = 0; k < kn; ++k) count16(col[k * PLANE]);
           }
         }
       }
@@ -785,10 +870,12 @@ __device__ __forceinline__ bool stage_members_tma(const Field &f, float *sm, flo
 #pragma unroll
         for (int p = 0; p < PER; ++p) {
           if (!bin[p]) continue;
-          const float *col = box + off[p];
+          const int sh = shift0(p, k0);
+          const float *col = box + off[p] + sh;
           float *w0 = sm + 2 * HALO + lv[p];
           for (int k = 0; k < kn; ++k)
-            w0[hist_bin(col[k * PLANE], mn[p], sc[p], B) * HALO] += 1.f;
+            w0[hist_bin(col[k * PLANE + (((sh + k * pl) & 3) - sh)], mn[p], sc[p], B) * HALO] +=
+                1.f;
         }
       }
       __syncthreads();
@@ -871,13 +958,15 @@ __device__ __forceinline__ void integrate_tile(const Field &f, int ty0, int tx0,
 // expired; the tile is then marked).  SADDLE selects the saddle probability (Eq. saddleProb)
 // instead of the minimum / maximum: a separate instance, so neither pays for
 // the other.  TMA: the members are staged through the tensor map tmap into
-// `box`, with the mbarrier `bar` (FROM_MEMBERS only).  RB > 0 (histograms
+// `box`, with the mbarrier `bar` (FROM_MEMBERS only); with ASYNC as well,
+// by asynchronous copies into the same box instead (members the tensor
+// memory accelerator cannot address; tmap unused).  RB > 0 (histograms
 // of at most RB bins): the walk runs over per-bin rows in R4 (hist_r4_rows
 // rows of hist_r4_stride float4, 16-byte aligned; it may overlap `box`)
 // instead of the segment walker's tail table; each kernel instance carries
 // one of the two walks.
 template <int MODEL, bool FROM_MEMBERS, int TYv, bool SADDLE = false, bool TMA = false,
-          int RB = 0>
+          int RB = 0, bool ASYNC = false>
 __device__ __forceinline__ bool process_tile(const Field &f, int ty0, int tx0, float *sm,
                                              const CUtensorMap *tmap = nullptr,
                                              float *box = nullptr, uint64_t *bar = nullptr,
@@ -888,7 +977,7 @@ __device__ __forceinline__ bool process_tile(const Field &f, int ty0, int tx0, f
 
   bool staged = true;
   if constexpr (FROM_MEMBERS && TMA) {
-    staged = stage_members_tma<MODEL, TY, RB>(f, sm, box, bar, tmap, ty0, tx0, R4);
+    staged = stage_members_tma<MODEL, TY, RB, ASYNC>(f, sm, box, bar, tmap, ty0, tx0, R4);
   } else if (FROM_MEMBERS) {
     // work items per halo row: the two halo columns (scalar) and eight
     // groups of four interior columns (one float4 per member when aligned)

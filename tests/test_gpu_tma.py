@@ -1,9 +1,10 @@
-"""The tile kernels' member staging by the tensor memory accelerator (widths
-that are a multiple of 4 on a 16-byte aligned base) against the oracle, and
-against the per-thread staging of the same members (a base one float off
-16 bytes takes that path): identical parameters and probabilities, across
-narrow grids, grids smaller than a box, several boxes per tile (N up to 100),
-non-finite members, all models, minimum / maximum and saddle."""
+"""The tile kernels' member staging into a shared-memory box: by the tensor
+memory accelerator (widths that are a multiple of 4 on a 16-byte aligned
+base) and by 4-byte asynchronous copies (any other members: a base one
+float off 16 bytes, or a width that is not a multiple of 4).  Against the
+oracle and against each other: identical parameters and probabilities,
+across narrow grids, grids smaller than a box, several boxes per tile (N up
+to 100), non-finite members, all models, minimum / maximum and saddle."""
 import numpy as np
 import pytest
 import torch
@@ -139,3 +140,52 @@ def test_large_grid_64bit_offsets(ucp, ctx, orc):
             assert abs(pmin[y, x].item() - a[0]) <= 1e-5
             assert abs(pmax[y, x].item() - b[0]) <= 1e-5
         del pmin, pmax, params
+
+
+@pytest.mark.parametrize("model,bins", MODELS + [("histogram", 16), ("histogram", 13)])
+@pytest.mark.parametrize("shape,N", [((17, 37), 20), ((9, 2), 7), ((33, 63), 50),
+                                     ((8, 130), 100), ((40, 101), 300)])
+def test_async_staging_odd_widths(ucp, ctx, orc, model, bins, shape, N):
+    """Members of a width the tensor memory accelerator cannot address,
+    staged by asynchronous copies, against the same members padded to the
+    next multiple of 4 columns (staged by the accelerator): bit for bit on
+    every column whose neighbourhood the padding leaves alone (all but the
+    last), for minimum, maximum, status and saddle; the last column against
+    the oracle."""
+    H, W = shape
+    if N > 100 and model in ("gaussian", "histogram_semi"):
+        pytest.skip("covered at smaller N")
+    ens_np = _members(shape, N, seed=H * 13 + W + N)
+    Wp = (W + 3) // 4 * 4
+    pad = np.zeros((N, H, Wp), np.float32)
+    pad[:, :, :W] = ens_np
+    pad[:, :, W:] = ens_np[:, :, W - 1:W]
+    odd = torch.from_numpy(np.ascontiguousarray(ens_np)).cuda()
+    al = torch.from_numpy(pad).cuda()
+    d = ucp.make_desc(model, bins=bins or 8, mc_samples=64, seed=9)
+    ro = ctx.probability(odd, d)
+    so, _ = ctx.saddle(odd, d)
+    if model == "histogram_semi":
+        # its samples are keyed by the vertex index y * W + x, which the
+        # padding changes: against the same estimator from the fitted
+        # parameters instead
+        params = ctx.fit(odd, d)
+        rp = ctx.probability_from_params(params, d)
+        torch.cuda.synchronize()
+        for x, y in zip(ro[:2], rp[:2]):
+            np.testing.assert_allclose(x.cpu().numpy(), y.cpu().numpy(), rtol=0, atol=1e-6)
+        return
+    ra = ctx.probability(al, d)
+    sa, _ = ctx.saddle(al, d)
+    torch.cuda.synchronize()
+    for x, y in zip(ro, ra):
+        np.testing.assert_array_equal(x.cpu().numpy()[:, :W - 1], y.cpu().numpy()[:, :W - 1])
+    np.testing.assert_array_equal(so.cpu().numpy()[:, :W - 1], sa.cpu().numpy()[:, :W - 1])
+    if model == "gaussian":
+        return
+    params = ctx.fit(odd, d)
+    torch.cuda.synchronize()
+    gp = params.double().cpu().numpy()
+    rmin, rmax, _ = orc.prob(gp, d.model, bins=d.bins)
+    assert np.abs(ro[0].cpu().numpy() - rmin).max() <= TOL
+    assert np.abs(ro[1].cpu().numpy() - rmax).max() <= TOL
