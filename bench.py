@@ -193,7 +193,13 @@ ADJ_EPAN_FLOPS_PER_VERTEX = 2 * EPAN_FLOPS_PER_VERTEX_TYPE
 # three-model kernel) and of each model's own kernel, from the ncu captures
 # summarised in profiles/; None once a kernel has changed since its counters
 # were taken
-TRAFFIC_BYTES = {"fused": None, "uniform": None, "epanechnikov": None, "histogram": None}
+TRAFFIC_BYTES = {"fused": 95689472, "uniform": 88039424, "epanechnikov": 85209088,
+                 "histogram": 85687552, "hist_adjoint_16": 652988928}
+TRAFFIC_SOURCE = {"fused": "profiles/fused_kernel_1024x1024x20.md",
+                  "uniform": "profiles/fused_kernel_1024x1024x20.md",
+                  "epanechnikov": "profiles/fused_kernel_1024x1024x20.md",
+                  "histogram": "profiles/fused_kernel_1024x1024x20.md",
+                  "hist_adjoint_16": "profiles/adjoint_hist16_2048x2048x50.md"}
 
 
 def work_of(model, N, HW, params=None, bins=BINS2):
@@ -435,7 +441,8 @@ def run_ours(args):
                         "kernel": "the model's own fused fit + integrate kernel",
                         "roofline": {"bound": bound, "achieved": ach, "peak": peak,
                                      "unit": unit, "frac": ach / peak,
-                                     "traffic": TRAFFIC_BYTES[m]}}
+                                     "traffic": TRAFFIC_BYTES[m],
+                                     "traffic_source": TRAFFIC_SOURCE[m]}}
         shares[m] = avg
     # The step is one launch of the fused kernel (uniform + Epanechnikov +
     # histogram, members staged once): its duration is the step's.  Its
@@ -453,7 +460,7 @@ def run_ours(args):
           "kernel": "tile3_kernel (uniform + Epanechnikov + histogram-8 of one ensemble, "
                     "members staged once by TMA)",
           "traffic": TRAFFIC_BYTES["fused"],
-          "traffic_source": "profiles/fused_kernel_1024x1024x20.md (ncu dram__bytes_read/write)",
+          "traffic_source": TRAFFIC_SOURCE["fused"] + " (ncu dram__bytes_read/write)",
           "work": f"{EPAN_FLOPS_PER_VERTEX_TYPE} flops per vertex and type (Epanechnikov) + "
                   f"{HIST_FLOPS_PER_PIECE_TYPE} per merged histogram piece and type",
           "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz (derived)",
@@ -627,7 +634,11 @@ def other_rows(torch, ucp, ctx, dev, args, flush, peaks):
                 row["adjoint_roofline"] = {
                     "bound": "alu", "achieved": ach, "peak": fp32, "unit": "TFLOP/s",
                     "frac": ach / fp32, "work": f"{ADJ_HIST_FLOPS_PER_PIECE} flops per merged piece",
-                    "peak_source": fp32_src}
+                    "peak_source": fp32_src,
+                    "kernel": "hist_adj_tile<16> (+ hist_adj_fixup)",
+                    "algorithmic_bytes": (2.0 * b + 3.0) * 4.0 * HW4,
+                    "traffic": TRAFFIC_BYTES["hist_adjoint_16"],
+                    "traffic_source": TRAFFIC_SOURCE["hist_adjoint_16"] + " (hist_adj_tile alone)"}
                 row["oracle"] = oracle_fwd_bwd_rate(e4, Wt, m, b, rows=128)
             elif m == "epanechnikov":
                 fl = HW4 * EPAN_FLOPS_PER_VERTEX_TYPE / (ms_fw / 1e3) / 1e12
