@@ -50,6 +50,31 @@ constexpr float kFar = 3.0e38f;  // "never starts" breakpoint (finite: 0*kFar = 
 // sequence): support widths and bin widths only.
 __device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
 
+// NaN-propagating minimum / maximum (a NaN input gives NaN; otherwise the
+// same value as fminf / fmaxf): a running min and max over members then
+// flag a non-finite member by themselves (NaN: both NaN; +Inf: the max;
+// -Inf: the min).
+__device__ __forceinline__ float fmin_nan(float a, float b) {
+  float r;
+  asm("min.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float fmax_nan(float a, float b) {
+  float r;
+  asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float fmin3_nan(float a, float b, float c) {
+  float r;
+  asm("min.NaN.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ float fmax3_nan(float a, float b, float c) {
+  float r;
+  asm("max.NaN.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
 // Compensated (Kahan) summation: the running rounding error c is fed back
 // into the next addend.
 struct Kahan {

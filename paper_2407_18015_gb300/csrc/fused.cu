@@ -104,22 +104,37 @@ __device__ __forceinline__ bool stage3(const Field &f, float *smh, float *sme, f
     for (int p = 0; p < PER; ++p) {
       if (!in[p]) continue;
       const float *col = box + off[p];
+      // as stage_members_tma: member 0 starts min / max (and adds 0 to the
+      // sums), the others in pairs into NaN-propagating min / max
+      int k = 0;
       if (k0 == 0) {
         x0[p] = mn[p] = mx[p] = col[0];
-        nf[p] = false;
+        k = 1;
       }
-      for (int k = 0; k < kn; ++k) {
-        const float v = col[k * PLANE];
-        nf[p] |= !isfinite(v);
-        mn[p] = fminf(mn[p], v);
-        mx[p] = fmaxf(mx[p], v);
+      auto add = [&](float v) {
         const float d = v - x0[p];
         s1[p].add(d);
         s2[p].add(d * d);
+      };
+#pragma unroll 4
+      for (; k + 1 < kn; k += 2) {
+        const float v1 = col[k * PLANE], v2 = col[(k + 1) * PLANE];
+        mn[p] = fmin3_nan(mn[p], v1, v2);
+        mx[p] = fmax3_nan(mx[p], v1, v2);
+        add(v1);
+        add(v2);
+      }
+      if (k < kn) {
+        const float v = col[k * PLANE];
+        mn[p] = fmin_nan(mn[p], v);
+        mx[p] = fmax_nan(mx[p], v);
+        add(v);
       }
     }
     __syncthreads();
   }
+#pragma unroll
+  for (int p = 0; p < PER; ++p) nf[p] = !(isfinite(mn[p]) && isfinite(mx[p]));
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
     if (!in[p]) continue;

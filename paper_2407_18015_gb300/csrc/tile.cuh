@@ -701,24 +701,41 @@ __device__ __forceinline__ bool stage_members_tma(const Field &f, float *sm, flo
       if (!in[p]) continue;
       const int sh = shift0(p, k0);
       const float *col = box + off[p] + sh;
+      // member 0 starts the running min / max (and is the shift x0 of the
+      // Epanechnikov sums, to which it adds 0); the others go in pairs into
+      // NaN-propagating three-input min / max, so that a non-finite member
+      // shows in mn / mx (nf below)
+      int k = 0;
       if (k0 == 0) {
         x0[p] = mn[p] = mx[p] = col[0];
-        nf[p] = false;
+        k = 1;
       }
       auto add = [&](float v) {
-        nf[p] |= !isfinite(v);
-        mn[p] = fminf(mn[p], v);
-        mx[p] = fmaxf(mx[p], v);
         if constexpr (EP) {
           const float d = v - x0[p];
           s1[p].add(d);
           s2[p].add(d * d);
         }
       };
+      auto add2 = [&](float v1, float v2) {
+        mn[p] = fmin3_nan(mn[p], v1, v2);
+        mx[p] = fmax3_nan(mx[p], v1, v2);
+        add(v1);
+        add(v2);
+      };
       if (pl == 0) {
-        for (int k = 0; k < kn; ++k) add(col[k * PLANE]);
+#pragma unroll 4
+        for (; k + 1 < kn; k += 2) add2(col[k * PLANE], col[(k + 1) * PLANE]);
       } else {
-        for (int k = 0; k < kn; ++k) add(col[k * PLANE + (((sh + k * pl) & 3) - sh)]);
+        for (; k + 1 < kn; k += 2)
+          add2(col[k * PLANE + (((sh + k * pl) & 3) - sh)],
+               col[(k + 1) * PLANE + (((sh + (k + 1) * pl) & 3) - sh)]);
+      }
+      if (k < kn) {
+        const float v = col[k * PLANE + (((sh + k * pl) & 3) - sh)];
+        mn[p] = fmin_nan(mn[p], v);
+        mx[p] = fmax_nan(mx[p], v);
+        add(v);
       }
     }
     __syncthreads();
@@ -730,6 +747,8 @@ __device__ __forceinline__ bool stage_members_tma(const Field &f, float *sm, flo
     __syncthreads();
     return false;
   }
+#pragma unroll
+  for (int p = 0; p < PER; ++p) nf[p] = !(isfinite(mn[p]) && isfinite(mx[p]));
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
     if (!in[p]) continue;
