@@ -252,8 +252,10 @@ int ucp_probability_host(ucp_ctx *ctx, const float *ens_host, int N, int H, int 
 
 /* Several models of one ensemble, device arrays: one uniform, one
  * Epanechnikov and one histogram model of at most 8 bins (in any order, one
- * boundary rule, members 16-byte aligned with W a multiple of 4) run as one
- * fused kernel on `stream` that stages the members once for all three;
+ * boundary rule) run as one fused kernel on `stream` that stages the
+ * members once for all three (by the tensor memory accelerator when the
+ * members are 16-byte aligned with W a multiple of 4, else by asynchronous
+ * copies);
  * otherwise the models' kernels run concurrently on the context's compute
  * streams, forked from `stream` and joined back into it (asynchronous
  * either way; the results are those of ucp_probability for each model, bit

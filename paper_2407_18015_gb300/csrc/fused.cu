@@ -15,6 +15,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstring>
 #include <atomic>
 
 #include "device.cuh"
@@ -40,8 +41,10 @@ __host__ __device__ constexpr long long htile3_floats() { return 4LL * kHALO3 + 
 __host__ __device__ constexpr long long etile3_floats() { return 2LL * kHALO3; }
 
 // Staging of one fused tile (see stage_members_tma: the same box walk, the
-// same per-vertex arithmetic for each model).  Returns false if a bounded
-// wait gave up.
+// same per-vertex arithmetic for each model; ASYNC: the box filled by
+// asynchronous copies, members the tensor memory accelerator cannot
+// address).  Returns false if a bounded wait gave up.
+template <bool ASYNC>
 __device__ __forceinline__ bool stage3(const Field &f, float *smh, float *sme, float *box,
                                        uint64_t *bar, const CUtensorMap *tmap, int ty0, int tx0,
                                        float4 *R4) {
@@ -51,7 +54,10 @@ __device__ __forceinline__ bool stage3(const Field &f, float *smh, float *sme, f
   const int N = f.N, nc = f.tma_nc, B = f.B;
   const unsigned box_bytes = (unsigned)(PLANE * nc * sizeof(float));
   const int ylim = min(f.H, f.y1 + 1);
-  int off[PER], lv[PER];
+  // element shifts of the asynchronous-copy box (all 0 for the accelerator)
+  const int eb = ASYNC ? (int)(reinterpret_cast<uintptr_t>(f.ens) >> 2) & 3 : 0;
+  const int pl = ASYNC ? (int)(f.plane & 3) : 0, w4 = ASYNC ? f.W & 3 : 0;
+  int off[PER], lv[PER], rq[PER];
   bool in[PER];
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
@@ -61,7 +67,9 @@ __device__ __forceinline__ bool stage3(const Field &f, float *smh, float *sme, f
     lv[p] = l;
     in[p] = l < HALO && gy >= 0 && gy < ylim && gx >= 0 && gx < f.W;
     off[p] = r * kBoxW + c + 3;
+    rq[p] = ((gy & 3) * w4) & 3;
   }
+  auto shift0 = [&](int p, int k0) { return (eb + (k0 & 3) * pl + rq[p]) & 3; };
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     mbar_init_fence();
@@ -74,6 +82,10 @@ __device__ __forceinline__ bool stage3(const Field &f, float *smh, float *sme, f
   // one warp polls the barrier, the others wait at the CTA barrier; every
   // thread then tests the completed phase once (its own acquire)
   auto load = [&](int k0) -> bool {
+    if constexpr (ASYNC) {
+      box_copy_async<HY>(f, box, k0, nc, ty0, tx0, ylim);
+      return true;
+    }
     if (threadIdx.x == 0) {
       proxy_async_fence();
       mbar_expect_tx(bar, box_bytes);
@@ -103,7 +115,10 @@ __device__ __forceinline__ bool stage3(const Field &f, float *smh, float *sme, f
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
       if (!in[p]) continue;
-      const float *col = box + off[p];
+      const int sh = shift0(p, k0);
+      const float *col = box + off[p] + sh;
+      // member k of the box at col[at(k)]
+      auto at = [&](int k) { return k * PLANE + (pl == 0 ? 0 : ((sh + k * pl) & 3) - sh); };
       // as stage_members_tma: member 0 starts min / max (and adds 0 to the
       // sums), the others in pairs into NaN-propagating min / max
       int k = 0;
@@ -118,14 +133,14 @@ __device__ __forceinline__ bool stage3(const Field &f, float *smh, float *sme, f
       };
 #pragma unroll 4
       for (; k + 1 < kn; k += 2) {
-        const float v1 = col[k * PLANE], v2 = col[(k + 1) * PLANE];
+        const float v1 = col[at(k)], v2 = col[at(k + 1)];
         mn[p] = fmin3_nan(mn[p], v1, v2);
         mx[p] = fmax3_nan(mx[p], v1, v2);
         add(v1);
         add(v2);
       }
       if (k < kn) {
-        const float v = col[k * PLANE];
+        const float v = col[at(k)];
         mn[p] = fmin_nan(mn[p], v);
         mx[p] = fmax_nan(mx[p], v);
         add(v);
@@ -178,14 +193,16 @@ __device__ __forceinline__ bool stage3(const Field &f, float *smh, float *sme, f
 #pragma unroll
       for (int p = 0; p < PER; ++p) {
         if (!bin[p]) continue;
-        const float *col = box + off[p];
+        const int sh = shift0(p, k0);
+        const float *col = box + off[p] + sh;
+        auto at = [&](int k) { return k * PLANE + (pl == 0 ? 0 : ((sh + k * pl) & 3) - sh); };
         if (!wide) {
 #pragma unroll 4
           for (int k = 0; k < kn; ++k)
-            cw[p][0] += 1ull << (hist_bin_nonneg(col[k * PLANE], mn[p], sc[p], B) << 3);
+            cw[p][0] += 1ull << (hist_bin_nonneg(col[at(k)], mn[p], sc[p], B) << 3);
         } else {
           for (int k = 0; k < kn; ++k) {
-            const int j = hist_bin_nonneg(col[k * PLANE], mn[p], sc[p], B);
+            const int j = hist_bin_nonneg(col[at(k)], mn[p], sc[p], B);
             const unsigned long long inc = 1ull << ((j & 3) << 4);
             cw[p][0] += (j >> 2) == 0 ? inc : 0ull;
             cw[p][1] += (j >> 2) == 1 ? inc : 0ull;
@@ -323,6 +340,7 @@ __device__ __forceinline__ void integrate3(const Field3 &F, int ty0, int tx0, co
   }
 }
 
+template <bool ASYNC>
 __global__ void __launch_bounds__(NTHREADS, kOcc3)
     tile3_kernel(Field3 F, int tiles_x, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(128) float smem[];
@@ -334,7 +352,7 @@ __global__ void __launch_bounds__(NTHREADS, kOcc3)
   float *sme = smh + htile3_floats();
   uint64_t *bar = reinterpret_cast<uint64_t *>(sme + ((etile3_floats() + 1) & ~1LL));
   float4 *R4 = reinterpret_cast<float4 *>(smem);
-  const bool ok = stage3(f, smh, sme, smem, bar, &tmap, ty0, tx0, R4);
+  const bool ok = stage3<ASYNC>(f, smh, sme, smem, bar, &tmap, ty0, tx0, R4);
   __syncthreads();
   if (!ok) {  // a bounded wait gave up: NaN and the timeout flag, every model
     const int v = threadIdx.x, gy = ty0 + v / 32, gx = tx0 + v % 32;
@@ -357,9 +375,11 @@ cudaError_t launch_closed3(const Field3 &F, cudaStream_t s, bool *launched) {
   *launched = false;
   const Field &f = F.f;
   if (f.B < 1 || f.B > 8 || f.N < 1 || f.N > 65535) return cudaSuccess;
-  if (f.W % 4 != 0 || (reinterpret_cast<uintptr_t>(f.ens) & 15) != 0) return cudaSuccess;
+  // members the tensor memory accelerator cannot address (W not a multiple
+  // of 4, a base not 16-byte aligned) are staged by asynchronous copies
+  const bool tma = f.W % 4 == 0 && (reinterpret_cast<uintptr_t>(f.ens) & 15) == 0;
   auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encoder_fn());
-  if (!enc) return cudaSuccess;
+  if (tma && !enc) return cudaSuccess;
   const size_t fixed_b =
       (size_t)(htile3_floats() + ((etile3_floats() + 1) & ~1LL)) * sizeof(float) + 16;
   const size_t rows_b = (size_t)rows3_floats(f.B) * sizeof(float);
@@ -375,15 +395,18 @@ cudaError_t launch_closed3(const Field3 &F, cudaStream_t s, bool *launched) {
   const long long tiles = (long long)tiles_x * tiles_y;
   if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
   CUtensorMap map;
-  const cuuint64_t dims[3] = {(cuuint64_t)f.W, (cuuint64_t)f.H, (cuuint64_t)f.N};
-  const cuuint64_t strides[2] = {(cuuint64_t)f.W * sizeof(float),
-                                 (cuuint64_t)f.plane * sizeof(float)};
-  const cuuint32_t box[3] = {(cuuint32_t)kBoxW, (cuuint32_t)(kTY3 + 2), (cuuint32_t)nc};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(f.ens), dims, strides, box,
-          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-    return cudaSuccess;
+  memset(&map, 0, sizeof(map));
+  if (tma) {
+    const cuuint64_t dims[3] = {(cuuint64_t)f.W, (cuuint64_t)f.H, (cuuint64_t)f.N};
+    const cuuint64_t strides[2] = {(cuuint64_t)f.W * sizeof(float),
+                                   (cuuint64_t)f.plane * sizeof(float)};
+    const cuuint32_t box[3] = {(cuuint32_t)kBoxW, (cuuint32_t)(kTY3 + 2), (cuuint32_t)nc};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(f.ens), dims, strides,
+            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaSuccess;
+  }
   // per device: the attribute is set once (host threads may race to set it;
   // setting it twice is harmless, the flag itself is atomic)
   static std::atomic<bool> attr_set[128] = {};
@@ -392,7 +415,11 @@ cudaError_t launch_closed3(const Field3 &F, cudaStream_t s, bool *launched) {
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
   if (!attr_set[dev].load(std::memory_order_acquire)) {
-    e = cudaFuncSetAttribute(tile3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    e = cudaFuncSetAttribute(tile3_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             227 * 1024);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(tile3_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               227 * 1024);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return e;
@@ -402,7 +429,10 @@ cudaError_t launch_closed3(const Field3 &F, cudaStream_t s, bool *launched) {
   Field3 G = F;
   G.f.tma_nc = nc;
   const size_t smem = std::max((size_t)nc * per_member, rows_b) + fixed_b;
-  tile3_kernel<<<(int)tiles, NTHREADS, smem, s>>>(G, tiles_x, map);
+  if (tma)
+    tile3_kernel<false><<<(int)tiles, NTHREADS, smem, s>>>(G, tiles_x, map);
+  else
+    tile3_kernel<true><<<(int)tiles, NTHREADS, smem, s>>>(G, tiles_x, map);
   *launched = true;
   return cudaGetLastError();
 }

@@ -46,7 +46,7 @@ struct Field3 {
   float *out_max[3];
   uint8_t *status[3];
 };
-// Launches the fused kernel when it applies (members TMA aligned, at most 8
+// Launches the fused kernel when it applies (any member alignment, at most 8
 // bins and 65535 members); *launched tells whether it did.
 cudaError_t launch_closed3(const Field3 &f, cudaStream_t s, bool *launched);
 // cuTensorMapEncodeTiled from the driver (nullptr if unavailable)

@@ -548,6 +548,53 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
+// Members [k0, k0 + min(nc, N - k0)) of the box of the tile at (ty0, tx0),
+// rows below ylim, by 16-byte asynchronous copies of the aligned blocks
+// that hold each (member, row) segment (see `load` in stage_members_tma for
+// the layout: column c of member m, row r at m PLANE + r kBoxW + c + d, d =
+// (address / 4) mod 4); the copies have landed for the whole CTA on return.
+template <int HY>
+__device__ __forceinline__ void box_copy_async(const Field &f, float *box, int k0, int nc,
+                                               int ty0, int tx0, int ylim) {
+  constexpr int PLANE = HY * kBoxW;
+  const int N = f.N;
+  constexpr int SLOTS = NTHREADS / 5, DM = SLOTS / HY, DR = SLOTS % HY;
+  const int nseg = min(nc, N - k0) * HY;
+  if (threadIdx.x < SLOTS * 5) {
+    const int q = threadIdx.x % 5;
+    int sg = threadIdx.x / 5;
+    const int m = sg / HY;
+    int r = sg - m * HY;
+    // smem columns (before the shift d) that staged vertices read
+    const int lo0 = max(tx0 - 1, 0) - tx0 + 4, hi0 = min(tx0 + 33, f.W) - tx0 + 4;
+    const uintptr_t rstep = (uintptr_t)f.W * 4u, pstep = (uintptr_t)f.plane * 4u;
+    uintptr_t a = reinterpret_cast<uintptr_t>(f.ens) +
+                  (uintptr_t)(((long long)(k0 + m) * f.plane +
+                               (long long)(ty0 - 1 + r) * f.W + (tx0 - 4)) * 4);
+    float *dst = box + m * PLANE + r * kBoxW + 8 * q;
+    for (; sg < nseg; sg += SLOTS) {
+      const int gy = ty0 - 1 + r;
+      if ((unsigned)gy < (unsigned)ylim) {
+        const int d = (int)(a >> 2) & 3;
+        const int lo = lo0 + d, hi = hi0 + d, j = 8 * q;
+        const uintptr_t cb = (a & ~(uintptr_t)15) + 32u * q;
+        if (j + 4 > lo && j < hi) cp_async16(dst, cb);
+        if (j + 8 > lo && j + 4 < hi) cp_async16(dst + 4, cb + 16);
+      }
+      r += DR;
+      a += DM * pstep + DR * rstep;
+      dst += DM * PLANE + DR * kBoxW;
+      if (r >= HY) {
+        r -= HY;
+        a += pstep - HY * rstep;
+        dst += PLANE - HY * kBoxW;
+      }
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+}
+
 // wait for the completion of phase `parity`; gives up after a bounded number
 // of polls (each poll itself returns after a bounded time)
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
@@ -637,41 +684,7 @@ __device__ __forceinline__ bool stage_members_tma(const Field &f, float *sm, flo
   // readers add it, per row, and per member when pl != 0.
   auto load = [&](int k0) -> bool {
     if constexpr (ASYNC) {
-      constexpr int SLOTS = NTHREADS / 5, DM = SLOTS / HY, DR = SLOTS % HY;
-      const int nseg = min(nc, N - k0) * HY;
-      if (threadIdx.x < SLOTS * 5) {
-        const int q = threadIdx.x % 5;
-        int sg = threadIdx.x / 5;
-        const int m = sg / HY;
-        int r = sg - m * HY;
-        // smem columns (before the shift d) that staged vertices read
-        const int lo0 = max(tx0 - 1, 0) - tx0 + 4, hi0 = min(tx0 + 33, f.W) - tx0 + 4;
-        const uintptr_t rstep = (uintptr_t)f.W * 4u, pstep = (uintptr_t)f.plane * 4u;
-        uintptr_t a = reinterpret_cast<uintptr_t>(f.ens) +
-                      (uintptr_t)(((long long)(k0 + m) * f.plane +
-                                   (long long)(ty0 - 1 + r) * f.W + (tx0 - 4)) * 4);
-        float *dst = box + m * PLANE + r * kBoxW + 8 * q;
-        for (; sg < nseg; sg += SLOTS) {
-          const int gy = ty0 - 1 + r;
-          if ((unsigned)gy < (unsigned)ylim) {
-            const int d = (int)(a >> 2) & 3;
-            const int lo = lo0 + d, hi = hi0 + d, j = 8 * q;
-            const uintptr_t cb = (a & ~(uintptr_t)15) + 32u * q;
-            if (j + 4 > lo && j < hi) cp_async16(dst, cb);
-            if (j + 8 > lo && j + 4 < hi) cp_async16(dst + 4, cb + 16);
-          }
-          r += DR;
-          a += DM * pstep + DR * rstep;
-          dst += DM * PLANE + DR * kBoxW;
-          if (r >= HY) {
-            r -= HY;
-            a += pstep - HY * rstep;
-            dst += PLANE - HY * kBoxW;
-          }
-        }
-      }
-      cp_async_wait_all();
-      __syncthreads();
+      box_copy_async<HY>(f, box, k0, nc, ty0, tx0, ylim);
       return true;
     }
     if (threadIdx.x == 0) {

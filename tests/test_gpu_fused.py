@@ -2,9 +2,10 @@
 histogram of at most 8 bins of one ensemble, one launch) against the three
 single-model launches: the same probabilities and status bit for bit, on
 ragged shapes, several member boxes, more than 255 members (16-bit bin
-counters), both boundary rules, non-finite members; and the cases that do
-not fuse (more bins, members not TMA aligned, other model sets) give the
-single-model results too."""
+counters), both boundary rules, non-finite members, members staged by the
+tensor memory accelerator and by asynchronous copies (odd widths, a base
+one float off 16 bytes); and the cases that do not fuse (more bins, other
+model sets) give the single-model results too."""
 import numpy as np
 import pytest
 import torch
@@ -53,7 +54,8 @@ def _models_vs_single(ucp, ctx, ens, descs, cptypes=3):
 
 @pytest.mark.parametrize("shape,N,bins,boundary", [
     ((64, 64), 20, 8, 0), ((37, 52), 20, 8, 1), ((8, 32), 3, 5, 0), ((130, 96), 60, 8, 0),
-    ((17, 100), 300, 7, 0), ((1, 64), 12, 8, 0), ((300, 4), 9, 1, 1)])
+    ((17, 100), 300, 7, 0), ((1, 64), 12, 8, 0), ((300, 4), 9, 1, 1), ((33, 63), 20, 8, 0),
+    ((41, 101), 50, 8, 1), ((9, 2), 7, 3, 0), ((65, 1023), 20, 8, 0), ((12, 30), 300, 8, 0)])
 def test_fused_equals_single_models(ucp, ctx, shape, N, bins, boundary):
     H, W = shape
     ens_np = _members(H, W, N, seed=H * 7 + W + N)
