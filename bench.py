@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-rows", action="store_true", help="headline workload only")
-    ap.add_argument("--rows", default="mvn,fwdbwd,batch,saddle,gmm,stencil")
+    ap.add_argument("--rows", default="mvn,fwdbwd,batch,saddle,gmm,stencil,sizes")
     ap.add_argument("--batch-fields", type=int, default=64, help="fields of the batch row")
     ap.add_argument("--batch-max", type=int, default=2048, help="largest field side of the batch row")
     return ap.parse_args()
@@ -195,6 +195,27 @@ ADJ_EPAN_FLOPS_PER_VERTEX = 2 * EPAN_FLOPS_PER_VERTEX_TYPE
 # were taken
 TRAFFIC_BYTES = {"fused": 95689472, "uniform": 88039424, "epanechnikov": 85209088,
                  "histogram": 85687552, "hist_adjoint_16": 652988928}
+# warp instructions per launch of the same kernels (ncu smsp__inst_executed.sum,
+# profiles/instructions_bench_headline_1024x1024x20.md): the issue-rate
+# fraction reported beside the FP32 / HBM one; None once a kernel changed
+ISSUE_WARP_INSTR = {"fused": 206773693, "uniform": 23586076, "epanechnikov": 62221552,
+                    "histogram": 141878590}
+ISSUE_SOURCE = "profiles/instructions_bench_headline_1024x1024x20.md"
+
+
+def issue_block(key, ms, mhz):
+    """Issue-rate fraction of a kernel of `ms` per launch: its warp
+    instructions per launch against 152 SMs x 4 schedulers x 1 instruction
+    per clock."""
+    n = ISSUE_WARP_INSTR.get(key)
+    if n is None:
+        return None
+    peak = SM_COUNT * 4 * mhz * 1e6 / 1e9
+    ach = n / (ms / 1e3) / 1e9
+    return {"warp_instructions": n, "achieved": ach, "peak": peak,
+            "unit": "G warp instructions/s", "frac": ach / peak, "source": ISSUE_SOURCE}
+
+
 TRAFFIC_SOURCE = {"fused": "profiles/fused_kernel_1024x1024x20.md",
                   "uniform": "profiles/fused_kernel_1024x1024x20.md",
                   "epanechnikov": "profiles/fused_kernel_1024x1024x20.md",
@@ -442,7 +463,8 @@ def run_ours(args):
                         "roofline": {"bound": bound, "achieved": ach, "peak": peak,
                                      "unit": unit, "frac": ach / peak,
                                      "traffic": TRAFFIC_BYTES[m],
-                                     "traffic_source": TRAFFIC_SOURCE[m]}}
+                                     "traffic_source": TRAFFIC_SOURCE[m]},
+                        "issue": issue_block(m, avg, peaks["sm_max_mhz"])}
         shares[m] = avg
     # The step is one launch of the fused kernel (uniform + Epanechnikov +
     # histogram, members staged once): its duration is the step's.  Its
@@ -466,7 +488,8 @@ def run_ours(args):
           "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz (derived)",
           "hbm_achieved_gbs": hbm_b / (t_kernel / 1e3) / 1e9,
           "hbm_frac": hbm_b / (t_kernel / 1e3) / 1e9 / peaks["hbm_gbs"],
-          "share": 1.0}
+          "share": 1.0,
+          "issue": issue_block("fused", t_kernel, peaks["sm_max_mhz"])}
 
     line = {
         "metric": "critical-point probability vertices/s (uniform + Epanechnikov + "
@@ -505,12 +528,15 @@ def _g(x):
 def summarise(line):
     """A compact digest of the line (ms, vertices/s and roofline fraction per
     kernel and row), placed last so that it survives a truncated tail."""
+    iss = lambda b: _g(b["frac"]) if isinstance(b, dict) else None
     out = {"headline": {"ms": _g(line["ms_per_step"]), "vps": _g(line["value"]),
                         "frac": _g(line["roofline"]["frac"]),
+                        "issue_frac": iss(line["roofline"].get("issue")),
                         "e2e_vps": _g(line.get("e2e", {}).get("value"))}}
     for m, r in line.get("per_model", {}).items():
         out[m] = {"ms": _g(r["ms"]), "vps": _g(r["vertices_per_s"]),
-                  "frac": _g(r["roofline"]["frac"]), "bound": r["roofline"]["bound"]}
+                  "frac": _g(r["roofline"]["frac"]), "bound": r["roofline"]["bound"],
+                  "issue_frac": iss(r.get("issue"))}
     for name, r in (line.get("rows") or {}).items():
         d = {}
         for k in ("ms", "ms_fwd", "ms_adjoint", "ms_fwd_bwd", "ms_batched_graph",
@@ -667,6 +693,24 @@ def other_rows(torch, ucp, ctx, dev, args, flush, peaks):
         rows[f"batch_{args.batch_fields}_fields"] = batch_row(torch, ucp, ctx, dev, steps, flush,
                                                               args.batch_fields, args.batch_max,
                                                               peaks)
+    if "sizes" in want:
+        # the uniform kernel (N=20, both types) over grid sizes: whether its
+        # HBM fraction at 1024^2 is a size effect or the kernel's own bound
+        out = {}
+        for S in (512, 1024, 2048, 4096):
+            g = torch.Generator(device=dev).manual_seed(S)
+            es = torch.randn((20, S, S), device=dev, generator=g)
+            pm = torch.empty((S, S), device=dev)
+            px = torch.empty_like(pm)
+            d = ucp.make_desc("uniform")
+            ms, _ = timed_steps(torch, lambda ev: ucp.ucp_probability(ctx.handle, es, d, 3, pm, px),
+                                max(steps, 10), 3, flush)
+            ms /= max(steps, 10)
+            gbs = (4.0 * 20 + 8.0) * S * S / (ms / 1e3) / 1e9
+            out[f"{S}x{S}x20"] = {"ms": ms, "algorithmic_GBps": gbs,
+                                  "hbm_frac": gbs / peaks["hbm_gbs"]}
+            del es, pm, px
+        rows["uniform_sizes_n20"] = out
     if "saddle" in want:
         e2 = torch.from_numpy(synth.ensemble_bimodal(H2, W2, N2, seed=SEED2)).to(dev)
         out = torch.empty((H2, W2), device=dev)
