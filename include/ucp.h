@@ -283,7 +283,11 @@ int ucp_probability_models(ucp_ctx *ctx, const float *ens, int N, int H, int W,
  * for the types in cptypes; an entry may be NULL, and that field of that
  * model is then not copied back (the pointer arrays themselves must not be
  * NULL).  status_host may be NULL, or an array of nmodels pointers any of
- * which may be NULL.  Context-owned device buffers: N*H*W floats of members and
+ * which may be NULL.  When the models fuse (see ucp_probability_models) and
+ * every wanted output array is mapped pinned host memory (cudaHostAlloc, or
+ * cudaHostRegister with mapping), the fused kernel writes the probabilities
+ * straight into those arrays over the host link, and nothing is read back.
+ * Context-owned device buffers: N*H*W floats of members and
  * 9*nmodels*H*W bytes of outputs.  Results are those of ucp_probability. */
 int ucp_probability_host_models(ucp_ctx *ctx, const float *ens_host, int N, int H, int W,
                                 const ucp_model_desc *descs, int nmodels, unsigned cptypes,

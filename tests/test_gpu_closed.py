@@ -292,6 +292,44 @@ def test_host_models_match_device(ucp, ctx, shape, N):
             np.testing.assert_array_equal(hmin[m], ref[m][0].cpu().numpy())
 
 
+@pytest.mark.parametrize("shape,N", [((300, 257), 9), ((1024, 1024), 20), ((65, 1023), 30)])
+def test_host_models_pinned_outputs(ucp, ctx, shape, N):
+    """ucp_probability_host_models with pinned output arrays: the fused
+    kernel writes the caller's mapped arrays directly (no read-back copies).
+    The same bits as the device-array call, with and without status arrays,
+    minimum only, and with one pageable output (the read-back path)."""
+    from paper_2407_18015_gb300 import synth
+    H, W = shape
+    ens_np = synth.ensemble_bimodal(H, W, N, seed=7 + W, lam_scale=0.5)
+    descs = [ucp.make_desc("histogram", bins=8), ucp.make_desc("uniform"),
+             ucp.make_desc("epanechnikov")]
+    ref = [ctx.probability(_dev(ens_np), d) for d in descs]
+    torch.cuda.synchronize()
+    ens_h = torch.from_numpy(ens_np).pin_memory()
+    pinned = lambda dt: torch.full((H, W), -1, dtype=dt).pin_memory()
+    for with_status in (True, False):
+        hmin = [pinned(torch.float32) for _ in descs]
+        hmax = [pinned(torch.float32) for _ in descs]
+        hst = [pinned(torch.uint8) for _ in descs] if with_status else None
+        ucp.ucp_probability_host_models(ctx.handle, ens_h, descs, 3, hmin, hmax, hst)
+        for m in range(3):
+            assert torch.equal(hmin[m], ref[m][0].cpu())
+            assert torch.equal(hmax[m], ref[m][1].cpu())
+            if with_status:
+                assert torch.equal(hst[m], ref[m][2].cpu())
+    hmin = [pinned(torch.float32) for _ in descs]
+    ucp.ucp_probability_host_models(ctx.handle, ens_h, descs, ucp.UCP_MIN, hmin, [None] * 3)
+    for m in range(3):
+        assert torch.equal(hmin[m], ref[m][0].cpu())
+    hmin = [pinned(torch.float32) for _ in descs]
+    hmax = [pinned(torch.float32) for _ in descs]
+    hmax[1] = np.full((H, W), -1, np.float32)  # pageable: every output read back
+    ucp.ucp_probability_host_models(ctx.handle, ens_h, descs, 3, hmin, hmax)
+    for m in range(3):
+        assert torch.equal(hmin[m], ref[m][0].cpu())
+        np.testing.assert_array_equal(np.asarray(hmax[m]), ref[m][1].cpu().numpy())
+
+
 def test_host_models_rejects(ucp, ctx):
     ens = np.zeros((3, 8, 8), np.float32)
     out = [np.zeros((8, 8), np.float32)]
