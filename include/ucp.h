@@ -80,7 +80,8 @@ typedef enum {
    * absent neighbours are 0.  Sampling contract: sample s of the vertex with
    * linear index i draws two Philox4x32-10 blocks (Salmon et al., SC'11) with
    * counter (s, i, field_id, j), j = 0, 1, and key (seed & 0xffffffff,
-   * seed >> 32); words r give uniforms ((r >> 8) + 0.5) * 2^-24; Box-Muller
+   * seed >> 32); words r give uniforms ((r >> 9) + 0.5) * 2^-23 (exact in
+   * binary32, strictly inside (0, 1)); Box-Muller
    * on (u0,u1), (u2,u3), (u4,u5) gives z_0..z_5; x = mu + L z with L the
    * Cholesky factor of the covariance of the vertex and its present
    * neighbours in the order v, e, n, w, s (z_0..z_k used).  If the

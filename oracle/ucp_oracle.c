@@ -1008,7 +1008,8 @@ static int cholesky(const double *A, int n, double *L) {
 /* Monte Carlo for selected vertices.  params: [20][H][W] doubles (see
  * orc_fit).  Sample s of vertex i uses two Philox4x32-10 blocks with
  * counter (s, i, field, j), j = 0, 1, and key (seed_lo, seed_hi); the eight
- * words give uniforms u = ((r >> 8) + 0.5) / 2^24, and Box-Muller on the
+ * words give uniforms u = ((r >> 9) + 0.5) / 2^23 (exact in binary32 as in
+ * binary64, and strictly inside (0, 1)), and Box-Muller on the
  * pairs (u0,u1), (u2,u3), (u4,u5) gives z_0..z_5, of which z_0..z_k are used
  * (k = number of in-grid neighbours): x = mu + L z with L the Cholesky factor
  * of the covariance of the vertex and its present neighbours (in the order
@@ -1119,7 +1120,7 @@ int orc_mvn_mc_at(const double *params, int H, int W, int boundary, const int64_
         orc_philox4x32_10(ctr, key, r8);
         ctr[3] = 1;
         orc_philox4x32_10(ctr, key, r8 + 4);
-        for (a = 0; a < 6; ++a) u[a] = ((double)(r8[a] >> 8) + 0.5) / 16777216.0;
+        for (a = 0; a < 6; ++a) u[a] = ((double)(r8[a] >> 9) + 0.5) / 8388608.0;
         for (a = 0; a < 3; ++a) {
           double rad = sqrt(-2.0 * log(u[2 * a]));
           double th = two_pi * u[2 * a + 1];

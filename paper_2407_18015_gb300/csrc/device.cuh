@@ -1049,9 +1049,16 @@ __device__ __forceinline__ uint4 philox_block(uint4 c, const PhiloxKeys &K) {
   return c;
 }
 
+// ((r >> 8) + 0.5) * 2^-24 rounded to binary32 (one rounding: exact below
+// 1/2, the nearest even multiple of 2^-24 above, 1.0 for the largest r):
+// the semianalytical estimator's uniforms
 __device__ __forceinline__ float u01(uint32_t r) {
-  // ((r >> 8) + 0.5) * 2^-24, exact in binary32
   return fmaf(__uint2float_rn(r >> 8), 0x1p-24f, 0x1p-25f);
+}
+// ((r >> 9) + 0.5) * 2^-23, exact in binary32 and strictly inside (0, 1):
+// the Monte Carlo path's uniforms (a logarithm of each is taken)
+__device__ __forceinline__ float u01_23(uint32_t r) {
+  return fmaf(__uint2float_rn(r >> 9), 0x1p-23f, 0x1p-24f);
 }
 
 // ---------------------------------------------------------------------------

@@ -6,7 +6,8 @@
 //
 // One warp per vertex.  Lanes split the samples; each sample draws two
 // Philox4x32-10 blocks (counter (s, vertex, field, j), key = seed), maps the
-// words to uniforms ((r >> 8) + 0.5) 2^-24, and Box-Muller gives six
+// words to uniforms ((r >> 9) + 0.5) 2^-23 (exact in binary32, inside
+// (0, 1)), and Box-Muller gives six
 // normals, five of which are used.  The comparisons x_v < x_n are evaluated
 // on the differences y_n = x_v - x_n = (mu_v - mu_n) + (L_v. - L_n.) z, and
 // hits are counted with __ballot_sync + __popc.
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(256) mvn_fit_kernel(Field f) {
 // ---------------------------------------------------------------------------
 // Monte Carlo, warp per vertex
 
-template <bool FROM_MEMBERS>
+template <bool FROM_MEMBERS, bool SADDLE>
 __global__ void __launch_bounds__(256) mvn_mc_kernel(Field f, int S, uint32_t k0, uint32_t k1,
                                                      uint32_t field) {
   const int lane = threadIdx.x & 31;
@@ -301,28 +302,36 @@ __global__ void __launch_bounds__(256) mvn_mc_kernel(Field f, int S, uint32_t k0
           uint4 r0, r1;
           philox_pair((uint32_t)s, vid, field, K, r0, r1);
           float z[6];
-          box_muller(u01(r0.x), u01(r0.y), z[0], z[1]);
-          box_muller(u01(r0.z), u01(r0.w), z[2], z[3]);
-          box_muller(u01(r1.x), u01(r1.y), z[4], z[5]);
-          bool lt = true, gt = true, t1 = has_saddle, t2 = has_saddle;
+          box_muller(u01_23(r0.x), u01_23(r0.y), z[0], z[1]);
+          box_muller(u01_23(r0.z), u01_23(r0.w), z[2], z[3]);
+          box_muller(u01_23(r1.x), u01_23(r1.y), z[4], z[5]);
+          // x_v below every neighbour: the largest y_n = x_v - x_n is < 0;
+          // above every one: the smallest is > 0
+          float ymax = -kFar, ymin = kFar;
+          bool t1 = has_saddle, t2 = has_saddle;
 #pragma unroll
           for (int n = 1; n < 5; ++n) {
             if (n < nv) {
               float yv = D[n];
 #pragma unroll
               for (int b = 0; b <= n; ++b) yv = fmaf(M[n][b], z[b], yv);
-              lt &= yv < 0.f;
-              gt &= yv > 0.f;
-              // y = x_v - x_n: t1 wants x_v < x_n where the sign is +1
-              const float sy = ssg[n] * yv;
-              t1 &= sy < 0.f;
-              t2 &= sy > 0.f;
+              ymax = fmaxf(ymax, yv);
+              ymin = fminf(ymin, yv);
+              if constexpr (SADDLE) {
+                // y = x_v - x_n: t1 wants x_v < x_n where the sign is +1
+                const float sy = ssg[n] * yv;
+                t1 &= sy < 0.f;
+                t2 &= sy > 0.f;
+              }
             }
           }
           const bool valid = s < S;
-          cmin += __popc(__ballot_sync(0xffffffffu, valid && lt));
-          cmax += __popc(__ballot_sync(0xffffffffu, valid && gt));
-          if (f.cptypes & kSaddle) csad += __popc(__ballot_sync(0xffffffffu, valid && (t1 || t2)));
+          if constexpr (!SADDLE) {
+            cmin += __popc(__ballot_sync(0xffffffffu, valid && ymax < 0.f));
+            cmax += __popc(__ballot_sync(0xffffffffu, valid && ymin > 0.f));
+          } else {
+            csad += __popc(__ballot_sync(0xffffffffu, valid && (t1 || t2)));
+          }
         }
         pmin = zero_mm ? 0.f : (float)cmin / (float)S;
         pmax = zero_mm ? 0.f : (float)cmax / (float)S;
@@ -330,10 +339,16 @@ __global__ void __launch_bounds__(256) mvn_mc_kernel(Field f, int S, uint32_t k0
       }
     }
     if (lane == 0) {
-      if ((f.cptypes & kMin) && f.out_min) f.out_min[v] = pmin;
-      if ((f.cptypes & kMax) && f.out_max) f.out_max[v] = pmax;
-      if ((f.cptypes & kSaddle) && f.out_saddle) f.out_saddle[v] = psad;
-      if (f.status) f.status[v] = st;
+      // each instance writes its own outputs; the status once (by the
+      // minimum / maximum instance when it runs)
+      if constexpr (!SADDLE) {
+        if ((f.cptypes & kMin) && f.out_min) f.out_min[v] = pmin;
+        if ((f.cptypes & kMax) && f.out_max) f.out_max[v] = pmax;
+        if (f.status) f.status[v] = st;
+      } else {
+        if (f.out_saddle) f.out_saddle[v] = psad;
+        if (f.status && !(f.cptypes & (kMin | kMax))) f.status[v] = st;
+      }
     }
   }
 }
@@ -356,11 +371,24 @@ cudaError_t launch_mvn_mc(const Field &f, bool from_members, int samples, uint64
   long long b = (nvtx + 7) / 8;
   if (b > (1LL << 30)) b = 1LL << 30;
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-  if (from_members)
-    mvn_mc_kernel<true><<<(int)b, 256, 0, s>>>(f, samples, k0, k1, field_id);
-  else
-    mvn_mc_kernel<false><<<(int)b, 256, 0, s>>>(f, samples, k0, k1, field_id);
-  return cudaGetLastError();
+  // minimum / maximum and the saddle are separate instances, so that
+  // neither pays for the other's tests in the sample loop
+  cudaError_t e = cudaSuccess;
+  if (f.cptypes & (kMin | kMax)) {
+    if (from_members)
+      mvn_mc_kernel<true, false><<<(int)b, 256, 0, s>>>(f, samples, k0, k1, field_id);
+    else
+      mvn_mc_kernel<false, false><<<(int)b, 256, 0, s>>>(f, samples, k0, k1, field_id);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && (f.cptypes & kSaddle)) {
+    if (from_members)
+      mvn_mc_kernel<true, true><<<(int)b, 256, 0, s>>>(f, samples, k0, k1, field_id);
+    else
+      mvn_mc_kernel<false, true><<<(int)b, 256, 0, s>>>(f, samples, k0, k1, field_id);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 }  // namespace ucp
