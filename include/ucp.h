@@ -310,8 +310,10 @@ int ucp_params_from_error_bound(ucp_ctx *ctx, const float *decompressed, float e
  * of its neighbours; neighbour factors are differentiated under the
  * integral, the uniform centre adds the boundary terms of its moving support.
  * Point masses get zero derivatives for their own (a, b) / (m, w).  Uses
- * context workspace of 5*Q*H*W floats.  Not available for UCP_MVN_MC
- * (UCP_ERR_UNSUPPORTED). */
+ * context workspace: 160 floats per tile of 8 x 32 vertices for uniform
+ * and Epanechnikov, 80 * bins per tile plus partial blocks for histograms
+ * of at most 16 bins, 5*Q*H*W floats for more bins.  Not available for
+ * UCP_MVN_MC (UCP_ERR_UNSUPPORTED). */
 int ucp_backward(ucp_ctx *ctx, const float *params, int H, int W, const ucp_model_desc *desc,
                  int cptype, const float *weight, float *grad_params, ucp_stream stream);
 
@@ -324,9 +326,10 @@ int ucp_backward(ucp_ctx *ctx, const float *params, int H, int W, const ucp_mode
  * file-scope device array of ucp_backward_static_capacity() floats (16 MiB),
  * held by every device that loads the library until exit.  Inputs and
  * outputs are as for ucp_backward, on the CURRENT device.  The scratch must
- * fit the array, else UCP_ERR_SHAPE and nothing runs: 5 * 2 * H * W floats
- * for uniform and Epanechnikov (and 5 * bins * H * W for histograms of more
- * than 16 bins); for histograms of at most 16 bins 80 * bins floats per tile
+ * fit the array, else UCP_ERR_SHAPE and nothing runs: 160 floats per tile
+ * of 8 x 32 vertices for uniform and Epanechnikov (and 5 * bins * H * W for
+ * histograms of more than 16 bins); for histograms of at most 16 bins 80 *
+ * bins floats per tile
  * of 8 x 32 vertices plus one block of 1280 * bins floats (more blocks, up to
  * four per SM, when they fit; fewer make the call slower, not wrong) plus
  * 64 floats of block flags.  The first call on a device looks up the

@@ -1,12 +1,16 @@
 // backward.cu -- adjoint of L = sum_v W_v P_v with respect to every vertex's
 // model parameters (uniform (a, b), Epanechnikov (m, w), histogram masses).
 //
-// P_v depends on the parameters of v and of its in-grid neighbours.  Pass 1
-// (one thread per centre v) writes W_v dP_v/d(theta_u) for u = v and its four
-// neighbours into rows[slot][q][H][W] (slot 0 = v, 1..4 = e, n, w, s).  Pass 2
-// gathers, for every u, its own row and the rows its neighbours wrote about it
-// (u is the west neighbour of its east neighbour, and so on), in a fixed
-// order, so the result is deterministic and needs no atomics.
+// P_v depends on the parameters of v and of its in-grid neighbours.  Each
+// centre v gives the partials W_v dP_v/d(theta_u) for u = v and its four
+// neighbours (slot 0 = v, 1..4 = e, n, w, s); every u's gradient is its own
+// partial plus those its neighbours gave about it (u is the west neighbour
+// of its east neighbour, and so on), summed in a fixed order, so the result
+// is deterministic and needs no atomics.  The tile kernels (closed_adj_tile,
+// hist_adj_tile) sum the partials of each tile's inner pairs in the CTA and
+// hand the rest to the neighbouring tiles through a ring (hist_adj_fixup);
+// histograms of more than 16 bins keep partial rows rows[slot][q][H][W] and a
+// gather pass.
 //
 // Derivatives (exact, of the closed forms integrated in device.cuh):
 //   neighbour n: d/dtheta_n int pdf_1 prod G = int pdf_1 (dG_n/dtheta_n) prod_{m!=n} G_m
@@ -592,82 +596,6 @@ __device__ __noinline__ void hist_grad_vertex(const float *params, long long pla
     // bins entirely above the walk: the survival of the bin is 1 on [0, W1]
     for (int q = (n.j < 0 ? 0 : n.j + 1); q < n.B; ++q)
       rn[(long long)n.v.orig(q) * ostride] = wv * n.C;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// pass 1: partial rows per centre (uniform, Epanechnikov; histograms:
-// hist_partials_tile above)
-
-template <int MODEL>
-__global__ void __launch_bounds__(128) partials_kernel(Field f, int want_max,
-                                                       const float *__restrict__ weight,
-                                                       float *__restrict__ rows) {
-  const long long plane = f.plane;
-  static_assert(MODEL == kUniform || MODEL == kEpan, "histograms use hist_partials_tile");
-  const int Q = 2;
-  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < plane;
-       v += (long long)gridDim.x * blockDim.x) {
-    const int y = (int)(v / f.W), x = (int)(v % f.W);
-    bool present[4];
-    long long ni[4];
-    int k = 0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int yy = y + kDy[i], xx = x + kDx[i];
-      present[i] = (yy >= 0 && yy < f.H && xx >= 0 && xx < f.W);
-      ni[i] = present[i] ? (long long)yy * f.W + xx : v;
-      k += present[i];
-    }
-    // validity of every participant
-    bool bad = false;
-    for (int t = 0; t < 5; ++t) {
-      if (t > 0 && !present[t - 1]) continue;
-      const long long u = t == 0 ? v : ni[t - 1];
-      const float a = f.params[u], b = f.params[plane + u];
-      if (!isfinite(a) || !isfinite(b)) bad = true;
-      else if (MODEL == kEpan ? (b < 0.f) : (a > b)) bad = true;
-    }
-    const float wv = weight[v];
-    if (bad || (f.boundary == 1 && k < 4)) {
-      const float fill = bad ? qnan_b() : 0.f;
-      for (int s = 0; s < 5; ++s)
-        for (int q = 0; q < Q; ++q) rows[((long long)s * Q + q) * plane + v] = fill;
-      continue;
-    }
-    if (MODEL == kUniform) {
-      float an[4], bn[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        an[i] = f.params[ni[i]];
-        bn[i] = f.params[plane + ni[i]];
-      }
-      UniGrad g;
-      uniform_grad_vertex(f.params[v], f.params[plane + v], an, bn, present, want_max != 0, g);
-      rows[v] = wv * g.ga;
-      rows[plane + v] = wv * g.gb;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        rows[((long long)(1 + i) * 2) * plane + v] = wv * g.na[i];
-        rows[((long long)(1 + i) * 2 + 1) * plane + v] = wv * g.nb[i];
-      }
-    } else if (MODEL == kEpan) {
-      float mn[4], wn[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        mn[i] = f.params[ni[i]];
-        wn[i] = f.params[plane + ni[i]];
-      }
-      EpanGrad g;
-      epan_grad_vertex(f.params[v], f.params[plane + v], mn, wn, present, want_max != 0, g);
-      rows[v] = wv * g.gm;
-      rows[plane + v] = wv * g.gw;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        rows[((long long)(1 + i) * 2) * plane + v] = wv * g.nm[i];
-        rows[((long long)(1 + i) * 2 + 1) * plane + v] = wv * g.nw[i];
-      }
-    }
   }
 }
 
@@ -1301,6 +1229,123 @@ __global__ void __launch_bounds__(256) hist_adj_fixup(Field f, int tiles_x, int 
   }
 }
 
+// Uniform and Epanechnikov adjoint, tiled as hist_adj_tile: one CTA per
+// 8 x 32 tile, one centre per thread.  A centre's ten weighted partials
+// (slot 0 the centre, 1 + i neighbour i; parameter q of two) go to shared
+// memory; after the tile's centres are done each thread sums, for its own
+// vertex u, u's partials and those its neighbours inside the tile wrote
+// about u, in the fixed order own, e, n, w, s, and writes grad.  The
+// partials about vertices of other tiles go to the tile's ring (80 x 2
+// floats, the layout of hist_adj_tile's ring), which hist_adj_fixup adds to
+// them afterwards.  No global scratch besides the ring, no atomics.
+template <int MODEL>
+__global__ void __launch_bounds__(NTHREADS) closed_adj_tile(Field f, int tiles_x, int want_max,
+                                                            const float *__restrict__ weight,
+                                                            float *__restrict__ ring,
+                                                            float *__restrict__ grad) {
+  static_assert(MODEL == kUniform || MODEL == kEpan, "two parameters per vertex");
+  constexpr int TY = kAdjTY, TX = 32, TV = kAdjTV, Q = 2;
+  __shared__ float sc[5 * Q * TV];
+  const long long plane = f.plane;
+  const int tile = blockIdx.x;
+  const int ty0 = f.y0 + (tile / tiles_x) * TY, tx0 = (tile % tiles_x) * TX;
+  const int v = threadIdx.x, lr = v / TX, lc = v % TX;
+  const int y = ty0 + lr, x = tx0 + lc;
+  const bool live = y < f.y1 && x < f.W;
+  if (live) {
+    const long long vi = (long long)y * f.W + x;
+    bool present[4];
+    long long ni[4];
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int yy = y + kDy[i], xx = x + kDx[i];
+      present[i] = (yy >= 0 && yy < f.H && xx >= 0 && xx < f.W);
+      ni[i] = present[i] ? (long long)yy * f.W + xx : vi;
+      k += present[i];
+    }
+    // validity of every participant
+    bool bad = false;
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+      if (t > 0 && !present[t - 1]) continue;
+      const long long u = t == 0 ? vi : ni[t - 1];
+      const float a = f.params[u], b = f.params[plane + u];
+      if (!isfinite(a) || !isfinite(b)) bad = true;
+      else if (MODEL == kEpan ? (b < 0.f) : (a > b)) bad = true;
+    }
+    float g[5 * Q];
+    if (bad || (f.boundary == 1 && k < 4)) {
+      const float fill = bad ? qnan_b() : 0.f;
+#pragma unroll
+      for (int t = 0; t < 5 * Q; ++t) g[t] = fill;
+    } else {
+      const float wv = weight[vi];
+      float an[4], bn[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        an[i] = f.params[ni[i]];
+        bn[i] = f.params[plane + ni[i]];
+      }
+      if constexpr (MODEL == kUniform) {
+        UniGrad r;
+        uniform_grad_vertex(f.params[vi], f.params[plane + vi], an, bn, present, want_max != 0,
+                            r);
+        g[0] = wv * r.ga;
+        g[1] = wv * r.gb;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          g[2 + 2 * i] = wv * r.na[i];
+          g[3 + 2 * i] = wv * r.nb[i];
+        }
+      } else {
+        EpanGrad r;
+        epan_grad_vertex(f.params[vi], f.params[plane + vi], an, bn, present, want_max != 0, r);
+        g[0] = wv * r.gm;
+        g[1] = wv * r.gw;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          g[2 + 2 * i] = wv * r.nm[i];
+          g[3 + 2 * i] = wv * r.nw[i];
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 5 * Q; ++t) sc[t * TV + v] = g[t];
+  }
+  __syncthreads();
+  if (!live) return;
+  // gather: vertex u = v of the tile
+  const long long gi = (long long)y * f.W + x;
+  bool in_tile[4];
+  int vn[4];
+#pragma unroll
+  for (int d = 0; d < 4; ++d) {
+    const int yy = y + kDy[d], xx = x + kDx[d];
+    const int rr = lr + kDy[d], cc = lc + kDx[d];
+    in_tile[d] = yy >= 0 && yy < f.y1 && xx >= 0 && xx < f.W && rr >= 0 && rr < TY && cc >= 0 &&
+                 cc < TX;
+    vn[d] = rr * TX + cc;
+  }
+  float *ring_t = ring + (long long)tile * kAdjRing * Q;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    float acc = sc[q * TV + v];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      // u is the opposite-direction neighbour of v = u + dir d
+      const int opp = (d + 2) & 3;
+      if (in_tile[d]) acc += sc[((1 + opp) * Q + q) * TV + vn[d]];
+    }
+    grad[(long long)q * plane + gi] = acc;
+    // this centre's partials about vertices of other tiles
+    if (lr == 0) ring_t[q * 32 + lc] = sc[((1 + 1) * Q + q) * TV + v];               // n
+    if (lr == TY - 1) ring_t[(Q + q) * 32 + lc] = sc[((1 + 3) * Q + q) * TV + v];    // s
+    if (lc == 0) ring_t[64 * Q + q * 8 + lr] = sc[((1 + 2) * Q + q) * TV + v];       // w
+    if (lc == TX - 1) ring_t[72 * Q + q * 8 + lr] = sc[((1 + 0) * Q + q) * TV + v];  // e
+  }
+}
+
 // shared-memory bytes of hist_adj_tile at B bins
 static size_t hist_adj_smem(int B) {
   constexpr int HALO = 10 * 34;
@@ -1348,6 +1393,10 @@ static size_t adj_layout(long long nt, int B, long long nslots, long long *flags
 }
 
 size_t backward_scratch_floats(const Field &f, int model, int ctas) {
+  if (model == kUniform || model == kEpan) {  // the tiles' rings
+    int tx;
+    return (size_t)adj_tiles(f, &tx) * kAdjRing * 2;
+  }
   if (model == kHist && f.B <= 16) {
     int tx;
     const long long nt = adj_tiles(f, &tx);
@@ -1365,9 +1414,29 @@ cudaError_t launch_backward(const Field &f, int model, int cptype, const float *
   long long b = (f.plane + 127) / 128;
   if (b > (1LL << 30)) b = 1LL << 30;
   const int want_max = cptype == 2;
+  if (model == kUniform || model == kEpan) {
+    // tiled, partials in shared memory; ring partials after the tiles
+    int tiles_x;
+    const long long nt = adj_tiles(f, &tiles_x);
+    if (nt > 0x7fffffffLL) return cudaErrorInvalidValue;
+    if (nt == 0) return cudaSuccess;
+    if ((size_t)nt * kAdjRing * 2 > rows_floats) return cudaErrorInvalidValue;
+    if (model == kUniform)
+      closed_adj_tile<kUniform><<<(int)nt, NTHREADS, 0, s>>>(f, tiles_x, want_max, weight, rows,
+                                                             grad);
+    else
+      closed_adj_tile<kEpan><<<(int)nt, NTHREADS, 0, s>>>(f, tiles_x, want_max, weight, rows,
+                                                          grad);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    Field g = f;
+    g.B = 2;  // the ring's parameters per vertex
+    const long long fx = (nt * (2 * 32 + 2 * (kAdjTY - 2)) + 255) / 256;
+    hist_adj_fixup<<<(int)std::min<long long>(fx, 1LL << 30), 256, 0, s>>>(g, tiles_x, (int)nt,
+                                                                          rows, grad);
+    return cudaGetLastError();
+  }
   switch (model) {
-    case kUniform: partials_kernel<kUniform><<<(int)b, 128, 0, s>>>(f, want_max, weight, rows); break;
-    case kEpan: partials_kernel<kEpan><<<(int)b, 128, 0, s>>>(f, want_max, weight, rows); break;
     case kHist: {
       if (f.B <= 16) {
         // per-bin rows, 8 x 32 tiles, two CTAs per SM; partials of a tile in

@@ -4,8 +4,10 @@
 // device memory budget, or a latency-critical path on which cudaMalloc /
 // cudaFree, which may synchronise the whole device, are not acceptable).
 //
-// The partial rows that ucp_backward keeps in context workspace live here in
-// a file-scope device array of fixed size instead.  Every device that loads
+// The adjoint scratch that ucp_backward keeps in context workspace (the
+// tiles' rings, partial blocks and, for histograms of more than 16 bins,
+// partial rows) lives here in a file-scope device array of fixed size
+// instead.  Every device that loads
 // this library holds the array until the process exits.  Host code may not
 // use the array's name as a device address (in host code it names a host
 // stand-in), so the device address is looked up once per device with
@@ -32,10 +34,10 @@ using namespace ucp;
 
 namespace {
 
-// 16 MiB of adjoint scratch: 5 * Q * H * W floats of partial rows (Q = 2 for
-// uniform / Epanechnikov, Q = bins for histograms of more than 16 bins); for
-// histograms of at most 16 bins the block flags, the ring (80 * B floats per
-// 8 x 32 tile) and at least one partial block of 1280 * B floats.
+// 16 MiB of adjoint scratch: for uniform / Epanechnikov the rings (160
+// floats per 8 x 32 tile); for histograms of at most 16 bins the block
+// flags, the ring (80 * B floats per tile) and at least one partial block of
+// 1280 * B floats; for more bins 5 * B * H * W floats of partial rows.
 constexpr size_t kStaticRowsFloats = size_t(4) << 20;
 
 __device__ __align__(256) float g_static_rows[kStaticRowsFloats];

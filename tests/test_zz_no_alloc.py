@@ -49,18 +49,18 @@ def test_static_adjoint_matches_context_adjoint(ucp, model, mid, bins):
 
 def test_static_adjoint_rejects_oversize(ucp):
     """Shapes whose scratch exceeds the fixed array are refused before any
-    launch: 5 * 2 * H * W floats for uniform / Epanechnikov; for histograms
-    of at most 16 bins 80 * B floats per 8 x 32 tile plus 1280 * B."""
+    launch: 160 floats per 8 x 32 tile for uniform / Epanechnikov; for
+    histograms of at most 16 bins 80 * B floats per tile plus 1280 * B."""
     cap = ucp.ucp_backward_static_capacity()
     assert cap == 4 << 20
     cases = [("histogram", 16, 8 * 60, 32 * 60),       # 3600 tiles: ring alone too large
-             ("uniform", 8, 700, 700)]                  # 4.9 M floats of partial rows
+             ("uniform", 8, 8 * 160, 32 * 168)]         # 26880 tiles: 4.3 M floats of rings
     for model, bins, Hh, Ww in cases:
         desc = ucp.make_desc(model, bins=bins)
         P = 2 + bins if model == "histogram" else 2
         Q = bins if model == "histogram" else 2
-        assert (model != "histogram" or
-                ((Hh + 7) // 8) * ((Ww + 31) // 32) * 80 * bins + 1280 * bins > cap)
+        tiles = ((Hh + 7) // 8) * ((Ww + 31) // 32)
+        assert (tiles * 80 * bins + 1280 * bins if model == "histogram" else tiles * 160) > cap
         p = torch.zeros((P, Hh, Ww), device="cuda")
         W = torch.zeros((Hh, Ww), device="cuda")
         g = torch.zeros((Q, Hh, Ww), device="cuda")
