@@ -561,9 +561,10 @@ def e2e_headline(torch, ucp, ctx, ens_np, args):
     """Same metric end to end through the C ABI with host buffers: every step
     is one ucp_probability_host_models call on pinned host memory -- the
     members copied to the device once, in row strips overlapped with the
-    three models' kernels, and the six probability fields copied back -- so
-    the copies are inside the timed region (wall clock; the call returns
-    after its streams are synchronised)."""
+    fused kernel, which writes the six probability fields into the pinned
+    output arrays over the host link -- so both transfers are inside the
+    timed region (wall clock; the call returns after its streams are
+    synchronised)."""
     ens_h = torch.from_numpy(ens_np).pin_memory()
     descs = [ucp.make_desc(m, bins=b or 8) for m, b in MODELS2]
     outs_min = [torch.empty((H2, W2)).pin_memory() for _ in MODELS2]
@@ -584,7 +585,8 @@ def e2e_headline(torch, ucp, ctx, ens_np, args):
             "h2d_bytes_per_step": ens_np.nbytes,
             "d2h_bytes_per_step": len(MODELS2) * 2 * H2 * W2 * 4,
             "api": "ucp_probability_host_models on pinned host arrays (members copied once "
-                   "per step in row strips overlapped with the kernels; six fields back)"}
+                   "per step in row strips overlapped with the fused kernel, which writes the "
+                   "six fields into the pinned output arrays)"}
 
 
 def other_rows(torch, ucp, ctx, dev, args, flush, peaks):
