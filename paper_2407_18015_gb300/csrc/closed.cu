@@ -152,8 +152,19 @@ __global__ void __launch_bounds__(NTHREADS, (TileOcc<MODEL, RB>::value))
 // asynchronous copies -- for per-bin-row histograms the same room then
 // takes the rows, once the box is no longer read -- then the parameter
 // tile, then the mbarrier.
+// resident CTAs per SM the register budget of a box-staged tile kernel is
+// set for: the model's, at most four for the Epanechnikov saddle (its
+// mixed-factor integrals in packed node pairs need more registers than the
+// minimum / maximum: at five CTAs they spilled)
+template <int MODEL, bool SADDLE, int RB>
+struct TmaOcc {
+  static constexpr int value = SADDLE && MODEL == kEpan && TileOcc<MODEL, RB>::value > 4
+                                   ? 4
+                                   : TileOcc<MODEL, RB>::value;
+};
+
 template <int MODEL, bool SADDLE, int TYm, int RB, bool ASYNC>
-__global__ void __launch_bounds__(NTHREADS, (TileOcc<MODEL, RB>::value))
+__global__ void __launch_bounds__(NTHREADS, (TmaOcc<MODEL, SADDLE, RB>::value))
     tile_kernel_tma(Field f, int tiles_x, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(128) float smem[];
   const int tile = blockIdx.x;

@@ -978,23 +978,37 @@ __device__ __forceinline__ float epan_mixed(EpanParams c, const EpanParams *nb, 
   const float x[6] = {L, t[0], t[1], t[2], t[3], R};
   const float iw1 = frcp(w1), c1 = 0.75f * iw1;
   Kahan acc;
+  // the 8 nodes in the symmetric pairs (-x_k, x_k), which share the weight
+  // w_k: one pair per float2 (packed FP32 instructions, the same operations
+  // per node as the scalar form)
+  const float2 one2 = make_float2(1.f, 1.f), two2 = make_float2(2.f, 2.f);
 #pragma unroll
   for (int j = 0; j <= 4; ++j) {
     const float half = 0.5f * (x[j + 1] - x[j]), mid = 0.5f * (x[j] + x[j + 1]);
-    float sacc = 0.f;
+    float2 s2 = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const float xi = (q < 4) ? -kGLx[3 - q] : kGLx[q - 4];
-      const float wi = (q < 4) ? kGLw[3 - q] : kGLw[q - 4];
-      const float xx = fmaf(half, xi, mid);
-      const float u1 = xx * iw1;
-      float f = c1 * fmaxf(fmaf(-u1, u1, 1.f), 0.f);
+    for (int k = 0; k < 4; ++k) {
+      const float2 xx = __ffma2_rn(make_float2(half, half), make_float2(-kGLx[k], kGLx[k]),
+                                   make_float2(mid, mid));
+      const float2 u1 = __fmul2_rn(xx, make_float2(iw1, iw1));
+      const float2 g = __ffma2_rn(make_float2(-u1.x, -u1.y), u1, one2);
+      float2 f = __fmul2_rn(make_float2(c1, c1), make_float2(fmaxf(g.x, 0.f), fmaxf(g.y, 0.f)));
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-        if (sgn[i] != 0.f) f *= epan_surv(sgn[i] * (xx - d[i]) * iw[i]);
-      sacc = fmaf(wi, f, sacc);
+      for (int i = 0; i < 4; ++i) {
+        if (sgn[i] == 0.f) continue;
+        // epan_surv of sgn (x - d) / w at both nodes
+        float2 u = __fmul2_rn(__fmul2_rn(make_float2(sgn[i], sgn[i]),
+                                         __fadd2_rn(xx, make_float2(-d[i], -d[i]))),
+                              make_float2(iw[i], iw[i]));
+        u = make_float2(fminf(fmaxf(u.x, -1.f), 1.f), fminf(fmaxf(u.y, -1.f), 1.f));
+        const float2 qq = __fadd2_rn(one2, make_float2(-u.x, -u.y));
+        const float2 sv = __fmul2_rn(__fmul2_rn(__fmul2_rn(make_float2(0.25f, 0.25f), qq), qq),
+                                     __fadd2_rn(two2, u));
+        f = __fmul2_rn(f, sv);
+      }
+      s2 = __ffma2_rn(make_float2(kGLw[k], kGLw[k]), f, s2);
     }
-    acc.add(sacc * half);
+    acc.add((s2.x + s2.y) * half);
   }
   return acc.get();
 }
