@@ -182,7 +182,71 @@ __device__ __forceinline__ void uniform_vertex_k(UniParams c, const UniParams *n
 
 // ---------------------------------------------------------------------------
 // Epanechnikov: with K neighbours the integrand has degree <= 2 + 3K = 26 on
-// a piece; the 16-point Gauss-Legendre rule is exact to degree 31
+// a piece; each piece takes the smallest rule of {2, 3, 5, 6, 8, 16} nodes
+// that is exact for its degree (the 16-point rule: to degree 31)
+
+// Node / weight q (ascending) of the NG-point Gauss-Legendre rule, NG in
+// {2, 3, 5, 6, 8, 16}.
+template <int NG>
+__device__ __forceinline__ float sgl_x(int q) {
+  if constexpr (NG == 16) return q < 8 ? -kGL16x[7 - q] : kGL16x[q - 8];
+  else return gl_x<NG>(q);
+}
+template <int NG>
+__device__ __forceinline__ float sgl_w(int q) {
+  if constexpr (NG == 16) return q < 8 ? kGL16w[7 - q] : kGL16w[q - 8];
+  else return gl_w<NG>(q);
+}
+
+// Piece J of epan_side_k: the centre density (degree 2) times the J started
+// survivals (degree 3 each), degree 2 + 3J; the n-point rule with 2n - 1 >=
+// 2 + 3J is exact: n = 2, 3, 5, 6, 8, then 16 (J = 5..8 need 9..14).
+template <int J>
+struct StencilNodes {
+  static constexpr int value = J <= 4 ? EpanNodes<J>::value : 16;
+};
+template <int J, int K>
+__device__ __forceinline__ void epan_pieces_k(const float *x, const float (*pay)[kMaxK], float iw1,
+                                              float c1, Kahan &acc) {
+  constexpr int NG = StencilNodes<J>::value;
+  const float x0 = x[J], x1 = x[J + 1];
+  const float half = 0.5f * (x1 - x0), mid = 0.5f * (x0 + x1);
+  // nodes in pairs, one per half of a float2 (packed FP32 instructions)
+  const float2 one2 = make_float2(1.f, 1.f);
+  float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int q = 0; q + 1 < NG; q += 2) {
+    const float2 xx = __ffma2_rn(make_float2(half, half),
+                                 make_float2(sgl_x<NG>(q), sgl_x<NG>(q + 1)), make_float2(mid, mid));
+    const float2 u1 = __fmul2_rn(xx, make_float2(iw1, iw1));
+    const float2 g = __ffma2_rn(make_float2(-u1.x, -u1.y), u1, one2);
+    float2 f = __fmul2_rn(make_float2(c1, c1), make_float2(fmaxf(g.x, 0.f), fmaxf(g.y, 0.f)));
+#pragma unroll
+    for (int i = 0; i < J; ++i) {
+      // the started factors' arguments lie in [-1, 1] on this piece (as in
+      // epan_pieces): epan_surv without its clamp
+      const float2 u = __fmul2_rn(__fadd2_rn(xx, make_float2(-pay[0][i], -pay[0][i])),
+                                  make_float2(pay[1][i], pay[1][i]));
+      const float2 qq = __fadd2_rn(one2, make_float2(-u.x, -u.y));
+      const float2 sv = __fmul2_rn(__fmul2_rn(make_float2(0.25f, 0.25f), __fmul2_rn(qq, qq)),
+                                   __fadd2_rn(make_float2(2.f, 2.f), u));
+      f = __fmul2_rn(f, sv);
+    }
+    s2 = __ffma2_rn(make_float2(sgl_w<NG>(q), sgl_w<NG>(q + 1)), f, s2);
+  }
+  float sum = s2.x + s2.y;
+  if constexpr (NG & 1) {
+    constexpr int q = NG - 1;
+    const float xx = fmaf(half, sgl_x<NG>(q), mid);
+    const float u1 = xx * iw1;
+    float f = c1 * fmaxf(fmaf(-u1, u1, 1.f), 0.f);
+#pragma unroll
+    for (int i = 0; i < J; ++i) f *= epan_surv((xx - pay[0][i]) * pay[1][i]);
+    sum = fmaf(sgl_w<NG>(q), f, sum);
+  }
+  acc.add(sum * half);
+  if constexpr (J < K) epan_pieces_k<J + 1, K>(x, pay, iw1, c1, acc);
+}
 
 // epan_side with K factors (same frame and arguments)
 template <int K>
@@ -205,23 +269,7 @@ __device__ __forceinline__ float epan_side_k(float w1, float L, float R, const f
   const float iw1 = frcp(w1);
   const float c1 = 0.75f * iw1;
   Kahan acc;
-#pragma unroll
-  for (int j = 0; j <= K; ++j) {
-    const float x0 = x[j], x1 = x[j + 1];
-    const float half = 0.5f * (x1 - x0), mid = 0.5f * (x0 + x1);
-    float s = 0.f;
-    for (int q = 0; q < 16; ++q) {
-      const float xi = (q < 8) ? -kGL16x[7 - q] : kGL16x[q - 8];
-      const float wi = (q < 8) ? kGL16w[7 - q] : kGL16w[q - 8];
-      const float xx = fmaf(half, xi, mid);
-      const float u1 = xx * iw1;
-      float f = c1 * fmaxf(fmaf(-u1, u1, 1.f), 0.f);
-#pragma unroll
-      for (int i = 0; i < j; ++i) f *= epan_surv((xx - pay[0][i]) * pay[1][i]);
-      s = fmaf(wi, f, s);
-    }
-    acc.add(s * half);
-  }
+  epan_pieces_k<0, K>(x, pay, iw1, c1, acc);
   return acc.get();
 }
 
