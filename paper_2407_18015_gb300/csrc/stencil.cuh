@@ -53,6 +53,26 @@ __device__ __forceinline__ float bern_mean_k(const float *L, const float *R) {
   return s;
 }
 
+// bern_mean_k of two products at once, one per half of a float2 (the same
+// operations per half, packed FP32 instructions)
+template <int K>
+__device__ __forceinline__ float2 bern_mean_k_x2(const float2 *L, const float2 *R) {
+  float2 e[K + 1];
+  e[0] = L[0];
+  e[1] = R[0];
+#pragma unroll
+  for (int i = 1; i < K; ++i) {
+    e[i + 1] = __fmul2_rn(e[i], R[i]);
+#pragma unroll
+    for (int j = i; j >= 1; --j) e[j] = __ffma2_rn(e[j - 1], R[i], __fmul2_rn(e[j], L[i]));
+    e[0] = __fmul2_rn(e[0], L[i]);
+  }
+  float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j <= K; ++j) s = __ffma2_rn(e[j], make_float2(bern_w(K, j), bern_w(K, j)), s);
+  return s;
+}
+
 // ascending sort of K keys with NP payload rows (odd-even transposition)
 template <int NP>
 __device__ __forceinline__ void cswap_k(float *k, float (*p)[kMaxK], int a, int b) {
@@ -376,13 +396,15 @@ __device__ __forceinline__ void hist_walk_k(const float *tab, long long crow, in
   float sc = __ldg(tab + crow), scn = __ldg(tab + crow + 1);
   float dens = (sc - scn) * ih1;
   float nxc = B > 1 ? h1 : W1;
-  float Gl[K], Fl[K];
+  // (G, F) of each factor at the piece's left and right ends
+  float2 Pl[K];
 #pragma unroll
   for (int i = 0; i < K; ++i) {
-    Gl[i] = nw[i].G(0.f);
-    Fl[i] = T[i] - Gl[i];
+    const float g = nw[i].G(0.f);
+    Pl[i] = make_float2(g, T[i] - g);
   }
-  float amin = 0.f, amax = 0.f;
+  float2 acc = make_float2(0.f, 0.f);
+  (void)want;
   float x0 = 0.f;
   const int max_steps = (K + 1) * (B + 2) + 4;
   for (int step = 0; step < max_steps && x0 < W1; ++step) {
@@ -390,20 +412,19 @@ __device__ __forceinline__ void hist_walk_k(const float *tab, long long crow, in
 #pragma unroll
     for (int i = 0; i < K; ++i) x1 = fminf(x1, nw[i].nx);
     x1 = fmaxf(x1, x0);
-    float Gr[K], Fr[K];
+    float2 Pr[K];
 #pragma unroll
     for (int i = 0; i < K; ++i) {
-      Gr[i] = nw[i].G(x1);
-      Fr[i] = T[i] - Gr[i];
+      const float g = nw[i].G(x1);
+      Pr[i] = make_float2(g, T[i] - g);
     }
     const float wgt = (x1 - x0) * dens;
-    if (want & kMin) amin = fmaf(wgt, bern_mean_k<K>(Gl, Gr), amin);
-    if (want & kMax) amax = fmaf(wgt, bern_mean_k<K>(Fl, Fr), amax);
+    acc = __ffma2_rn(make_float2(wgt, wgt), bern_mean_k_x2<K>(Pl, Pr), acc);
 #pragma unroll
     for (int i = 0; i < K; ++i) {
       const bool c = nw[i].step(tab, x1, Bf);
-      Gl[i] = c ? nw[i].s : Gr[i];
-      Fl[i] = T[i] - Gl[i];
+      const float g = c ? nw[i].s : Pr[i].x;
+      Pl[i] = make_float2(g, T[i] - g);
     }
     {
       const bool c = nxc <= x1;
@@ -417,8 +438,8 @@ __device__ __forceinline__ void hist_walk_k(const float *tab, long long crow, in
     }
     x0 = x1;
   }
-  pmin = fmaxf(amin, 0.f);
-  pmax = fmaxf(amax, 0.f);
+  pmin = fmaxf(acc.x, 0.f);
+  pmax = fmaxf(acc.y, 0.f);
 }
 
 // survival and CDF of a histogram neighbour (tail-table row) at a point v
