@@ -193,13 +193,13 @@ ADJ_EPAN_FLOPS_PER_VERTEX = 2 * EPAN_FLOPS_PER_VERTEX_TYPE
 # three-model kernel) and of each model's own kernel, from the ncu captures
 # summarised in profiles/; None once a kernel has changed since its counters
 # were taken
-TRAFFIC_BYTES = {"fused": 95689472, "uniform": 88039424, "epanechnikov": 85209088,
-                 "histogram": 85687552, "hist_adjoint_16": 652988928}
+TRAFFIC_BYTES = {"fused": 93154816, "uniform": 88159744, "epanechnikov": 84930816,
+                 "histogram": 85625344, "hist_adjoint_16": 652988928}
 # warp instructions per launch of the same kernels (ncu smsp__inst_executed.sum,
 # profiles/instructions_bench_headline_1024x1024x20.md): the issue-rate
 # fraction reported beside the FP32 / HBM one; None once a kernel changed
-ISSUE_WARP_INSTR = {"fused": 206773693, "uniform": 23586076, "epanechnikov": 62221552,
-                    "histogram": 141878590}
+ISSUE_WARP_INSTR = {"fused": 206773693, "uniform": 23585236, "epanechnikov": 62221552,
+                    "histogram": 141878595}
 ISSUE_SOURCE = "profiles/instructions_bench_headline_1024x1024x20.md"
 
 
@@ -216,10 +216,10 @@ def issue_block(key, ms, mhz):
             "unit": "G warp instructions/s", "frac": ach / peak, "source": ISSUE_SOURCE}
 
 
-TRAFFIC_SOURCE = {"fused": "profiles/fused_kernel_1024x1024x20.md",
-                  "uniform": "profiles/fused_kernel_1024x1024x20.md",
-                  "epanechnikov": "profiles/fused_kernel_1024x1024x20.md",
-                  "histogram": "profiles/fused_kernel_1024x1024x20.md",
+TRAFFIC_SOURCE = {"fused": "profiles/instructions_bench_headline_1024x1024x20.md",
+                  "uniform": "profiles/instructions_bench_headline_1024x1024x20.md",
+                  "epanechnikov": "profiles/instructions_bench_headline_1024x1024x20.md",
+                  "histogram": "profiles/instructions_bench_headline_1024x1024x20.md",
                   "hist_adjoint_16": "profiles/adjoint_hist16_2048x2048x50.md"}
 
 
