@@ -1154,20 +1154,36 @@ __global__ void __launch_bounds__(NTHREADS, 2)
       vn[d] = rr * TX + cc;
     }
     float *ring_t = ring + (long long)tile * kAdjRing * B;
-    for (int q = 0; q < B; ++q) {
-      float acc = sc[q * TV + v];
+    // four bins at a time: every read of the block first (independent L2
+    // reads in flight together), then the sums and stores
+    for (int q0 = 0; q0 < B; q0 += 4) {
+      float own[4], nbv[4][4], rv[4][4];
 #pragma unroll
-      for (int d = 0; d < 4; ++d) {
-        // u is the opposite-direction neighbour of v = u + dir d
-        const int opp = (d + 2) & 3;
-        if (in_tile[d]) acc += sc[((1 + opp) * B + q) * TV + vn[d]];
+      for (int j = 0; j < 4; ++j) {
+        const int q = min(q0 + j, B - 1);
+        own[j] = sc[q * TV + v];
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+          const int opp = (d + 2) & 3;
+          nbv[j][d] = in_tile[d] ? sc[((1 + opp) * B + q) * TV + vn[d]] : 0.f;
+          rv[j][d] = sc[((1 + d) * B + q) * TV + v];
+        }
       }
-      grad[(long long)q * plane + gi] = acc;
-      // this centre's partials about vertices of other tiles
-      if (lr == 0) ring_t[q * 32 + lc] = sc[((1 + 1) * B + q) * TV + v];               // n
-      if (lr == TY - 1) ring_t[(B + q) * 32 + lc] = sc[((1 + 3) * B + q) * TV + v];    // s
-      if (lc == 0) ring_t[64 * B + q * 8 + lr] = sc[((1 + 2) * B + q) * TV + v];       // w
-      if (lc == TX - 1) ring_t[72 * B + q * 8 + lr] = sc[((1 + 0) * B + q) * TV + v];  // e
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int q = q0 + j;
+        if (q >= B) break;
+        float acc = own[j];
+#pragma unroll
+        for (int d = 0; d < 4; ++d)
+          if (in_tile[d]) acc += nbv[j][d];
+        grad[(long long)q * plane + gi] = acc;
+        // this centre's partials about vertices of other tiles
+        if (lr == 0) ring_t[q * 32 + lc] = rv[j][1];               // n
+        if (lr == TY - 1) ring_t[(B + q) * 32 + lc] = rv[j][3];    // s
+        if (lc == 0) ring_t[64 * B + q * 8 + lr] = rv[j][2];       // w
+        if (lc == TX - 1) ring_t[72 * B + q * 8 + lr] = rv[j][0];  // e
+      }
     }
   }
   // every read of the block is done: release it
