@@ -113,6 +113,70 @@ __global__ void __launch_bounds__(256) fit_kernel(Field f) {
   }
 }
 
+// Histogram fit of at most 16 bins and MAXN members in one pass over the
+// members: a thread holds its vertex's members in registers (every load in
+// flight at once), takes their minimum and maximum (NaN-propagating: a
+// non-finite member shows in them) and bins them from the registers, where
+// fit_kernel reads them twice.  The same values as fit_kernel: the same
+// bins, counters and count / N table.
+template <int MAXN>
+__global__ void __launch_bounds__(128) fit_hist_regs(Field f) {
+  __shared__ float mtab[MAXN + 1];
+  const int N = f.N, B = f.B;
+  for (int c = threadIdx.x; c <= N; c += blockDim.x) mtab[c] = __fdiv_rn((float)c, (float)N);
+  __syncthreads();
+  const long long plane = f.plane;
+  float *out = const_cast<float *>(f.params);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < plane;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float *p = f.ens + i;
+    float v[MAXN];
+    v[0] = __ldg(p);
+#pragma unroll
+    for (int k = 1; k < MAXN; ++k) v[k] = k < N ? __ldg(p + (long long)k * plane) : v[0];
+    // members past N repeat member 0: they change neither minimum nor maximum
+    float mn = v[0], mx = v[0];
+#pragma unroll
+    for (int k = 1; k + 1 < MAXN; k += 2) {
+      mn = fmin3_nan(mn, v[k], v[k + 1]);
+      mx = fmax3_nan(mx, v[k], v[k + 1]);
+    }
+    if constexpr ((MAXN & 1) == 0) {
+      mn = fmin_nan(mn, v[MAXN - 1]);
+      mx = fmax_nan(mx, v[MAXN - 1]);
+    }
+    uint8_t st = 0;
+    if (!(isfinite(mn) && isfinite(mx))) {
+      for (int q = 0; q < 2 + B; ++q) out[q * plane + i] = __int_as_float(0x7fc00000);
+      st |= V_NONFINITE;
+    } else {
+      unsigned long long c0 = 0ull, c1 = 0ull;
+      if (mn == mx) {
+        c0 = (unsigned long long)N;
+        st |= V_DEGENERATE;
+      } else {
+        const float sc = __fdiv_rn((float)B, __fsub_rn(mx, mn));
+#pragma unroll
+        for (int k = 0; k < MAXN; ++k) {
+          if (k < N) {
+            const int j = hist_bin_nonneg(v[k], mn, sc, B);
+            const unsigned long long inc = 1ull << ((j & 7) << 3);
+            c0 += j < 8 ? inc : 0ull;
+            c1 += j < 8 ? 0ull : inc;
+          }
+        }
+      }
+      out[i] = mn;
+      out[plane + i] = mx;
+      for (int q = 0; q < B; ++q) {
+        const unsigned c = (unsigned)((q < 8 ? c0 : c1) >> ((q & 7) << 3)) & 255u;
+        out[(2 + q) * plane + i] = mtab[c];
+      }
+    }
+    if (f.status) f.status[i] = st;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // tile kernel
 
@@ -209,7 +273,15 @@ cudaError_t launch_fit(const Field &f, int model, cudaStream_t s) {
     case kEpan: fit_kernel<kEpan><<<g, 256, 0, s>>>(f); break;
     case kGauss: fit_kernel<kGauss><<<g, 256, 0, s>>>(f); break;
     case kHist:
-    case kSemi: fit_kernel<kHist><<<g, 256, 0, s>>>(f); break;
+    case kSemi:
+      if (f.B <= 16 && f.N >= 1 && f.N <= 64) {
+        const int g2 = grid_for(f.plane, 128);
+        if (f.N <= 32) fit_hist_regs<32><<<g2, 128, 0, s>>>(f);
+        else fit_hist_regs<64><<<g2, 128, 0, s>>>(f);
+      } else {
+        fit_kernel<kHist><<<g, 256, 0, s>>>(f);
+      }
+      break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
