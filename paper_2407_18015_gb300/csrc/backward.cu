@@ -1235,12 +1235,36 @@ __global__ void __launch_bounds__(256) hist_adj_fixup(Field f, int tiles_x, int 
       else if (d == 2) src[d] = rt + 72 * B + lr;   // w: the left tile's e ring (its right column)
       else src[d] = rt + lc;                        // s: the lower tile's n ring (its top row)
     }
-    for (int q = 0; q < B; ++q) {
-      float acc = grad[(long long)q * plane + gi];
+    // eight parameters at a time, every read first (the compiler cannot
+    // tell the planes' addresses apart, so a read after a store would wait
+    // for it), then the sums in the order grad, e, n, w, s and the stores
+    // (launched for at most 16 parameters: histograms of <= 16 bins, and
+    // the two of uniform / Epanechnikov)
 #pragma unroll
-      for (int d = 0; d < 4; ++d)
-        if (have[d]) acc += src[d][(d == 0 || d == 2) ? q * 8 : q * 32];
-      grad[(long long)q * plane + gi] = acc;
+    for (int q0 = 0; q0 < 16; q0 += 8) {
+      if (q0 >= B) break;
+      float gv[8], rv[8][4];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int q = q0 + j;
+        if (q < B) {
+          gv[j] = grad[(long long)q * plane + gi];
+#pragma unroll
+          for (int d = 0; d < 4; ++d)
+            rv[j][d] = have[d] ? src[d][(d == 0 || d == 2) ? q * 8 : q * 32] : 0.f;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int q = q0 + j;
+        if (q < B) {
+          float acc = gv[j];
+#pragma unroll
+          for (int d = 0; d < 4; ++d)
+            if (have[d]) acc += rv[j][d];
+          grad[(long long)q * plane + gi] = acc;
+        }
+      }
     }
   }
 }
