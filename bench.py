@@ -194,7 +194,7 @@ ADJ_EPAN_FLOPS_PER_VERTEX = 2 * EPAN_FLOPS_PER_VERTEX_TYPE
 # summarised in profiles/; None once a kernel has changed since its counters
 # were taken
 TRAFFIC_BYTES = {"fused": 93154816, "uniform": 88159744, "epanechnikov": 84930816,
-                 "histogram": 85625344, "hist_adjoint_16": 652988928}
+                 "histogram": 85625344, "hist_adjoint_16": 654388992}
 # warp instructions per launch of the same kernels (ncu smsp__inst_executed.sum,
 # profiles/instructions_bench_headline_1024x1024x20.md): the issue-rate
 # fraction reported beside the FP32 / HBM one; None once a kernel changed
