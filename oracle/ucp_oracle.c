@@ -873,7 +873,9 @@ int orc_fit(const float *ens, int N, int H, int W, int model, int B, double epan
         if (v < mn) mn = v;
         if (v > mx) mx = v;
       }
-      if (model != ORC_MVN && mn == mx) st |= ST_DEGENERATE;
+      /* a vertex with a non-finite member has no distribution (its
+       * parameters are NaN): not degenerate, whatever min and max are */
+      if (model != ORC_MVN && mn == mx && !(st & ST_NONFINITE)) st |= ST_DEGENERATE;
       if (st & ST_NONFINITE) {
         /* parameters are written as NaN below */
       } else if (model == ORC_UNIFORM) {

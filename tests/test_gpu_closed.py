@@ -373,3 +373,30 @@ def test_models_concurrent_match_single(ucp, ctx):
         ucp.ucp_probability_models(ctx.handle, ens, [ucp.make_desc("uniform",
                                                                    stencil=ucp.UCP_STENCIL_6)],
                                    1, omin[:1], omax[:1])
+
+
+@pytest.mark.parametrize("N", [1, 2, 20, 31, 32, 33, 50, 64, 65, 300])
+@pytest.mark.parametrize("bins", [1, 8, 9, 16, 17])
+def test_histogram_fit_matches_oracle(ucp, ctx, orc, N, bins):
+    """The histogram statistics pass alone (ucp_fit) across member counts on
+    both sides of the register path's bounds (32 and 64 members, 16 bins)
+    and of the 8-bit counters (255): range bit for bit, the same bin count
+    for every bin (mass * N), the same status, with non-finite members and
+    point masses."""
+    rng = np.random.default_rng(1000 * N + bins)
+    H, W = 13, 45
+    ens_np = rng.normal(size=(N, H, W)).astype(np.float32)
+    ens_np[:, 2, 3] = 0.75                       # point mass
+    ens_np[N // 2, 4, 4] = np.nan                # non-finite members
+    ens_np[N - 1, 5, 40] = np.inf
+    ens_np[0, 6, 7] = -np.inf
+    desc = ucp.make_desc("histogram", bins=bins)
+    params, fst = ctx.fit(_dev(ens_np), desc, with_status=True)
+    torch.cuda.synchronize()
+    gp = params.double().cpu().numpy()
+    op, ost = orc.fit(ens_np, desc.model, bins=bins)
+    np.testing.assert_array_equal(fst.cpu().numpy(), ost)
+    np.testing.assert_array_equal(gp[:2], op[:2])
+    np.testing.assert_array_equal(np.isnan(gp[2:]), np.isnan(op[2:]))
+    np.testing.assert_array_equal(np.nan_to_num(np.rint(gp[2:] * N)),
+                                  np.nan_to_num(np.rint(op[2:] * N)))
