@@ -61,6 +61,24 @@ def test_backward_matches_oracle(ucp, ctx, orc, model, mid, bins, cptype, bounda
     _close(g.cpu().numpy(), ref, f"{model} cp{cptype} b{boundary}")
 
 
+@pytest.mark.parametrize("model,mid,bins", MODELS + [("histogram", 2, 16)])
+@pytest.mark.parametrize("cptype", [1, 2])
+def test_backward_multi_tile_ragged(ucp, ctx, orc, model, mid, bins, cptype):
+    """A grid of 3 x 3 adjoint tiles (8 x 32), ragged in both directions:
+    partials handed between tiles through the rings (north / south and west
+    / east) and the fix-up pass, against the oracle."""
+    rng = np.random.default_rng(700 + 10 * mid + cptype + bins)
+    Hh, Ww = 21, 75
+    p = H_.random_params(mid, Hh, Ww, rng, bins=bins or 8).astype(np.float32)
+    W = rng.uniform(0, 1, (Hh, Ww)).astype(np.float32)
+    desc = ucp.make_desc(model, bins=bins or 8)
+    g = ctx.backward(_dev(p), desc, cptype, _dev(W))
+    torch.cuda.synchronize()
+    ref = orc.grad(p.astype(np.float64), mid, W.astype(np.float64), cptype=cptype,
+                   bins=bins or 8)
+    _close(g.cpu().numpy(), ref, f"{model} B{bins} cp{cptype} 21x75")
+
+
 @pytest.mark.parametrize("model,mid,bins", MODELS)
 def test_backward_point_masses(ucp, ctx, orc, model, mid, bins):
     rng = np.random.default_rng(7)
