@@ -1118,12 +1118,7 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     __threadfence();
     slot_sm = got;
   }
-  for (int l = threadIdx.x; l < HALO; l += NTHREADS) {
-    const int r = l / HX, c = l - r * HX;
-    const int gy = ty0 + r - 1, gx = tx0 + c - 1;
-    if (gy < 0 || gy >= ylim || gx < 0 || gx >= f.W) continue;
-    hist_rows_from_params<HALO, RS, RB>(f, sm, R4, l, (long long)gy * f.W + gx, B, mirrored);
-  }
+  hist_rows_from_params_tile<HALO, RS, RB, HX, true>(f, sm, R4, ty0, tx0, ylim, B, mirrored);
   __syncthreads();
   const int slot = slot_sm;
   const int v = threadIdx.x;

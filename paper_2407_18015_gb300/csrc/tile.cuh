@@ -446,28 +446,40 @@ __device__ __forceinline__ void hist_row_table_counts(float *sm, float4 *R, int 
   sm[3 * HALO + l] = (float)st;
 }
 
-// Per-bin rows, lo, hi, total and status of one staged vertex straight from
-// its parameters (mirrored: -X, bins reversed), the masses held in
-// registers; the same rows and status as hist_row_table builds from a
-// parameter tile.
+// The parameters of one vertex in registers (mirrored: -X, bins
+// reversed): support [a, b] and masses m[0..B-1], read with every load in
+// flight at once.
+template <int RB>
+struct HistParamRegs {
+  float a, b, m[RB];
+  __device__ __forceinline__ void load(const Field &f, long long gi, int B, bool mirrored) {
+    const long long plane = f.plane;
+    const float a0 = __ldg(f.params + gi), b0 = __ldg(f.params + plane + gi);
+    a = mirrored ? -b0 : a0;
+    b = mirrored ? -a0 : b0;
+#pragma unroll
+    for (int q = 0; q < RB; ++q)
+      m[q] = q < B ? __ldg(f.params + (long long)(2 + (mirrored ? B - 1 - q : q)) * plane + gi)
+                   : 0.f;
+  }
+};
+
+// Per-bin rows, lo, hi, total and status of one staged vertex from its
+// parameters in registers; the same rows and status as hist_row_table
+// builds from a parameter tile.
 template <int HALO, int RS, int RB>
-__device__ __forceinline__ void hist_rows_from_params(const Field &f, float *sm, float4 *R, int l,
-                                                      long long gi, int B, bool mirrored) {
-  const long long plane = f.plane;
-  const float a0 = f.params[gi], b0 = f.params[plane + gi];
-  const float a = mirrored ? -b0 : a0, b = mirrored ? -a0 : b0;
+__device__ __forceinline__ void hist_rows_build_regs(const HistParamRegs<RB> &P, float *sm,
+                                                     float4 *R, int l, int B) {
+  const float a = P.a, b = P.b;
   uint8_t st = (!isfinite(a) || !isfinite(b)) ? V_NONFINITE
                                              : (a > b ? V_BAD : (a == b ? V_DEGENERATE : 0));
-  float m[RB];
   float t = 0.f;
 #pragma unroll
   for (int q = 0; q < RB; ++q) {
-    m[q] = 0.f;
     if (q < B) {
-      m[q] = __ldg(f.params + (long long)(2 + (mirrored ? B - 1 - q : q)) * plane + gi);
-      if (!isfinite(m[q])) st |= V_NONFINITE;
-      else if (m[q] < 0.f) st |= V_BAD;
-      t += m[q];
+      if (!isfinite(P.m[q])) st |= V_NONFINITE;
+      else if (P.m[q] < 0.f) st |= V_BAD;
+      t += P.m[q];
     }
   }
   R += l;
@@ -484,7 +496,7 @@ __device__ __forceinline__ void hist_rows_from_params(const Field &f, float *sm,
 #pragma unroll
     for (int k = 0; k < RB; ++k) {
       if (k < B) {
-        c += m[k];
+        c += P.m[k];
         const float sn = k + 1 < B ? t - c : 0.f;
         R[k * RS] = make_float4(sk, t - sk, (sk - sn) * ih, k + 1 < B ? (float)(k + 1) * h : w);
         sk = sn;
@@ -496,6 +508,45 @@ __device__ __forceinline__ void hist_rows_from_params(const Field &f, float *sm,
   sm[HALO + l] = b;
   sm[2 * HALO + l] = t;
   sm[3 * HALO + l] = (float)st;
+}
+
+// Per-bin rows of every in-grid halo vertex of the tile at (ty0, tx0) from
+// the parameters.  BATCH: each thread first reads the parameters of all the
+// halo vertices it owns (l = tid, tid + NTHREADS, ...), every load in
+// flight at once, then builds their rows -- for kernels at two CTAs per SM,
+// whose CTA otherwise waits for two rounds of reads (2048 x 2048 x 50, 16
+// bins: forward from parameters 1.11 -> 1.06 ms, adjoint 2.85 -> 2.83 ms);
+// else one vertex after another (the 8-bin forward at four CTAs per SM:
+// 0.53 ms, against 0.57 batched).
+template <int HALO, int RS, int RB, int HX, bool BATCH>
+__device__ __forceinline__ void hist_rows_from_params_tile(const Field &f, float *sm, float4 *R,
+                                                           int ty0, int tx0, int ylim, int B,
+                                                           bool mirrored) {
+  if constexpr (!BATCH) {
+    for (int l = threadIdx.x; l < HALO; l += NTHREADS) {
+      const int r = l / HX, c = l - r * HX;
+      const int gy = ty0 + r - 1, gx = tx0 + c - 1;
+      if (gy < 0 || gy >= ylim || gx < 0 || gx >= f.W) continue;
+      HistParamRegs<RB> P;
+      P.load(f, (long long)gy * f.W + gx, B, mirrored);
+      hist_rows_build_regs<HALO, RS, RB>(P, sm, R, l, B);
+    }
+    return;
+  }
+  constexpr int PER = (HALO + NTHREADS - 1) / NTHREADS;
+  HistParamRegs<RB> P[PER];
+  bool in[PER];
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int l = threadIdx.x + p * NTHREADS;
+    const int r = l / HX, c = l - r * HX;
+    const int gy = ty0 + r - 1, gx = tx0 + c - 1;
+    in[p] = l < HALO && gy >= 0 && gy < ylim && gx >= 0 && gx < f.W;
+    if (in[p]) P[p].load(f, (long long)gy * f.W + gx, B, mirrored);
+  }
+#pragma unroll
+  for (int p = 0; p < PER; ++p)
+    if (in[p]) hist_rows_build_regs<HALO, RS, RB>(P[p], sm, R, threadIdx.x + p * NTHREADS, B);
 }
 
 // ---------------------------------------------------------------------------
@@ -1034,12 +1085,7 @@ __device__ __forceinline__ bool process_tile(const Field &f, int ty0, int tx0, f
   } else if constexpr (MODEL == kHist && RB > 0) {
     // per-bin rows straight from the parameters (masses in registers)
     constexpr int RS = hist_r4_stride(HALO);
-    for (int l = threadIdx.x; l < HALO; l += NTHREADS) {
-      const int r = l / HX, c = l - r * HX;
-      const int gy = ty0 + r - 1, gx = tx0 + c - 1;
-      if (gy < 0 || gy >= ylim || gx < 0 || gx >= f.W) continue;
-      hist_rows_from_params<HALO, RS, RB>(f, sm, R4, l, (long long)gy * f.W + gx, f.B, false);
-    }
+    hist_rows_from_params_tile<HALO, RS, RB, HX, (RB > 8)>(f, sm, R4, ty0, tx0, ylim, f.B, false);
   } else {
     for (int l = threadIdx.x; l < HALO; l += NTHREADS) {
       const int r = l / HX, c = l - r * HX;
