@@ -348,12 +348,17 @@ int ucp_backward_static(const float *params, int H, int W, const ucp_model_desc 
                         int cptype, const float *weight, float *grad_params, ucp_stream stream);
 
 /* Batched launch: many fields of different sizes, member counts, models
- * (uniform, Epanechnikov, histogram) and types in one persistent kernel.
+ * (uniform, Epanechnikov, histogram) and types in a few persistent kernels:
+ * one per class of fields (model, tile height, histogram row bound, members
+ * staged by the tensor memory accelerator or by asynchronous copies) and
+ * one generic kernel for the rest (more than 16 bins, 32-row tiles).
  * ucp_batch_add records a field (device pointers, borrowed until the batch
  * is destroyed); ucp_batch_tune times the tile shapes on `stream` and keeps
  * the fastest per model (optional; call before any stream capture);
- * ucp_batch_run enqueues the whole batch (a counter reset and one kernel
- * launch, so it can be captured into a CUDA graph). */
+ * ucp_batch_run enqueues the whole batch: a counter reset on `stream`, then
+ * the kernels on the batch's own streams, forked from `stream` and joined
+ * back into it (no allocation or synchronisation, so it can be captured
+ * into a CUDA graph). */
 int ucp_batch_create(ucp_ctx *ctx, ucp_batch **batch);
 int ucp_batch_add(ucp_batch *batch, const float *ens, int N, int H, int W,
                   const ucp_model_desc *desc, unsigned cptypes, float *out_min, float *out_max);
