@@ -194,12 +194,12 @@ ADJ_EPAN_FLOPS_PER_VERTEX = 2 * EPAN_FLOPS_PER_VERTEX_TYPE
 # summarised in profiles/; None once a kernel has changed since its counters
 # were taken
 TRAFFIC_BYTES = {"fused": 93154816, "uniform": 88159744, "epanechnikov": 84930816,
-                 "histogram": 85625344, "hist_adjoint_16": 654388992}
+                 "histogram": 85532160, "hist_adjoint_16": 654388992}
 # warp instructions per launch of the same kernels (ncu smsp__inst_executed.sum,
 # profiles/instructions_bench_headline_1024x1024x20.md): the issue-rate
 # fraction reported beside the FP32 / HBM one; None once a kernel changed
 ISSUE_WARP_INSTR = {"fused": 206773693, "uniform": 23585236, "epanechnikov": 62221552,
-                    "histogram": 141878595}
+                    "histogram": 142005566}
 ISSUE_SOURCE = "profiles/instructions_bench_headline_1024x1024x20.md"
 
 
